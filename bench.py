@@ -1,0 +1,352 @@
+"""Benchmark of the acoustic FDTD hot path on GB300.
+
+Default workload (one "step" = one full solve): the field-scale 2D slice —
+619 x 1000 cells at 10 m + 50-cell CPML left/right/bottom, free surface, seeded
+procedural velocity, one Ricker source at the surface centre, 1000 receivers,
+nt = 8000 steps of 1 ms, FP32 snapshots every 10 steps for the first 5 s.
+
+Metric: cell-updates per second over the padded grid (Gcell/s). `value` is
+device-timed (CUDA events on the solver's stream, inputs resident, L2 flushed
+between timed solves); `e2e` repeats the solve through the C ABI with pinned
+host buffers (model upload, gather and snapshot download inside the timing).
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+Under torchrun every rank runs an independent replica (the single-shot solve
+does not shard); value = all ranks' cell-updates / max-over-ranks time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s (FP32 fwd, adjoint) vs HBM roofline; gradient s/shot at tol"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c2x32"])
+    ap.add_argument("--nt", type=int, default=0, help="override nt (profiling runs only)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload(args):
+    import synth
+    nt = args.nt or 8000
+    cfg = synth.config_c2(nt=nt)
+    nshots = 32 if args.workload == "c2x32" else 1
+    if nshots > 1:
+        cfg["src"] = np.stack([500.0 + 280.0 * np.arange(nshots), np.full(nshots, 10.0)], axis=1)
+        cfg.update(snap_every=0, snap_end=0)
+    return cfg, nshots
+
+
+def padded_cells(cfg):
+    nb = cfg["nb"]
+    return (nb[0] + cfg["nz"] + nb[1]) * (nb[4] + cfg["nx"] + nb[5])
+
+
+def algorithmic_bytes_per_launch(cfg, nshots):
+    """Bytes one step-kernel launch must move at minimum: 16 B per cell (read
+    p^n, p^{n-1}, c; write p^{n+1}), 16 B per CPML strip cell and axis (psi,
+    zeta read + write), 4 B per receiver sample, 4 B per interior cell at
+    snapshot steps (averaged over the launches)."""
+    nb = cfg["nb"]
+    NZ = nb[0] + cfg["nz"] + nb[1]
+    NX = nb[4] + cfg["nx"] + nb[5]
+    cells = NZ * NX
+    strip = 0
+    if cfg.get("bc") == "cpml":
+        strip = (nb[4] + nb[5]) * NZ + (nb[0] + nb[1]) * NX
+    rec = len(cfg["rec"]) * 4
+    nsnap = 0
+    if cfg.get("snap_every", 0) > 0:
+        end = min(cfg["snap_end"], cfg["nt"])
+        nsnap = (end - cfg["snap_begin"] + cfg["snap_every"] - 1) // cfg["snap_every"]
+    snap = nsnap * cfg["nz"] * cfg["nx"] * 4 / cfg["nt"]
+    return nshots * (16 * cells + 16 * strip + rec + snap)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_file, key):
+    """DRAM bytes per launch recorded by the committed ncu summary for `key`,
+    valid only while the kernel source is unchanged (sha1 recorded beside it)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_2605_30541_gb300", "csrc", kernel_file)
+    try:
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        for ln in open(path):
+            f = ln.split()
+            if len(f) >= 3 and f[0] == key and f[1] == sha:
+                return float(f[2])
+    except OSError:
+        pass
+    return None
+
+
+def cpu_oracle_rate(cfg, target_s=12.0):
+    """FP64 oracle throughput on a bounded sample of the workload (first steps
+    of the same solve), sized to about target_s seconds of CPU work."""
+    import oracle
+    oracle.build()
+    cells = padded_cells(cfg)
+    probe = dict(cfg, nt=40, snap_every=0, snap_end=0)
+    v64 = cfg["vel"].astype(np.float64)
+    w64 = cfg["wavelet"].astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.forward(probe, v64, w64[:40], src=cfg["src"][0], rec=cfg["rec"])
+    rate = 40 * cells / (time.perf_counter() - t0)
+    nt = int(max(40, min(cfg["nt"], target_s * rate / cells)))
+    samp = dict(cfg, nt=nt, snap_end=min(cfg.get("snap_end", 0), nt))
+    t0 = time.perf_counter()
+    oracle.forward(samp, v64, w64[:nt], src=cfg["src"][0], rec=cfg["rec"], snaps=samp.get("snap_every", 0) > 0)
+    dt = time.perf_counter() - t0
+    return {"value": nt * cells / dt / 1e9, "unit": "Gcell/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "first %d of %d steps of the same slice solve (FP64, OpenMP over rows), %.1f s" %
+                      (nt, cfg["nt"], dt)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cfg, _ = workload(args)
+    import oracle
+    oracle.build()
+    cells = padded_cells(cfg)
+    v64 = cfg["vel"].astype(np.float64)
+    w64 = cfg["wavelet"].astype(np.float64)
+    probe = dict(cfg, nt=30, snap_every=0, snap_end=0)
+    t0 = time.perf_counter()
+    oracle.forward(probe, v64, w64[:30], src=cfg["src"][0], rec=cfg["rec"])
+    rate = 30 * cells / (time.perf_counter() - t0)
+    budget = 150.0 / max(1, args.steps + args.warmup)   # whole run within a few minutes
+    nt = int(max(30, min(cfg["nt"], budget * rate / cells)))
+    samp = dict(cfg, nt=nt, snap_end=min(cfg.get("snap_end", 0), nt))
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.forward(samp, v64, w64[:nt], src=cfg["src"][0], rec=cfg["rec"], snaps=samp.get("snap_every", 0) > 0)
+        if it >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    per = statistics.mean(times)
+    value = nt * cells / per / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gcell/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "c2 slice 619x1000 + 50-cell CPML, free top (bounded sample: first %d of %d steps)"
+                       % (nt, cfg["nt"]), "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "Gcell/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "first %d of %d steps per step" % (nt, cfg["nt"])},
+            "e2e": {"value": value, "unit": "Gcell/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2605_30541_gb300 as pkg
+
+    cfg, nshots = workload(args)
+    nt = cfg["nt"]
+    cells = padded_cells(cfg)
+    rec = np.ascontiguousarray(cfg["rec"])
+    src = np.ascontiguousarray(cfg["src"][:nshots])
+    stream = torch.cuda.current_stream()
+    sim = pkg.Simulator(cfg, cfg["vel"], max_shots=nshots, max_rec=len(rec), stream=stream)
+    nsnap = sim.info.nsnap
+    dev = torch.device("cuda", local)
+    vel_d = torch.as_tensor(cfg["vel"], device=dev)
+    wav_d = torch.as_tensor(cfg["wavelet"], device=dev)
+    gather_d = torch.empty((nshots, nt, len(rec)), dtype=torch.float32, device=dev)
+    snaps_d = torch.empty((nshots, nsnap, cfg["nz"], cfg["nx"]), dtype=torch.float32, device=dev) if nsnap else None
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def solve():
+        pkg.sim_forward(sim.handle, nshots, wav_d, src, len(rec), rec, gather_d, snaps_d, None)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    sim.sync()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            solve()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    sim.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total = sum(step_ms) / 1e3
+    t = torch.tensor([total], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    tmax = float(t.item())
+    units = world * args.steps * nshots * nt * cells
+    value = units / tmax / 1e9
+
+    # roofline of the step kernel: nt launches per solve (gaps included in the duration)
+    per_launch_s = (total / args.steps) / nt
+    algo = algorithmic_bytes_per_launch(cfg, nshots)
+    peak, peak_kind = read_peaks()
+    achieved = algo / per_launch_s / 1e9
+    key = "step2d_%s" % args.workload
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": ncu_traffic("fwd2d.cu", key), "kernel": "k_step2d",
+            "peak_kind": peak_kind + " (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind,
+            "algorithmic_bytes_per_launch": algo, "avg_launch_us": per_launch_s * 1e6}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        vel_h = torch.as_tensor(cfg["vel"]).pin_memory()
+        wav_h = torch.as_tensor(cfg["wavelet"]).pin_memory()
+        gather_h = torch.empty((nshots, nt, len(rec)), dtype=torch.float32).pin_memory()
+        snaps_h = torch.empty((nshots, nsnap, cfg["nz"], cfg["nx"]), dtype=torch.float32).pin_memory() if nsnap else None
+        for _ in range(max(1, min(2, args.warmup))):
+            pkg.sim_set_model(sim.handle, vel_h)
+            pkg.sim_forward(sim.handle, nshots, wav_h, src, len(rec), rec, gather_h, snaps_h, None)
+        et = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pkg.sim_set_model(sim.handle, vel_h)
+            pkg.sim_forward(sim.handle, nshots, wav_h, src, len(rec), rec, gather_h, snaps_h, None)
+            torch.cuda.synchronize()
+            et.append(time.perf_counter() - t0)
+        te = torch.tensor([sum(et)], dtype=torch.float64, device=dev)
+        if dist:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        h2d = vel_h.numel() * 4 + wav_h.numel() * 4
+        d2h = gather_h.numel() * 4 + (snaps_h.numel() * 4 if snaps_h is not None else 0)
+        e2e = {"value": world * args.steps * nshots * nt * cells / float(te.item()) / 1e9, "unit": "Gcell/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": float(te.item()) / args.steps * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_rate(cfg)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Gcell/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": ("c2: 2D slice 619x1000 (+50-cell CPML left/right/bottom, free top), "
+                                        "nt=%d, %d receivers, %d FP32 snapshots, %d shot(s) per GPU"
+                                        % (nt, len(rec), nsnap, nshots)),
+                           "padded_cells": cells, "l2": "flushed between timed solves (%d MB write)" %
+                                                        (L2_FLUSH_BYTES >> 20),
+                           "parallelism": "replicas x%d" % world},
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(), "e2e": e2e,
+                "gpu_launches": args.steps * (nt + 1)}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * sim.h — C ABI of the GB300 acoustic FDTD library (libsim).
+ *
+ * The library solves the constant-density acoustic wave equation
+ *     (1/v^2) p_tt - lap p (+ eta p_t) = s(x, t)                     (paper Sec. 2, Eq. acoustic;
+ *                                                                     App. E.2, Eq. acoustic_2d, Eq. cerjan_pde)
+ * on a regular grid with an 8th-order central Laplacian and second-order
+ * leapfrog in time (App. E.3, Tab. params), zero initial state (App. E.2),
+ * a free surface p = 0 on top (Eq. free_surface), an absorbing layer on the
+ * other faces (Cerjan sponge, Eq. cerjan_damp; or a CPML), a point source
+ * with a given wavelet (Sec. 2, App. E.4) and receivers that sample the field
+ * into a shot gather R p (Sec. 2), plus wavefield snapshots every k steps
+ * (App. E.3.3). It also returns the exact gradient of the L2 data misfit with
+ * respect to velocity (adjoint-state method on the discrete scheme; the paper
+ * names FWI as the consumer of these solves, Sec. 1).
+ *
+ * The discrete scheme, per padded cell i and step n = 0 .. nt-1:
+ *   (1+a_i) p_i^{n+1} = 2 p_i^n - (1-a_i) p_i^{n-1} + c_i ((L p^n)_i + s_i^n)
+ *   c = v^2 dt^2, a = eta v^2 dt / 2 (sponge; 0 otherwise),
+ *   s^n = w[n] / h^d at the source (bi/tri-linear weights), gather[n] = R p^n.
+ *
+ * Conventions (all entry points):
+ *  - Grids are row-major [z][y][x] (x fastest); 2D problems have ny = 1.
+ *    Depth z is the slowest axis; z = 0 is the top of the interior.
+ *  - Positions are metres from the interior origin, ordered (x, z) in 2D and
+ *    (x, y, z) in 3D, and must lie inside the interior box [0, (n-1) h].
+ *  - Data pointers (velocity, wavelet, gathers, snapshots, gradients) may be
+ *    device or host memory; the library tells them apart. Host inputs are
+ *    copied in; when any output is host memory the call synchronises its
+ *    stream before returning. Position arrays are read on the host.
+ *  - The element type of every `void*` data array is the handle's precision:
+ *    float for SIM_FP32, double for SIM_FP64 (FP16 snapshots are `uint16`
+ *    IEEE half with a float scale per snapshot).
+ *  - The caller owns every argument buffer. The library owns its padded
+ *    fields, coefficients, absorbing-layer memory, checkpoints and staging
+ *    buffers; all are allocated in sim_create and freed by sim_destroy.
+ *  - Calls are ordered on the handle's CUDA stream and return after enqueue
+ *    (unless an output is host memory). Device-side failures (non-finite
+ *    values, a bounded wait that gave up) surface at the next call or at
+ *    sim_sync. Errors are sticky per handle; sim_last_error explains them.
+ *  - No entry point aborts or throws; every one returns a sim_status.
+ */
+#ifndef GB300_SIM_H
+#define GB300_SIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SIM_OK = 0,
+    SIM_ERR_ARG = 1,            /* an argument is invalid (message in sim_last_error) */
+    SIM_ERR_CFL = 2,            /* v_max dt / h above the stability bound of App. E.3.2 */
+    SIM_WARN_DISPERSION = 3,    /* non-fatal: h > v_min / (4 f_max) (App. E.3.1) */
+    SIM_ERR_OOM = 4,            /* device or host allocation failed */
+    SIM_ERR_CUDA = 5,           /* a CUDA runtime call failed */
+    SIM_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+    SIM_ERR_UNSTABLE = 7,       /* non-finite values appeared in the field or outputs */
+    SIM_ERR_STATE = 8,          /* call made in the wrong state (e.g. no model set) */
+    SIM_ERR_UNSUPPORTED = 9     /* valid request this build does not implement */
+} sim_status;
+
+typedef enum { SIM_BC_SPONGE = 0, SIM_BC_CPML = 1, SIM_BC_NONE = 2 } sim_bc;
+typedef enum { SIM_FP32 = 0, SIM_FP64 = 1 } sim_precision;
+
+/* Problem description. Zero-initialise, then set the fields you need;
+ * sim_desc_init fills the defaults. */
+typedef struct {
+    int ndim;             /* 2 or 3 */
+    int nz, ny, nx;       /* interior cells (ny = 1 in 2D) */
+    double h;             /* isotropic grid spacing, m (Tab. params: 10 m) */
+    double dt;            /* time step, s (Tab. params: 1 ms) */
+    int nt;               /* steps; gather rows and snapshot steps n = 0 .. nt-1 */
+    int space_order;      /* 8 (M = 4); 0 means 8 */
+    int bc;               /* sim_bc */
+    int nb[6];            /* absorbing cells per face: -z,+z,-y,+y,-x,+x */
+    int free_surface;     /* 1: row z = 0 held at p = 0 (requires nb[0] = 0) */
+    double R;             /* design reflection of the absorbing layer; <= 0 means 1e-3 */
+    double f_ref;         /* CPML alpha reference frequency (Hz); <= 0 means 10 */
+    double f_max;         /* highest source frequency for the dispersion check; 0 skips it */
+    int snap_every;       /* snapshot period k (App. E.3.3); 0: no snapshots */
+    int snap_begin;       /* first snapshot step */
+    int snap_end;         /* snapshots at n = begin + j*k < min(end, nt) */
+    int snap_fp16;        /* 0: snapshots in the handle precision; 1: FP16 + per-snapshot scale */
+    int max_shots;        /* most shots one call carries; <= 0 means 1 */
+    int max_rec;          /* most receivers one call carries */
+    int precision;        /* sim_precision */
+    int skip_cfl_check;   /* 1: accept dt above the stability bound (tests only) */
+} sim_desc;
+
+/* Host-side facts about a description (no GPU needed). */
+typedef struct {
+    int NZ, NY, NX;           /* padded grid = interior + absorbing cells */
+    int nsnap;                /* snapshots per shot */
+    double courant;           /* v_max dt / h (0 if v_max unknown) */
+    double courant_limit;     /* paper bound s_max = 1/sqrt(d sum_{m>=1} |a_m|) (App. E.3.2) */
+    double courant_exact;     /* von Neumann bound 2/sqrt(d * 6.5016) of this stencil */
+    double vmin, vmax;        /* model range (from sim_set_model, or as given to sim_plan) */
+    double c_damp[6];         /* sponge c_damp = 1.5 ln(1/R)/nb per face (0 where nb = 0) */
+    long long cells_per_shot; /* padded cells updated per shot per step */
+    size_t device_bytes;      /* device memory the handle owns (0 from sim_plan) */
+    int tile_x, tile_y, tile_z; /* tile of the stencil kernels the autotuner chose */
+} sim_info;
+
+typedef struct sim_s *sim_t;
+
+/* Fill defaults: space_order 8, R 1e-3, f_ref 10 Hz, max_shots 1, FP32. */
+void sim_desc_init(sim_desc *d);
+
+/* Validate a description on the host and report its layout. With vmax > 0
+ * also applies the CFL check (SIM_ERR_CFL) and, with vmin > 0 and
+ * f_max > 0, the dispersion check (SIM_WARN_DISPERSION). Never touches the GPU. */
+sim_status sim_plan(const sim_desc *d, double vmin, double vmax, sim_info *out);
+
+/* Create a solver on the current CUDA device. `vel` is the interior velocity
+ * [nz][ny][nx] in m/s (host or device, handle precision) or NULL to set it
+ * later; `cuda_stream` is a cudaStream_t (NULL: the legacy default stream).
+ * Allocates every device buffer the handle needs. On failure *out is NULL. */
+sim_status sim_create(const sim_desc *d, const void *vel, void *cuda_stream, sim_t *out);
+
+/* Replace the velocity model (same layout as in sim_create). Recomputes
+ * c = v^2 dt^2 and the absorbing-layer coefficients; velocities in the
+ * absorbing layers copy the nearest interior cell. Returns SIM_ERR_CFL when
+ * v_max dt / h exceeds the bound (unless skip_cfl_check), SIM_WARN_DISPERSION
+ * (model still set) when the grid under-samples f_max, SIM_ERR_ARG when a
+ * velocity is not finite or not positive. Synchronises the stream. */
+sim_status sim_set_model(sim_t s, const void *vel);
+
+/* Forward modelling of `nshots` shots sharing the model and the receivers.
+ *   wavelet   [nt]                source time function w(t_n), shared by the shots
+ *   src_pos   [nshots][ndim]      source positions (host), metres
+ *   rec_pos   [nrec][ndim]        receiver positions (host), metres
+ *   gather    [nshots][nt][nrec]  out: R p^n (NULL: not recorded)
+ *   snaps     [nshots][nsnap][nz][ny][nx]  out: interior p^n at snapshot steps
+ *             (NULL: none); FP16 when desc.snap_fp16, else handle precision
+ *   snap_scale [nshots][nsnap]    out (FP16 only): scale s, value = half * s,
+ *             s = 2^(floor(log2 max|p|) - 14), 1 for an all-zero snapshot
+ * SIM_ERR_ARG for nshots > max_shots, nrec > max_rec or positions outside the
+ * interior. */
+sim_status sim_forward(sim_t s, int nshots, const void *wavelet, const double *src_pos,
+                       int nrec, const double *rec_pos, void *gather, void *snaps,
+                       float *snap_scale);
+
+/* Misfit J = 1/2 sum (g - d_obs)^2 over shots, steps and receivers, and its
+ * exact gradient with respect to the interior velocity, by the adjoint-state
+ * method on the discrete scheme. The forward pass keeps sqrt(nt)-spaced
+ * checkpoints and recomputes each segment in reverse.
+ *   d_obs      [nshots][nt][nrec]  observed data
+ *   gather_out [nshots][nt][nrec]  out: modelled gather (NULL ok)
+ *   misfit_out [1] (host)          out: J, accumulated over shots in FP64
+ *   ckpt_fp16  1: checkpoints and the stored imaging terms in FP16 with a
+ *              power-of-two scale per state; 0: handle precision
+ *   grad_v     [nz][ny][nx]        out: dJ/dv ACCUMULATED (+=) in handle
+ *              precision, after an FP64 sum over the shots
+ * Sponge and no-absorption boundaries; SIM_ERR_UNSUPPORTED for CPML. */
+sim_status sim_adjoint(sim_t s, int nshots, const void *wavelet, const double *src_pos,
+                       int nrec, const double *rec_pos, const void *d_obs,
+                       void *gather_out, double *misfit_out, int ckpt_fp16, void *grad_v);
+
+/* One entry of a batch: a handle (model + grid) and its shots. */
+typedef struct {
+    sim_t sim;
+    int nshots;
+    const void *wavelet;      /* [nt] */
+    const double *src_pos;    /* [nshots][ndim] (host) */
+    int nrec;
+    const double *rec_pos;    /* [nrec][ndim] (host) */
+    void *gather;             /* [nshots][nt][nrec] out (NULL: not recorded) */
+} sim_batch_item;
+
+/* Forward modelling of many shots on many (uneven) grids as ONE persistent
+ * kernel launch, replayed from a captured CUDA graph. All handles must share
+ * dt, nt and precision. Tiles of all shots are scheduled as a work list whose
+ * entries wait only on their spatial neighbours of the previous step; every
+ * such wait is bounded and returns SIM_ERR_TIMEOUT rather than hanging.
+ * `cuda_stream` as in sim_create. */
+sim_status sim_batch(int nitems, const sim_batch_item *items, void *cuda_stream);
+
+/* Wait for the handle's stream and report any device-side failure. */
+sim_status sim_sync(sim_t s);
+
+/* Layout and model facts of a live handle. */
+sim_status sim_get_info(sim_t s, sim_info *out);
+
+/* Human-readable reason of the last failure on this handle (or on this thread
+ * when s is NULL). Never NULL. */
+const char *sim_last_error(sim_t s);
+
+/* Free every resource of the handle (NULL is a no-op). */
+void sim_destroy(sim_t s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,811 @@
+// libsim C ABI: descriptor validation, device allocation, model set-up,
+// acquisition geometry (receiver and injection lists per tile) and the time
+// loop. Host code only; kernels live in the other translation units.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sim_internal.h"
+#include "stencil.cuh"
+
+using namespace gsim;
+
+namespace {
+
+thread_local std::string t_err;
+
+std::string vfmt(const char *fmt, va_list ap) {
+    char buf[1024];
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    return buf;
+}
+
+sim_status thread_fail(sim_status code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    t_err = vfmt(fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+long long roundup(long long v, long long m) { return (v + m - 1) / m * m; }
+
+// Stability bounds of the 8th-order scheme (App. E.3.2).
+double symbol_sum_abs() { return std::fabs(kC1) + std::fabs(kC2) + std::fabs(kC3) + std::fabs(kC4); }
+double courant_paper(int d) { return 1.0 / std::sqrt(d * symbol_sum_abs()); }
+double courant_exact(int d) {
+    const double sym = -(kC0 - 2 * kC1 + 2 * kC2 - 2 * kC3 + 2 * kC4);  // symbol at theta = pi
+    return 2.0 / std::sqrt(d * sym);
+}
+
+int nsnap_of(const sim_desc &d) {
+    if (d.snap_every <= 0) return 0;
+    const int end = std::min(d.snap_end, d.nt);
+    if (d.snap_begin < 0 || end <= d.snap_begin) return 0;
+    return (end - d.snap_begin + d.snap_every - 1) / d.snap_every;
+}
+
+void normalise(sim_desc &d) {
+    if (d.space_order == 0) d.space_order = 8;
+    if (!(d.R > 0)) d.R = 1e-3;
+    if (!(d.f_ref > 0)) d.f_ref = 10.0;
+    if (d.max_shots <= 0) d.max_shots = 1;
+    if (d.ndim == 2) {
+        d.ny = 1;
+        d.nb[2] = d.nb[3] = 0;
+    }
+}
+
+sim_status validate(const sim_desc &d) {
+    if (d.ndim != 2 && d.ndim != 3) return thread_fail(SIM_ERR_ARG, "ndim must be 2 or 3 (got %d)", d.ndim);
+    if (d.nz < 1 || d.nx < 1 || d.ny < 1) return thread_fail(SIM_ERR_ARG, "grid extents must be >= 1");
+    if (!(d.h > 0) || !(d.dt > 0)) return thread_fail(SIM_ERR_ARG, "h and dt must be positive");
+    if (d.nt < 1) return thread_fail(SIM_ERR_ARG, "nt must be >= 1");
+    if (d.space_order != 8) return thread_fail(SIM_ERR_UNSUPPORTED, "only space_order 8 is built");
+    if (d.bc < 0 || d.bc > 2) return thread_fail(SIM_ERR_ARG, "unknown bc %d", d.bc);
+    for (int k = 0; k < 6; k++)
+        if (d.nb[k] < 0 || d.nb[k] > 4096) return thread_fail(SIM_ERR_ARG, "nb[%d] out of range", k);
+    if (d.free_surface && d.nb[0] != 0)
+        return thread_fail(SIM_ERR_ARG, "a free surface needs nb[0] = 0 (no absorbing layer on top)");
+    if (d.snap_every < 0) return thread_fail(SIM_ERR_ARG, "snap_every must be >= 0");
+    if (d.precision != SIM_FP32 && d.precision != SIM_FP64) return thread_fail(SIM_ERR_ARG, "bad precision");
+    if (d.snap_fp16 && d.precision != SIM_FP32)
+        return thread_fail(SIM_ERR_ARG, "FP16 snapshots need an FP32 handle");
+    if (d.max_rec < 0) return thread_fail(SIM_ERR_ARG, "max_rec must be >= 0");
+    const long long NZ = (long long)d.nb[0] + d.nz + d.nb[1];
+    const long long NY = d.ndim == 3 ? (long long)d.nb[2] + d.ny + d.nb[3] : 1;
+    const long long NX = (long long)d.nb[4] + d.nx + d.nb[5];
+    if (NZ > (1 << 20) || NY > (1 << 20) || NX > (1 << 20) || NZ * NY * NX > (1LL << 36))
+        return thread_fail(SIM_ERR_ARG, "grid too large");
+    return SIM_OK;
+}
+
+Geom make_geom(const sim_desc &d) {
+    Geom g{};
+    g.ndim = d.ndim;
+    g.nz = d.nz;
+    g.ny = d.ndim == 3 ? d.ny : 1;
+    g.nx = d.nx;
+    g.nbz0 = d.nb[0];
+    g.nbz1 = d.nb[1];
+    g.nby0 = d.ndim == 3 ? d.nb[2] : 0;
+    g.nby1 = d.ndim == 3 ? d.nb[3] : 0;
+    g.nbx0 = d.nb[4];
+    g.nbx1 = d.nb[5];
+    g.NZ = g.nbz0 + g.nz + g.nbz1;
+    g.NY = g.nby0 + g.ny + g.nby1;
+    g.NX = g.nbx0 + g.nx + g.nbx1;
+    g.oz = g.nbz0;
+    g.oy = g.nby0;
+    g.ox = g.nbx0;
+    const int G = kGhost;
+    g.P = (int)roundup(G + roundup(g.NX, kRoundX) + G, 32);
+    g.PY = d.ndim == 3 ? (int)(G + roundup(g.NY, kRoundY) + G) : 1;
+    const long long planes = G + roundup(g.NZ, kRoundZ) + G;
+    g.fstride = planes * g.PY * g.P;
+    g.org = ((long long)G * g.PY + (d.ndim == 3 ? G : 0)) * g.P + G;
+    g.fs = d.free_surface;
+    return g;
+}
+
+void fill_info(const sim_desc &d, sim_info *out) {
+    memset(out, 0, sizeof(*out));
+    out->NZ = d.nb[0] + d.nz + d.nb[1];
+    out->NY = d.ndim == 3 ? d.nb[2] + d.ny + d.nb[3] : 1;
+    out->NX = d.nb[4] + d.nx + d.nb[5];
+    out->nsnap = nsnap_of(d);
+    out->courant_limit = courant_paper(d.ndim);
+    out->courant_exact = courant_exact(d.ndim);
+    for (int k = 0; k < 6; k++) out->c_damp[k] = d.nb[k] > 0 ? 1.5 * std::log(1.0 / d.R) / d.nb[k] : 0.0;
+    out->cells_per_shot = (long long)out->NZ * out->NY * out->NX;
+    out->tile_x = kTileX2;
+    out->tile_y = 1;
+    out->tile_z = kTileZ2;
+}
+
+sim_status model_checks(const sim_desc &d, double vmin, double vmax, sim_info *info) {
+    if (vmax > 0) {
+        info->courant = vmax * d.dt / d.h;
+        if (info->courant > courant_paper(d.ndim) && !d.skip_cfl_check)
+            return thread_fail(SIM_ERR_CFL, "v_max dt / h = %.4f exceeds the stability bound %.4f",
+                               info->courant, courant_paper(d.ndim));
+    }
+    info->vmin = vmin;
+    info->vmax = vmax;
+    if (vmin > 0 && d.f_max > 0 && d.h > vmin / (4.0 * d.f_max))
+        return thread_fail(SIM_WARN_DISPERSION, "h = %g m exceeds v_min / (4 f_max) = %g m", d.h,
+                           vmin / (4.0 * d.f_max));
+    return SIM_OK;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Interpolation stencil of a point: base cell (padded coordinates) and the
+// fractional offsets; a coordinate within 1e-6 cells of a grid line snaps to it.
+bool locate(const Geom &g, double h, const double *pos, int i0[3], double t[3]) {
+    const int nd = g.ndim;
+    double f[3];
+    f[2] = pos[0] / h + g.ox;
+    f[0] = pos[nd - 1] / h + g.oz;
+    f[1] = nd == 3 ? pos[1] / h + g.oy : 0.0;
+    const int lo[3] = {g.oz, g.oy, g.ox};
+    const int len[3] = {g.nz, g.ny, g.nx};
+    for (int a = 0; a < 3; a++) {
+        const double r = std::nearbyint(f[a]);
+        if (std::fabs(f[a] - r) < 1e-6) f[a] = r;
+        if (!(f[a] >= lo[a]) || !(f[a] <= lo[a] + len[a] - 1)) return false;
+        i0[a] = (int)std::floor(f[a]);
+        t[a] = f[a] - i0[a];
+    }
+    return true;
+}
+
+double corner_weight(const double t[3], int dz, int dy, int dx) {
+    return (dz ? t[0] : 1.0 - t[0]) * (dy ? t[1] : 1.0 - t[1]) * (dx ? t[2] : 1.0 - t[2]);
+}
+
+}  // namespace
+
+// ============================================================== handle
+
+struct sim_s {
+    sim_desc d{};
+    Geom g{};
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    size_t esz = 4;
+    int ntx = 0, nty = 1, ntz = 0;
+    int nsnap = 0;
+    std::vector<void *> allocs;
+    size_t bytes = 0;
+    // device buffers
+    void *pbuf = nullptr, *ch = nullptr, *vpad = nullptr, *vel = nullptr;
+    void *E = nullptr, *ca = nullptr, *cb = nullptr;
+    void *psi[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    void *zeta[3] = {nullptr, nullptr, nullptr};
+    double *part = nullptr;
+    SimIO *io = nullptr;
+    unsigned *flags = nullptr;
+    unsigned *snap_max = nullptr;
+    float *snap_scale = nullptr;
+    void *wave = nullptr, *gath = nullptr, *snaps = nullptr;
+    size_t snaps_bytes = 0;
+    int *rec_start = nullptr;
+    RecEntry *rec = nullptr;
+    int *inj_start = nullptr;
+    InjGroup *inj_grp = nullptr;
+    InjEntry *inj_ent = nullptr;
+    size_t cap_rec = 0, cap_grp = 0, cap_start = 0;
+    unsigned *flags_host = nullptr;  // pinned copy of the device flags
+    bool model_set = false;
+    double vmin = 0, vmax = 0;
+    sim_status sticky = SIM_OK;
+    std::string err;
+
+    sim_status fail(sim_status code, const char *fmt, ...) {
+        va_list ap;
+        va_start(ap, fmt);
+        err = vfmt(fmt, ap);
+        va_end(ap);
+        t_err = err;
+        if (code == SIM_ERR_CUDA || code == SIM_ERR_TIMEOUT || code == SIM_ERR_UNSTABLE) sticky = code;
+        return code;
+    }
+    sim_status cuda(cudaError_t e, const char *what) {
+        if (e == cudaSuccess) return SIM_OK;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? SIM_ERR_OOM : SIM_ERR_CUDA, "%s: %s", what,
+                    cudaGetErrorString(e));
+    }
+    void *alloc(size_t n, sim_status *rc) {
+        void *p = nullptr;
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *rc = fail(SIM_ERR_OOM, "cudaMalloc(%zu bytes) failed: %s", n, cudaGetErrorString(e));
+            return nullptr;
+        }
+        allocs.push_back(p);
+        bytes += n;
+        return p;
+    }
+    template <typename T>
+    T *field(void *base, int shot) const {
+        return static_cast<T *>(base) + (long long)shot * g.fstride;
+    }
+};
+
+namespace {
+
+// Surface device-side flags written by earlier work once the stream is idle.
+sim_status poll_flags(sim_t s, bool wait) {
+    if (s->sticky != SIM_OK) return s->sticky;
+    if (wait) {
+        if (sim_status r = s->cuda(cudaStreamSynchronize(s->st), "stream synchronize")) return r;
+    } else if (cudaStreamQuery(s->st) != cudaSuccess) {
+        cudaGetLastError();
+        return SIM_OK;
+    }
+    const unsigned f = *s->flags_host;
+    if (f & kFlagTimeout) return s->fail(SIM_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (f & kFlagUnstable) return s->fail(SIM_ERR_UNSTABLE, "non-finite values in the wavefield or outputs");
+    return SIM_OK;
+}
+
+template <typename T>
+void host_profiles(const sim_s &s, std::vector<T> &E, std::vector<T> &ca, std::vector<T> &cb) {
+    const sim_desc &d = s.d;
+    const Geom &g = s.g;
+    const int N[3] = {g.NZ, g.NY, g.NX};
+    const int lo[3] = {g.nbz0, g.nby0, g.nbx0}, hi[3] = {g.nbz1, g.nby1, g.nbx1};
+    E.assign(N[0] + N[1] + N[2], T(0));
+    ca.assign(E.size(), T(0));
+    cb.assign(E.size(), T(0));
+    int off = 0;
+    for (int a = 0; a < 3; a++) {
+        for (int i = 0; i < N[a]; i++) {
+            int w = 0;
+            double rho = 0;
+            if (i < lo[a]) {
+                w = lo[a];
+                rho = double(lo[a] - i) / lo[a];
+            } else if (i >= N[a] - hi[a]) {
+                w = hi[a];
+                rho = double(i - (N[a] - hi[a]) + 1) / hi[a];
+            }
+            if (w == 0) continue;
+            if (d.bc == SIM_BC_SPONGE) {
+                // Eq. cerjan_damp in SI (1e-3 s/m: the printed form uses km/s and ms),
+                // stored as eta h^2 / (2 dt) so that a = c_field * E
+                const double cdamp = 1.5 * std::log(1.0 / d.R) / w;
+                const double eta = 1e-3 * (cdamp / d.h) * (rho - std::sin(2 * M_PI * rho) / (2 * M_PI));
+                E[off + i] = T(eta * d.h * d.h / (2.0 * d.dt));
+            } else if (d.bc == SIM_BC_CPML) {
+                const double d0 = 3.0 * s.vmax * std::log(1.0 / d.R) / (2.0 * w * d.h);
+                const double dd = d0 * rho * rho;
+                const double alpha = M_PI * d.f_ref * (1.0 - rho);
+                const double b = std::exp(-(dd + alpha) * d.dt);
+                ca[off + i] = T(dd * (b - 1.0) / (dd + alpha));
+                cb[off + i] = T(b);
+            }
+        }
+        off += N[a];
+    }
+}
+
+template <typename T>
+sim_status set_model_t(sim_t s, const void *vel) {
+    const Geom &g = s->g;
+    const size_t nint = (size_t)g.nz * g.ny * g.nx;
+    const void *src = vel;
+    if (!is_device_ptr(vel)) {
+        if (sim_status r = s->cuda(cudaMemcpyAsync(s->vel, vel, nint * sizeof(T), cudaMemcpyHostToDevice, s->st),
+                                   "velocity upload"))
+            return r;
+        src = s->vel;
+    } else if (vel != s->vel) {
+        if (sim_status r = s->cuda(cudaMemcpyAsync(s->vel, vel, nint * sizeof(T), cudaMemcpyDeviceToDevice, s->st),
+                                   "velocity copy"))
+            return r;
+        src = s->vel;
+    }
+    if (sim_status r = s->cuda(launch_minmax<T>(g, static_cast<const T *>(src), s->part, s->st), "minmax")) return r;
+    std::vector<double> part(3 * kMinmaxBlocks);
+    if (sim_status r = s->cuda(cudaMemcpyAsync(part.data(), s->part, part.size() * sizeof(double),
+                                               cudaMemcpyDeviceToHost, s->st), "minmax readback"))
+        return r;
+    if (sim_status r = s->cuda(cudaStreamSynchronize(s->st), "minmax sync")) return r;
+    double lo = 1e300, hi = -1e300, bad = 0;
+    for (int b = 0; b < kMinmaxBlocks; b++) {
+        lo = std::min(lo, part[3 * b]);
+        hi = std::max(hi, part[3 * b + 1]);
+        bad += part[3 * b + 2];
+    }
+    if (bad > 0) return s->fail(SIM_ERR_ARG, "velocity has %.0f non-finite or non-positive cells", bad);
+    sim_info info{};
+    sim_status chk = model_checks(s->d, lo, hi, &info);
+    if (chk == SIM_ERR_CFL) {
+        s->err = t_err;
+        return chk;
+    }
+    s->vmin = lo;
+    s->vmax = hi;
+    std::vector<T> E, ca, cb;
+    host_profiles<T>(*s, E, ca, cb);
+    const size_t np = E.size() * sizeof(T);
+    if (sim_status r = s->cuda(cudaMemcpyAsync(s->E, E.data(), np, cudaMemcpyHostToDevice, s->st), "profiles")) return r;
+    if (sim_status r = s->cuda(cudaMemcpyAsync(s->ca, ca.data(), np, cudaMemcpyHostToDevice, s->st), "profiles")) return r;
+    if (sim_status r = s->cuda(cudaMemcpyAsync(s->cb, cb.data(), np, cudaMemcpyHostToDevice, s->st), "profiles")) return r;
+    if (sim_status r = s->cuda(launch_setup_model<T>(g, static_cast<const T *>(src), static_cast<T *>(s->ch),
+                                                     static_cast<T *>(s->vpad), s->d.dt / s->d.h, s->st),
+                               "model set-up"))
+        return r;
+    if (sim_status r = s->cuda(cudaStreamSynchronize(s->st), "model set-up sync")) return r;
+    s->model_set = true;
+    if (chk == SIM_WARN_DISPERSION) s->err = t_err;
+    return chk;
+}
+
+// Receivers: one entry per receiver, in the list of the tile that holds its
+// base cell; the stencil corners lie within that tile's radius-4 halo.
+sim_status build_receivers(sim_t s, int nrec, const double *rec_pos, std::vector<int> &start,
+                           std::vector<RecEntry> &ent) {
+    const Geom &g = s->g;
+    const int ntiles = s->ntx * s->nty * s->ntz;
+    std::vector<std::pair<int, RecEntry>> tmp;
+    tmp.reserve(nrec);
+    for (int r = 0; r < nrec; r++) {
+        int i0[3];
+        double t[3];
+        if (!locate(g, s->d.h, rec_pos + (size_t)r * g.ndim, i0, t))
+            return s->fail(SIM_ERR_ARG, "receiver %d lies outside the interior", r);
+        RecEntry e{};
+        e.rec = r;
+        const int tz = i0[0] / kTileZ2, tx = i0[2] / kTileX2;
+        e.lz = i0[0] - tz * kTileZ2;
+        e.ly = 0;
+        e.lx = i0[2] - tx * kTileX2;
+        int k = 0;
+        for (int dz = 0; dz < 2; dz++)
+            for (int dy = 0; dy < (g.ndim == 3 ? 2 : 1); dy++)
+                for (int dx = 0; dx < 2; dx++) e.w[k++] = corner_weight(t, dz, dy, dx);
+        tmp.push_back({tz * s->ntx + tx, e});
+    }
+    std::stable_sort(tmp.begin(), tmp.end(), [](const auto &a, const auto &b) { return a.first < b.first; });
+    start.assign(ntiles + 1, 0);
+    ent.clear();
+    for (auto &p : tmp) {
+        start[p.first + 1]++;
+        ent.push_back(p.second);
+    }
+    for (int i = 0; i < ntiles; i++) start[i + 1] += start[i];
+    return SIM_OK;
+}
+
+struct InjPoint {
+    int tile;   // list index (global tile)
+    int cell;   // local linear index
+    int pt;
+    double w;
+};
+
+// Point injection: every stencil corner with a non-zero weight is a target
+// cell of the tile that owns it (none on a free-surface row, which is held at
+// zero). Targets are grouped per cell so one thread sums each cell in order.
+void group_injection(std::vector<InjPoint> &pts, int nlists, std::vector<int> &start,
+                     std::vector<InjGroup> &grp, std::vector<InjEntry> &ent) {
+    std::stable_sort(pts.begin(), pts.end(), [](const InjPoint &a, const InjPoint &b) {
+        return a.tile != b.tile ? a.tile < b.tile : a.cell < b.cell;
+    });
+    start.assign(nlists + 1, 0);
+    grp.clear();
+    ent.clear();
+    for (size_t i = 0; i < pts.size();) {
+        size_t j = i;
+        InjGroup G{};
+        G.cell = pts[i].cell;
+        G.e0 = (int)ent.size();
+        while (j < pts.size() && pts[j].tile == pts[i].tile && pts[j].cell == pts[i].cell) {
+            InjEntry e{};
+            e.pt = pts[j].pt;
+            e.w = pts[j].w;
+            ent.push_back(e);
+            j++;
+        }
+        G.e1 = (int)ent.size();
+        grp.push_back(G);
+        start[pts[i].tile + 1]++;
+        i = j;
+    }
+    for (int i = 0; i < nlists; i++) start[i + 1] += start[i];
+}
+
+sim_status collect_points(sim_t s, int npts, const double *pos, bool per_shot, std::vector<InjPoint> &out,
+                          const char *what) {
+    const Geom &g = s->g;
+    const int ntiles = s->ntx * s->nty * s->ntz;
+    for (int q = 0; q < npts; q++) {
+        int i0[3];
+        double t[3];
+        if (!locate(g, s->d.h, pos + (size_t)q * g.ndim, i0, t))
+            return s->fail(SIM_ERR_ARG, "%s %d lies outside the interior", what, q);
+        for (int dz = 0; dz < 2; dz++)
+            for (int dy = 0; dy < (g.ndim == 3 ? 2 : 1); dy++)
+                for (int dx = 0; dx < 2; dx++) {
+                    const double w = corner_weight(t, dz, dy, dx);
+                    if (w == 0.0) continue;
+                    const int z = i0[0] + dz, x = i0[2] + dx;
+                    if (g.fs && z == 0) continue;
+                    const int tz = z / kTileZ2, tx = x / kTileX2;
+                    InjPoint p;
+                    p.tile = (per_shot ? q * ntiles : 0) + tz * s->ntx + tx;
+                    p.cell = (z - tz * kTileZ2) * kTileX2 + (x - tx * kTileX2);
+                    p.pt = q;
+                    p.w = w;
+                    out.push_back(p);
+                }
+    }
+    return SIM_OK;
+}
+
+template <typename V>
+sim_status upload(sim_t s, V *dst, const std::vector<V> &src, size_t cap, const char *what) {
+    if (src.size() > cap) return s->fail(SIM_ERR_ARG, "%s list exceeds its capacity", what);
+    if (src.empty()) return SIM_OK;
+    return s->cuda(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice, s->st), what);
+}
+
+template <typename T>
+StepArgs<T> step_args(sim_t s) {
+    StepArgs<T> a{};
+    a.g = s->g;
+    a.pbuf[0] = static_cast<T *>(s->pbuf);
+    a.pbuf[1] = static_cast<T *>(s->pbuf) + (long long)s->d.max_shots * s->g.fstride;
+    a.ch = static_cast<const T *>(s->ch);
+    const int N[3] = {s->g.NZ, s->g.NY, s->g.NX};
+    int off = 0;
+    for (int ax = 0; ax < 3; ax++) {
+        a.E[ax] = s->d.bc == SIM_BC_SPONGE ? static_cast<const T *>(s->E) + off : nullptr;
+        const bool on = s->d.bc == SIM_BC_CPML && s->psi[ax][0] != nullptr;
+        a.ca[ax] = on ? static_cast<const T *>(s->ca) + off : nullptr;
+        a.cb[ax] = on ? static_cast<const T *>(s->cb) + off : nullptr;
+        a.psi[ax][0] = static_cast<T *>(s->psi[ax][0]);
+        a.psi[ax][1] = static_cast<T *>(s->psi[ax][1]);
+        a.zeta[ax] = static_cast<T *>(s->zeta[ax]);
+        off += N[ax];
+    }
+    a.bc = s->d.bc;
+    a.src_scale = T(s->g.ndim == 3 ? 1.0 / s->d.h : 1.0);
+    a.ntx = s->ntx;
+    a.nty = s->nty;
+    a.ntz = s->ntz;
+    a.nt = s->d.nt;
+    a.nsnap = s->nsnap;
+    a.snap_every = s->d.snap_every > 0 ? s->d.snap_every : 1;
+    a.snap_begin = s->d.snap_begin;
+    a.snap_end = std::min(s->d.snap_end, s->d.nt);
+    a.rec_start = s->rec_start;
+    a.rec = s->rec;
+    a.inj_start = s->inj_start;
+    a.inj_grp = s->inj_grp;
+    a.inj_ent = s->inj_ent;
+    a.io = s->io;
+    a.flags = s->flags;
+    return a;
+}
+
+// Zero the per-run state of `nshots` shots: both pressure buffers, the CPML
+// memory and the FP16 snapshot maxima.
+sim_status reset_state(sim_t s, int nshots) {
+    const size_t fb = (size_t)s->g.fstride * s->esz * nshots;
+    const size_t half = (size_t)s->g.fstride * s->esz * s->d.max_shots;
+    if (sim_status r = s->cuda(cudaMemsetAsync(s->pbuf, 0, fb, s->st), "reset")) return r;
+    if (sim_status r = s->cuda(cudaMemsetAsync(static_cast<char *>(s->pbuf) + half, 0, fb, s->st), "reset")) return r;
+    for (int ax = 0; ax < 3; ax++) {
+        for (int k = 0; k < 2; k++)
+            if (s->psi[ax][k])
+                if (sim_status r = s->cuda(cudaMemsetAsync(s->psi[ax][k], 0, fb, s->st), "reset")) return r;
+        if (s->zeta[ax])
+            if (sim_status r = s->cuda(cudaMemsetAsync(s->zeta[ax], 0, fb, s->st), "reset")) return r;
+    }
+    if (s->nsnap > 0)
+        if (sim_status r = s->cuda(cudaMemsetAsync(s->snap_max, 0, sizeof(unsigned) * s->nsnap * nshots, s->st),
+                                   "reset"))
+            return r;
+    return SIM_OK;
+}
+
+template <typename T>
+sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src_pos, int nrec,
+                     const double *rec_pos, void *gather, void *snaps, float *snap_scale) {
+    const sim_desc &d = s->d;
+    const Geom &g = s->g;
+    if (g.ndim != 2) return s->fail(SIM_ERR_UNSUPPORTED, "3D forward is not built yet");
+    const size_t nt = d.nt;
+    // inputs
+    const void *wav = wavelet;
+    if (wavelet && !is_device_ptr(wavelet)) {
+        if (sim_status r = s->cuda(cudaMemcpyAsync(s->wave, wavelet, nt * sizeof(T), cudaMemcpyHostToDevice, s->st),
+                                   "wavelet upload"))
+            return r;
+        wav = s->wave;
+    }
+    // outputs
+    const bool g_host = gather && !is_device_ptr(gather);
+    void *gdev = g_host ? s->gath : gather;
+    const size_t gbytes = (size_t)nshots * nt * nrec * sizeof(T);
+    const bool sn_host = snaps && s->nsnap > 0 && !is_device_ptr(snaps);
+    const size_t sesz = d.snap_fp16 ? 2 : sizeof(T);
+    const size_t sbytes = (size_t)nshots * s->nsnap * g.nz * g.ny * g.nx * sesz;
+    void *sdev = snaps;
+    if (sn_host) {
+        if (s->snaps_bytes < sbytes) {
+            sim_status rc = SIM_OK;
+            s->snaps = s->alloc(sbytes, &rc);
+            if (!s->snaps) return rc;
+            s->snaps_bytes = sbytes;
+        }
+        sdev = s->snaps;
+    }
+    const bool sc_host = snap_scale && !is_device_ptr(snap_scale);
+    float *scdev = sc_host ? s->snap_scale : snap_scale;
+    if (d.snap_fp16 && snaps && s->nsnap > 0 && !snap_scale)
+        return s->fail(SIM_ERR_ARG, "FP16 snapshots need a snap_scale array");
+
+    // geometry lists
+    std::vector<int> rstart, istart;
+    std::vector<RecEntry> rent;
+    std::vector<InjGroup> igrp;
+    std::vector<InjEntry> ient;
+    if (sim_status r = build_receivers(s, nrec, rec_pos, rstart, rent)) return r;
+    std::vector<InjPoint> pts;
+    if (wavelet)
+        if (sim_status r = collect_points(s, nshots, src_pos, true, pts, "source")) return r;
+    const int ntiles = s->ntx * s->nty * s->ntz;
+    group_injection(pts, nshots * ntiles, istart, igrp, ient);
+    if (sim_status r = upload(s, s->rec_start, rstart, s->cap_start, "receiver start")) return r;
+    if (sim_status r = upload(s, s->rec, rent, s->cap_rec, "receiver")) return r;
+    if (sim_status r = upload(s, s->inj_start, istart, s->cap_start, "injection start")) return r;
+    if (sim_status r = upload(s, s->inj_grp, igrp, s->cap_grp, "injection group")) return r;
+    if (sim_status r = upload(s, s->inj_ent, ient, s->cap_grp, "injection entry")) return r;
+
+    SimIO io{};
+    io.wavelet = wav;
+    io.gather = nrec > 0 ? gdev : nullptr;
+    io.snaps = s->nsnap > 0 ? sdev : nullptr;
+    io.snap_scale = scdev;
+    io.snap_max = s->snap_max;
+    io.nrec = nrec;
+    io.nshots = nshots;
+    io.snap_fp16 = d.snap_fp16;
+    if (sim_status r = s->cuda(cudaMemcpyAsync(s->io, &io, sizeof io, cudaMemcpyHostToDevice, s->st), "io upload"))
+        return r;
+    if (sim_status r = reset_state(s, nshots)) return r;
+
+    StepArgs<T> a = step_args<T>(s);
+    a.inj_per_shot = 1;
+    a.inj_kind = 0;
+    for (int n = 0; n < d.nt; n++)
+        if (sim_status r = s->cuda(launch_step2d<T>(a, n, nshots, s->st), "step kernel")) return r;
+    // the buffer written last holds p^nt
+    if (sim_status r = s->cuda(launch_check_finite<T>(g, static_cast<const T *>(a.pbuf[d.nt & 1]), nshots, s->flags,
+                                                      s->st), "finite check"))
+        return r;
+    if (sim_status r = s->cuda(cudaMemcpyAsync(s->flags_host, s->flags, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                               s->st), "flag readback"))
+        return r;
+    bool wait = false;
+    if (g_host && nrec > 0) {
+        if (sim_status r = s->cuda(cudaMemcpyAsync(gather, gdev, gbytes, cudaMemcpyDeviceToHost, s->st), "gather"))
+            return r;
+        wait = true;
+    }
+    if (sn_host) {
+        if (sim_status r = s->cuda(cudaMemcpyAsync(snaps, sdev, sbytes, cudaMemcpyDeviceToHost, s->st), "snapshots"))
+            return r;
+        wait = true;
+    }
+    if (sc_host && d.snap_fp16 && s->nsnap > 0) {
+        if (sim_status r = s->cuda(cudaMemcpyAsync(snap_scale, scdev, sizeof(float) * nshots * s->nsnap,
+                                                   cudaMemcpyDeviceToHost, s->st), "scales"))
+            return r;
+        wait = true;
+    }
+    if (wait) return poll_flags(s, true);
+    return SIM_OK;
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+
+extern "C" {
+
+void sim_desc_init(sim_desc *d) {
+    if (!d) return;
+    memset(d, 0, sizeof(*d));
+    d->space_order = 8;
+    d->R = 1e-3;
+    d->f_ref = 10.0;
+    d->max_shots = 1;
+    d->precision = SIM_FP32;
+}
+
+sim_status sim_plan(const sim_desc *din, double vmin, double vmax, sim_info *out) {
+    if (!din || !out) return thread_fail(SIM_ERR_ARG, "NULL argument");
+    sim_desc d = *din;
+    normalise(d);
+    if (sim_status r = validate(d)) return r;
+    fill_info(d, out);
+    return model_checks(d, vmin, vmax, out);
+}
+
+sim_status sim_create(const sim_desc *din, const void *vel, void *cuda_stream, sim_t *out) {
+    if (!din || !out) return thread_fail(SIM_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    sim_desc d = *din;
+    normalise(d);
+    if (sim_status r = validate(d)) return r;
+    sim_s *s = new (std::nothrow) sim_s();
+    if (!s) return thread_fail(SIM_ERR_OOM, "host allocation failed");
+    s->d = d;
+    s->g = make_geom(d);
+    s->st = static_cast<cudaStream_t>(cuda_stream);
+    s->esz = d.precision == SIM_FP64 ? 8 : 4;
+    s->nsnap = nsnap_of(d);
+    s->ntx = (s->g.NX + kTileX2 - 1) / kTileX2;
+    s->ntz = (s->g.NZ + kTileZ2 - 1) / kTileZ2;
+    s->nty = 1;
+    sim_status rc = SIM_OK;
+    if (cudaGetDevice(&s->dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return thread_fail(SIM_ERR_CUDA, "no CUDA device available");
+    }
+    const Geom &g = s->g;
+    const size_t fb = (size_t)g.fstride * s->esz;
+    const int ms = d.max_shots;
+    const size_t nint = (size_t)g.nz * g.ny * g.nx;
+    const size_t nprof = (size_t)g.NZ + g.NY + g.NX;
+    const int ntiles = s->ntx * s->nty * s->ntz;
+    auto A = [&](size_t n) { return rc == SIM_OK ? s->alloc(n, &rc) : nullptr; };
+    s->pbuf = A(2 * fb * ms);
+    s->ch = A(fb);
+    s->vpad = A(fb);
+    s->vel = A(nint * s->esz);
+    s->E = A(nprof * s->esz);
+    s->ca = A(nprof * s->esz);
+    s->cb = A(nprof * s->esz);
+    if (d.bc == SIM_BC_CPML) {
+        const int nbz = d.nb[0] + d.nb[1], nby = d.ndim == 3 ? d.nb[2] + d.nb[3] : 0, nbx = d.nb[4] + d.nb[5];
+        const int on[3] = {nbz > 0, nby > 0, nbx > 0};
+        for (int ax = 0; ax < 3; ax++)
+            if (on[ax]) {
+                s->psi[ax][0] = A(fb * ms);
+                s->psi[ax][1] = A(fb * ms);
+                s->zeta[ax] = A(fb * ms);
+            }
+    }
+    s->part = static_cast<double *>(A(3 * kMinmaxBlocks * sizeof(double)));
+    s->io = static_cast<SimIO *>(A(sizeof(SimIO)));
+    s->flags = static_cast<unsigned *>(A(sizeof(unsigned)));
+    s->snap_max = static_cast<unsigned *>(A(sizeof(unsigned) * std::max(1, s->nsnap * ms)));
+    s->snap_scale = static_cast<float *>(A(sizeof(float) * std::max(1, s->nsnap * ms)));
+    s->wave = A((size_t)d.nt * s->esz);
+    s->gath = A((size_t)ms * d.nt * std::max(1, d.max_rec) * s->esz);
+    s->cap_start = (size_t)ms * ntiles + 1;
+    s->cap_rec = std::max(1, d.max_rec);
+    s->cap_grp = 8 * (size_t)std::max(ms, std::max(1, d.max_rec));
+    s->rec_start = static_cast<int *>(A(s->cap_start * sizeof(int)));
+    s->rec = static_cast<RecEntry *>(A(s->cap_rec * sizeof(RecEntry)));
+    s->inj_start = static_cast<int *>(A(s->cap_start * sizeof(int)));
+    s->inj_grp = static_cast<InjGroup *>(A(s->cap_grp * sizeof(InjGroup)));
+    s->inj_ent = static_cast<InjEntry *>(A(s->cap_grp * sizeof(InjEntry)));
+    if (rc == SIM_OK && cudaMallocHost(&s->flags_host, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        rc = s->fail(SIM_ERR_OOM, "pinned host allocation failed");
+    }
+    if (rc == SIM_OK) {
+        *s->flags_host = 0;
+        // ghost cells of every field must read as zero, forever
+        for (void *p : {s->pbuf, s->ch, s->vpad})
+            if (rc == SIM_OK)
+                rc = s->cuda(cudaMemsetAsync(p, 0, p == s->pbuf ? 2 * fb * ms : fb, s->st), "initial clear");
+        if (rc == SIM_OK) rc = s->cuda(cudaMemsetAsync(s->flags, 0, sizeof(unsigned), s->st), "initial clear");
+        if (rc == SIM_OK) rc = s->cuda(cudaStreamSynchronize(s->st), "create sync");
+    }
+    if (rc != SIM_OK) {
+        t_err = s->err;
+        sim_destroy(s);
+        return rc;
+    }
+    if (vel) {
+        rc = sim_set_model(s, vel);
+        if (rc != SIM_OK && rc != SIM_WARN_DISPERSION) {
+            t_err = s->err;
+            sim_destroy(s);
+            return rc;
+        }
+    }
+    *out = s;
+    return rc;
+}
+
+sim_status sim_set_model(sim_t s, const void *vel) {
+    if (!s || !vel) return thread_fail(SIM_ERR_ARG, "NULL argument");
+    if (s->sticky) return s->sticky;
+    cudaSetDevice(s->dev);
+    return s->d.precision == SIM_FP64 ? set_model_t<double>(s, vel) : set_model_t<float>(s, vel);
+}
+
+sim_status sim_forward(sim_t s, int nshots, const void *wavelet, const double *src_pos, int nrec,
+                       const double *rec_pos, void *gather, void *snaps, float *snap_scale) {
+    if (!s) return thread_fail(SIM_ERR_ARG, "NULL handle");
+    if (sim_status r = poll_flags(s, false)) return r;
+    if (!s->model_set) return s->fail(SIM_ERR_STATE, "no velocity model set");
+    if (nshots < 1 || nshots > s->d.max_shots)
+        return s->fail(SIM_ERR_ARG, "nshots = %d outside [1, %d]", nshots, s->d.max_shots);
+    if (nrec < 0 || nrec > s->d.max_rec) return s->fail(SIM_ERR_ARG, "nrec = %d outside [0, %d]", nrec, s->d.max_rec);
+    if (nrec > 0 && !rec_pos) return s->fail(SIM_ERR_ARG, "receivers need positions");
+    if (wavelet && !src_pos) return s->fail(SIM_ERR_ARG, "a wavelet needs source positions");
+    cudaSetDevice(s->dev);
+    return s->d.precision == SIM_FP64
+               ? forward_t<double>(s, nshots, wavelet, src_pos, nrec, rec_pos, gather, snaps, snap_scale)
+               : forward_t<float>(s, nshots, wavelet, src_pos, nrec, rec_pos, gather, snaps, snap_scale);
+}
+
+sim_status sim_adjoint(sim_t s, int, const void *, const double *, int, const double *, const void *, void *,
+                       double *, int, void *) {
+    if (!s) return thread_fail(SIM_ERR_ARG, "NULL handle");
+    return s->fail(SIM_ERR_UNSUPPORTED, "adjoint not built yet");
+}
+
+sim_status sim_batch(int, const sim_batch_item *, void *) {
+    return thread_fail(SIM_ERR_UNSUPPORTED, "batch not built yet");
+}
+
+sim_status sim_sync(sim_t s) {
+    if (!s) return thread_fail(SIM_ERR_ARG, "NULL handle");
+    cudaSetDevice(s->dev);
+    return poll_flags(s, true);
+}
+
+sim_status sim_get_info(sim_t s, sim_info *out) {
+    if (!s || !out) return thread_fail(SIM_ERR_ARG, "NULL argument");
+    fill_info(s->d, out);
+    out->vmin = s->vmin;
+    out->vmax = s->vmax;
+    out->courant = s->vmax * s->d.dt / s->d.h;
+    out->device_bytes = s->bytes;
+    return SIM_OK;
+}
+
+const char *sim_last_error(sim_t s) {
+    if (s) return s->err.c_str();
+    return t_err.c_str();
+}
+
+void sim_destroy(sim_t s) {
+    if (!s) return;
+    cudaSetDevice(s->dev);
+    cudaStreamSynchronize(s->st);
+    for (void *p : s->allocs) cudaFree(p);
+    if (s->flags_host) cudaFreeHost(s->flags_host);
+    cudaGetLastError();
+    delete s;
+}
+
+}  // extern "C"
