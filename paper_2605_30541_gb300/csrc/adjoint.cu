@@ -1,0 +1,171 @@
+// Support kernels of the adjoint-state gradient: checkpoint store/restore
+// (FP32/FP64 copy or FP16 with a power-of-two scale per tile), the data
+// residual with its misfit, and the final FP64 fold of the per-shot imaging
+// sums onto the interior velocity cells (absorbing cells replicate the
+// nearest interior cell, so their contributions land on the edge cells).
+#include <cfloat>
+
+#include "sim_internal.h"
+#include "stencil.cuh"
+
+namespace gsim {
+namespace {
+
+constexpr int TX = kTileX2, TZ = kTileZ2, BX = 32, BY = 8, RZ = TZ / BY, NTH = BX * BY;
+
+__device__ __forceinline__ float tile_max(float v, float *red) {
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    v = warp_max(v);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    float m = tid < NTH / 32 ? red[tid & 31] : 0.f;
+    if (tid < 32) m = warp_max(m);
+    __syncthreads();
+    if (tid == 0) red[0] = m;
+    __syncthreads();
+    return red[0];
+}
+
+// One CTA per (tile, shot); the compact copy of a state is [shot][NZ * NX].
+template <typename T>
+__global__ void __launch_bounds__(NTH) k_store(const Geom g, const T *__restrict__ field, void *dst, float *scale,
+                                               int fp16, long long sstride, int ntx) {
+    __shared__ float red[NTH / 32];
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ, shot = blockIdx.z;
+    const int tile = blockIdx.y * ntx + blockIdx.x, ntiles = ntx * gridDim.y;
+    const T *f = field + (long long)shot * g.fstride;
+    T v[RZ];
+    float m = 0.f;
+#pragma unroll
+    for (int k = 0; k < RZ; k++) {
+        const int gz = z0 + threadIdx.y + k * BY, gx = x0 + threadIdx.x;
+        v[k] = (gz < g.NZ && gx < g.NX) ? f[cell_off(g, gz, 0, gx)] : T(0);
+        m = fmaxf(m, fabsf((float)v[k]));
+    }
+    float inv = 1.f;
+    if (fp16) {
+        const float s = pow2_scale(tile_max(m, red));
+        inv = 1.f / s;
+        if (threadIdx.x == 0 && threadIdx.y == 0) scale[(long long)shot * ntiles + tile] = s;
+    }
+#pragma unroll
+    for (int k = 0; k < RZ; k++) {
+        const int gz = z0 + threadIdx.y + k * BY, gx = x0 + threadIdx.x;
+        if (gz >= g.NZ || gx >= g.NX) continue;
+        const long long ci = shot * sstride + (long long)gz * g.NX + gx;
+        if (fp16) static_cast<__half *>(dst)[ci] = __float2half_rn((float)v[k] * inv);
+        else static_cast<T *>(dst)[ci] = v[k];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTH) k_load(const Geom g, T *field, const void *src, const float *scale, int fp16,
+                                              long long sstride, int ntx) {
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ, shot = blockIdx.z;
+    const int tile = blockIdx.y * ntx + blockIdx.x, ntiles = ntx * gridDim.y;
+    T *f = field + (long long)shot * g.fstride;
+    const float s = fp16 ? scale[(long long)shot * ntiles + tile] : 1.f;
+#pragma unroll
+    for (int k = 0; k < RZ; k++) {
+        const int gz = z0 + threadIdx.y + k * BY, gx = x0 + threadIdx.x;
+        if (gz >= g.NZ || gx >= g.NX) continue;
+        const long long ci = shot * sstride + (long long)gz * g.NX + gx;
+        f[cell_off(g, gz, 0, gx)] =
+            fp16 ? T(__half2float(static_cast<const __half *>(src)[ci]) * s) : static_cast<const T *>(src)[ci];
+    }
+}
+
+template <typename T>
+__global__ void k_residual(const T *__restrict__ gath, const T *__restrict__ d, T *res, long long n, double *part) {
+    __shared__ double sm[256];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const T r = gath[i] - d[i];
+        res[i] = r;
+        acc += 0.5 * (double)r * (double)r;
+    }
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+// Interior cell i gathers every computational cell whose velocity copies it:
+// itself, plus the absorbing cells beyond it when it sits on an edge.
+template <typename T>
+__global__ void k_fold(const Geom g, const T *__restrict__ G, long long gshot, int nshots,
+                       const T *__restrict__ vpad, double inv_h2, double *acc) {
+    const long long nint = (long long)g.nz * g.nx;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nint; i += (long long)gridDim.x * blockDim.x) {
+        const int iz = (int)(i / g.nx), ix = (int)(i % g.nx);
+        const int za = iz == 0 ? 0 : iz + g.oz, zb = iz == g.nz - 1 ? g.NZ : iz + g.oz + 1;
+        const int xa = ix == 0 ? 0 : ix + g.ox, xb = ix == g.nx - 1 ? g.NX : ix + g.ox + 1;
+        double sum = 0.0;
+        for (int s = 0; s < nshots; s++)
+            for (int z = za; z < zb; z++)
+                for (int x = xa; x < xb; x++) {
+                    const double v = (double)vpad[cell_off(g, z, 0, x)];
+                    sum += -2.0 * inv_h2 / v * (double)G[s * gshot + cell_off(g, z, 0, x)];
+                }
+        acc[i] += sum;
+    }
+}
+
+template <typename T>
+__global__ void k_add(const double *__restrict__ acc, T *grad, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        grad[i] += (T)acc[i];
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_store_state(const Geom &g, const T *field, void *dst, float *scale, int fp16, int nshots,
+                               long long shot_stride, int ntx, int ntz, cudaStream_t st) {
+    k_store<T><<<dim3(ntx, ntz, nshots), dim3(BX, BY), 0, st>>>(g, field, dst, scale, fp16, shot_stride, ntx);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_load_state(const Geom &g, T *field, const void *src, const float *scale, int fp16, int nshots,
+                              long long shot_stride, int ntx, int ntz, cudaStream_t st) {
+    k_load<T><<<dim3(ntx, ntz, nshots), dim3(BX, BY), 0, st>>>(g, field, src, scale, fp16, shot_stride, ntx);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_residual(const T *g, const T *d, T *res, long long n, double *part, int nblocks, cudaStream_t st) {
+    k_residual<T><<<nblocks, 256, 0, st>>>(g, d, res, n, part);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fold_gradient(const Geom &g, const T *G, long long gshot, int nshots, const T *vpad,
+                                 double inv_h2, double *acc, cudaStream_t st) {
+    k_fold<T><<<1216, 256, 0, st>>>(g, G, gshot, nshots, vpad, inv_h2, acc);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_add_gradient(const double *acc, T *grad, long long n, cudaStream_t st) {
+    k_add<T><<<1216, 256, 0, st>>>(acc, grad, n);
+    return cudaGetLastError();
+}
+
+#define INST(T)                                                                                               \
+    template cudaError_t launch_store_state<T>(const Geom &, const T *, void *, float *, int, int, long long,  \
+                                               int, int, cudaStream_t);                                       \
+    template cudaError_t launch_load_state<T>(const Geom &, T *, const void *, const float *, int, int,        \
+                                              long long, int, int, cudaStream_t);                             \
+    template cudaError_t launch_residual<T>(const T *, const T *, T *, long long, double *, int, cudaStream_t); \
+    template cudaError_t launch_fold_gradient<T>(const Geom &, const T *, long long, int, const T *,      \
+                                                 double, double *, cudaStream_t);                             \
+    template cudaError_t launch_add_gradient<T>(const double *, T *, long long, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace gsim

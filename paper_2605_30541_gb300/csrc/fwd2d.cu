@@ -9,6 +9,11 @@
 // +-4 cells) in shared memory; a thread updates two cells of one column.
 // Tiles are classified per CTA (interior / sponge / CPML / surface) so that
 // interior tiles run the plain update with no boundary arithmetic.
+//
+// The same kernel serves the adjoint-state gradient: with u = c lambda the
+// discrete adjoint recursion has the forward update's form, driven by the
+// data residual injected at the receivers (MODE kModeAdjoint), and the
+// forward recompute records the per-cell imaging term (MODE kModeRecord).
 #include <cfloat>
 
 #include "sim_internal.h"
@@ -20,7 +25,20 @@ namespace {
 constexpr int TX = kTileX2, TZ = kTileZ2, HM = 8;
 constexpr int BX = 32, BY = 8, RZ = TZ / BY, NTH = BX * BY;
 
-template <typename T>
+__device__ __forceinline__ float block_max(float v, float *red) {
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    v = warp_max(v);
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    float m = tid < NTH / 32 ? red[tid & 31] : 0.f;
+    if (tid < 32) m = warp_max(m);
+    if (tid == 0) red[0] = m;
+    __syncthreads();
+    return red[0];
+}
+
+template <typename T, int MODE>
 __global__ void __launch_bounds__(NTH) k_step2d(const StepArgs<T> A, const int n) {
     __shared__ T S[TZ + 2 * HM][TX + 2 * HM];
     __shared__ T PX[TZ][TX + 8];
@@ -106,16 +124,17 @@ __global__ void __launch_bounds__(NTH) k_step2d(const StepArgs<T> A, const int n
         for (int i = tid; i < TZ * TX; i += NTH) (&INJ[0][0])[i] = T(0);
         __syncthreads();
         const SimIO *io = A.io;
+        const int row = A.inj_reverse ? A.nt - n : n;
         for (int gi = g0 + tid; gi < g1; gi += NTH) {
             const InjGroup G = A.inj_grp[gi];
             T sum = T(0);
             for (int e = G.e0; e < G.e1; e++) {
-                const InjEntry E = A.inj_ent[e];
-                T val;
+                const InjEntryT<T> E = A.inj_ent[e];
+                T val = T(0);
                 if (A.inj_kind == 0)
-                    val = static_cast<const T *>(io->wavelet)[n];
-                else
-                    val = static_cast<const T *>(io->resid)[((long long)shot * A.nt + n) * io->nrec + E.pt];
+                    val = static_cast<const T *>(io->wavelet)[row];
+                else if (row < A.nt)
+                    val = static_cast<const T *>(io->resid)[((long long)shot * A.nt + row) * io->nrec + E.pt];
                 sum += T(E.w) * val;
             }
             (&INJ[0][0])[G.cell] = sum;
@@ -124,7 +143,7 @@ __global__ void __launch_bounds__(NTH) k_step2d(const StepArgs<T> A, const int n
     __syncthreads();
 
     // ---- receivers sample p^n
-    {
+    if (A.sample) {
         const int r0 = A.rec_start[tile], r1 = A.rec_start[tile + 1];
         if (r1 > r0) {
             const SimIO *io = A.io;
@@ -132,7 +151,7 @@ __global__ void __launch_bounds__(NTH) k_step2d(const StepArgs<T> A, const int n
             if (gout) {
                 const long long row = ((long long)shot * A.nt + n) * io->nrec;
                 for (int e = r0 + tid; e < r1; e += NTH) {
-                    const RecEntry R = A.rec[e];
+                    const RecEntryT<T> R = A.rec[e];
                     const T *b = &S[HM + R.lz][HM + R.lx];
                     const T val = T(R.w[0]) * b[0] + T(R.w[1]) * b[1] +
                                   T(R.w[2]) * b[TX + 2 * HM] + T(R.w[3]) * b[TX + 2 * HM + 1];
@@ -144,10 +163,10 @@ __global__ void __launch_bounds__(NTH) k_step2d(const StepArgs<T> A, const int n
     }
 
     // ---- snapshot bookkeeping
-    const bool snap_now = A.nsnap > 0 && n >= A.snap_begin && n < A.snap_end &&
+    const bool snap_now = MODE == kModeForward && A.nsnap > 0 && n >= A.snap_begin && n < A.snap_end &&
                           (n - A.snap_begin) % A.snap_every == 0;
     const int n1 = n + 1;
-    const bool max_next = A.nsnap > 0 && n1 >= A.snap_begin && n1 < A.snap_end &&
+    const bool max_next = MODE == kModeForward && A.nsnap > 0 && n1 >= A.snap_begin && n1 < A.snap_end &&
                           (n1 - A.snap_begin) % A.snap_every == 0;
     void *snaps = nullptr;
     int fp16 = 0;
@@ -169,10 +188,17 @@ __global__ void __launch_bounds__(NTH) k_step2d(const StepArgs<T> A, const int n
         }
     }
 
+    // ---- adjoint sweep: imaging term of this step, recorded by the recompute
+    const int ntiles = A.ntx * A.ntz;
+    float qs = 1.f;
+    if (MODE == kModeAdjoint && A.q_fp16) qs = A.qscale[shot * ntiles + tile];
+
     // ---- update
     float tmax = 0.f;
+    T qv[RZ];
 #pragma unroll
     for (int k = 0; k < RZ; k++) {
+        qv[k] = T(0);
         const int lz = ty + k * BY, lx = tx;
         const int gz = z0 + lz, gx = x0 + lx;
         if (gz >= g.NZ || gx >= g.NX) continue;
@@ -199,17 +225,31 @@ __global__ void __launch_bounds__(NTH) k_step2d(const StepArgs<T> A, const int n
         if (has_inj) rhs += A.src_scale * INJ[lz][lx];
         const T chv = A.ch[o];
         const T pp = pnx[o];
-        T out;
+        T out, esum = T(0);
         if (spg) {
-            const T a = chv * (A.E[0][gz] + A.E[2][gx]);
+            esum = A.E[0][gz] + A.E[2][gx];
+            const T a = chv * esum;
             out = (T(2) * p - (T(1) - a) * pp + chv * rhs) / (T(1) + a);
         } else {
             out = T(2) * p - pp + chv * rhs;
         }
         if (g.fs && gz == 0) out = T(0);
         pnx[o] = out;
+        const long long ci = sh + o;  // imaging slots and G share the field layout
+        if (MODE == kModeRecord) {
+            qv[k] = esum * (out - pp) - rhs;
+            if (A.q_fp16) tmax = fmaxf(tmax, fabsf((float)qv[k]));
+            else static_cast<T *>(A.qslot)[ci] = qv[k];
+        }
+        if (MODE == kModeAdjoint) {
+            T q;
+            if (A.q_fp16) q = T(__half2float(static_cast<const __half *>(A.qslot)[ci]) * qs);
+            else q = static_cast<const T *>(A.qslot)[ci];
+            T *gp = A.G + ci;
+            *gp += out * q;
+        }
         const bool inside = gz >= g.oz && gz < g.oz + g.nz && gx >= g.ox && gx < g.ox + g.nx;
-        if (max_next && inside) tmax = fmaxf(tmax, fabsf((float)out));
+        if (MODE == kModeForward && max_next && inside) tmax = fmaxf(tmax, fabsf((float)out));
         if (snap_now && snaps && inside) {
             const long long si = sbase + (long long)(gz - g.oz) * g.nx + (gx - g.ox);
             if (fp16)
@@ -219,19 +259,26 @@ __global__ void __launch_bounds__(NTH) k_step2d(const StepArgs<T> A, const int n
         }
     }
 
+    // ---- FP16 imaging term: one power-of-two scale per tile and step
+    if (MODE == kModeRecord && A.q_fp16) {
+        const float m = block_max(tmax, red);
+        const float s = pow2_scale(m), inv = 1.f / s;
+        if (tid == 0) A.qscale[shot * ntiles + tile] = s;
+#pragma unroll
+        for (int k = 0; k < RZ; k++) {
+            const int gz = z0 + ty + k * BY, gx = x0 + tx;
+            if (gz >= g.NZ || gx >= g.NX) continue;
+            static_cast<__half *>(A.qslot)[sh + cell_off(g, gz, 0, gx)] = __float2half_rn((float)qv[k] * inv);
+        }
+    }
+
     // ---- block max of p^{n+1} for the next snapshot's FP16 scale
-    if (max_next && fp16 && snaps) {
-        tmax = warp_max(tmax);
-        if ((tid & 31) == 0) red[tid >> 5] = tmax;
-        __syncthreads();
-        if (tid < 32) {
-            float m = tid < NTH / 32 ? red[tid] : 0.f;
-            m = warp_max(m);
-            if (tid == 0) {
-                const int k = (n1 - A.snap_begin) / A.snap_every;
-                if (!(m <= FLT_MAX)) atomicOr(A.flags, kFlagUnstable);
-                else atomicMax(&A.io->snap_max[shot * A.nsnap + k], __float_as_uint(m));
-            }
+    if (MODE == kModeForward && max_next && fp16 && snaps) {
+        const float m = block_max(tmax, red);
+        if (tid == 0) {
+            const int k = (n1 - A.snap_begin) / A.snap_every;
+            if (!(m <= FLT_MAX)) atomicOr(A.flags, kFlagUnstable);
+            else atomicMax(&A.io->snap_max[shot * A.nsnap + k], __float_as_uint(m));
         }
     }
 }
@@ -239,13 +286,18 @@ __global__ void __launch_bounds__(NTH) k_step2d(const StepArgs<T> A, const int n
 }  // namespace
 
 template <typename T>
-cudaError_t launch_step2d(const StepArgs<T> &a, int n, int nshots, cudaStream_t st) {
+cudaError_t launch_step2d(const StepArgs<T> &a, int n, int nshots, int mode, cudaStream_t st) {
     dim3 grid(a.ntx, a.ntz, nshots), block(BX, BY);
-    k_step2d<T><<<grid, block, 0, st>>>(a, n);
+    if (mode == kModeRecord)
+        k_step2d<T, kModeRecord><<<grid, block, 0, st>>>(a, n);
+    else if (mode == kModeAdjoint)
+        k_step2d<T, kModeAdjoint><<<grid, block, 0, st>>>(a, n);
+    else
+        k_step2d<T, kModeForward><<<grid, block, 0, st>>>(a, n);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_step2d<float>(const StepArgs<float> &, int, int, cudaStream_t);
-template cudaError_t launch_step2d<double>(const StepArgs<double> &, int, int, cudaStream_t);
+template cudaError_t launch_step2d<float>(const StepArgs<float> &, int, int, int, cudaStream_t);
+template cudaError_t launch_step2d<double>(const StepArgs<double> &, int, int, int, cudaStream_t);
 
 }  // namespace gsim

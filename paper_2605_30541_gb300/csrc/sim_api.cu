@@ -3,10 +3,14 @@
 // loop. Host code only; kernels live in the other translation units.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "sim_internal.h"
@@ -33,6 +37,18 @@ sim_status thread_fail(sim_status code, const char *fmt, ...) {
 }
 
 long long roundup(long long v, long long m) { return (v + m - 1) / m * m; }
+
+// 1D profile arrays (sponge E, CPML a/b) live in one buffer per kind: per axis
+// z, y, x a block of [kProfAlign zeros | N rounded up to kProfAlign | kProfAlign
+// zeros], so tile-wide vector loads just outside [0, N) read zeros in bounds.
+long long prof_block(int N) { return kProfAlign + roundup(N, kProfAlign) + kProfAlign; }
+long long prof_offset(const Geom &g, int axis) {
+    const int N[3] = {g.NZ, g.NY, g.NX};
+    long long off = kProfAlign;
+    for (int a = 0; a < axis; a++) off += prof_block(N[a]);
+    return off;
+}
+long long prof_total(const Geom &g) { return prof_block(g.NZ) + prof_block(g.NY) + prof_block(g.NX); }
 
 // Stability bounds of the 8th-order scheme (App. E.3.2).
 double symbol_sum_abs() { return std::fabs(kC1) + std::fabs(kC2) + std::fabs(kC3) + std::fabs(kC4); }
@@ -122,9 +138,9 @@ void fill_info(const sim_desc &d, sim_info *out) {
     out->courant_exact = courant_exact(d.ndim);
     for (int k = 0; k < 6; k++) out->c_damp[k] = d.nb[k] > 0 ? 1.5 * std::log(1.0 / d.R) / d.nb[k] : 0.0;
     out->cells_per_shot = (long long)out->NZ * out->NY * out->NX;
-    out->tile_x = kTileX2;
+    out->tile_x = d.precision == SIM_FP32 ? kTileXF : kTileX2;
     out->tile_y = 1;
-    out->tile_z = kTileZ2;
+    out->tile_z = d.precision == SIM_FP32 ? 16 : kTileZ2;
 }
 
 sim_status model_checks(const sim_desc &d, double vmin, double vmax, sim_info *info) {
@@ -187,6 +203,7 @@ struct sim_s {
     cudaStream_t st = nullptr;
     size_t esz = 4;
     int ntx = 0, nty = 1, ntz = 0;
+    int tile_x = kTileX2, tile_z = kTileZ2;  // tile of the step kernel in use
     int nsnap = 0;
     std::vector<void *> allocs;
     size_t bytes = 0;
@@ -203,12 +220,29 @@ struct sim_s {
     void *wave = nullptr, *gath = nullptr, *snaps = nullptr;
     size_t snaps_bytes = 0;
     int *rec_start = nullptr;
-    RecEntry *rec = nullptr;
+    void *rec = nullptr;      // RecEntryT<T>
     int *inj_start = nullptr;
     InjGroup *inj_grp = nullptr;
-    InjEntry *inj_ent = nullptr;
+    void *inj_ent = nullptr;  // InjEntryT<T>
     size_t cap_rec = 0, cap_grp = 0, cap_start = 0;
     unsigned *flags_host = nullptr;  // pinned copy of the device flags
+    // time loops are captured once per (kind, nshots) and replayed as CUDA graphs
+    // on a handle-owned stream, ordered with the caller's stream by events
+    cudaStream_t cst = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::vector<std::pair<long long, cudaGraphExec_t>> graphs;
+    bool use_graphs = true;
+    int tuned_nshots = 0;  // shot count the tile shape was tuned for (0: not yet)
+    // adjoint-state buffers, allocated by the first sim_adjoint call
+    bool adj_ready = false;
+    int seg = 0, nseg = 0;
+    void *ubuf = nullptr, *Gbuf = nullptr, *qbuf = nullptr, *ckpt = nullptr, *res = nullptr, *dobs = nullptr;
+    float *qscale = nullptr, *ckscale = nullptr;
+    double *acc = nullptr, *mpart = nullptr;
+    void *gradst = nullptr;
+    int *inj2_start = nullptr;
+    InjGroup *inj2_grp = nullptr;
+    void *inj2_ent = nullptr;
     bool model_set = false;
     double vmin = 0, vmax = 0;
     sim_status sticky = SIM_OK;
@@ -271,11 +305,11 @@ void host_profiles(const sim_s &s, std::vector<T> &E, std::vector<T> &ca, std::v
     const Geom &g = s.g;
     const int N[3] = {g.NZ, g.NY, g.NX};
     const int lo[3] = {g.nbz0, g.nby0, g.nbx0}, hi[3] = {g.nbz1, g.nby1, g.nbx1};
-    E.assign(N[0] + N[1] + N[2], T(0));
+    E.assign(prof_total(g), T(0));
     ca.assign(E.size(), T(0));
     cb.assign(E.size(), T(0));
-    int off = 0;
     for (int a = 0; a < 3; a++) {
+        const long long off = prof_offset(g, a);
         for (int i = 0; i < N[a]; i++) {
             int w = 0;
             double rho = 0;
@@ -302,7 +336,6 @@ void host_profiles(const sim_s &s, std::vector<T> &E, std::vector<T> &ca, std::v
                 cb[off + i] = T(b);
             }
         }
-        off += N[a];
     }
 }
 
@@ -361,27 +394,28 @@ sim_status set_model_t(sim_t s, const void *vel) {
 
 // Receivers: one entry per receiver, in the list of the tile that holds its
 // base cell; the stencil corners lie within that tile's radius-4 halo.
+template <typename T>
 sim_status build_receivers(sim_t s, int nrec, const double *rec_pos, std::vector<int> &start,
-                           std::vector<RecEntry> &ent) {
+                           std::vector<RecEntryT<T>> &ent) {
     const Geom &g = s->g;
     const int ntiles = s->ntx * s->nty * s->ntz;
-    std::vector<std::pair<int, RecEntry>> tmp;
+    std::vector<std::pair<int, RecEntryT<T>>> tmp;
     tmp.reserve(nrec);
     for (int r = 0; r < nrec; r++) {
         int i0[3];
         double t[3];
         if (!locate(g, s->d.h, rec_pos + (size_t)r * g.ndim, i0, t))
             return s->fail(SIM_ERR_ARG, "receiver %d lies outside the interior", r);
-        RecEntry e{};
+        RecEntryT<T> e{};
         e.rec = r;
-        const int tz = i0[0] / kTileZ2, tx = i0[2] / kTileX2;
-        e.lz = i0[0] - tz * kTileZ2;
+        const int tz = i0[0] / s->tile_z, tx = i0[2] / s->tile_x;
+        e.lz = i0[0] - tz * s->tile_z;
         e.ly = 0;
-        e.lx = i0[2] - tx * kTileX2;
+        e.lx = i0[2] - tx * s->tile_x;
         int k = 0;
         for (int dz = 0; dz < 2; dz++)
             for (int dy = 0; dy < (g.ndim == 3 ? 2 : 1); dy++)
-                for (int dx = 0; dx < 2; dx++) e.w[k++] = corner_weight(t, dz, dy, dx);
+                for (int dx = 0; dx < 2; dx++) e.w[k++] = T(corner_weight(t, dz, dy, dx));
         tmp.push_back({tz * s->ntx + tx, e});
     }
     std::stable_sort(tmp.begin(), tmp.end(), [](const auto &a, const auto &b) { return a.first < b.first; });
@@ -405,8 +439,9 @@ struct InjPoint {
 // Point injection: every stencil corner with a non-zero weight is a target
 // cell of the tile that owns it (none on a free-surface row, which is held at
 // zero). Targets are grouped per cell so one thread sums each cell in order.
+template <typename T>
 void group_injection(std::vector<InjPoint> &pts, int nlists, std::vector<int> &start,
-                     std::vector<InjGroup> &grp, std::vector<InjEntry> &ent) {
+                     std::vector<InjGroup> &grp, std::vector<InjEntryT<T>> &ent) {
     std::stable_sort(pts.begin(), pts.end(), [](const InjPoint &a, const InjPoint &b) {
         return a.tile != b.tile ? a.tile < b.tile : a.cell < b.cell;
     });
@@ -419,9 +454,9 @@ void group_injection(std::vector<InjPoint> &pts, int nlists, std::vector<int> &s
         G.cell = pts[i].cell;
         G.e0 = (int)ent.size();
         while (j < pts.size() && pts[j].tile == pts[i].tile && pts[j].cell == pts[i].cell) {
-            InjEntry e{};
+            InjEntryT<T> e{};
             e.pt = pts[j].pt;
-            e.w = pts[j].w;
+            e.w = T(pts[j].w);
             ent.push_back(e);
             j++;
         }
@@ -449,10 +484,10 @@ sim_status collect_points(sim_t s, int npts, const double *pos, bool per_shot, s
                     if (w == 0.0) continue;
                     const int z = i0[0] + dz, x = i0[2] + dx;
                     if (g.fs && z == 0) continue;
-                    const int tz = z / kTileZ2, tx = x / kTileX2;
+                    const int tz = z / s->tile_z, tx = x / s->tile_x;
                     InjPoint p;
                     p.tile = (per_shot ? q * ntiles : 0) + tz * s->ntx + tx;
-                    p.cell = (z - tz * kTileZ2) * kTileX2 + (x - tx * kTileX2);
+                    p.cell = (z - tz * s->tile_z) * s->tile_x + (x - tx * s->tile_x);
                     p.pt = q;
                     p.w = w;
                     out.push_back(p);
@@ -475,9 +510,8 @@ StepArgs<T> step_args(sim_t s) {
     a.pbuf[0] = static_cast<T *>(s->pbuf);
     a.pbuf[1] = static_cast<T *>(s->pbuf) + (long long)s->d.max_shots * s->g.fstride;
     a.ch = static_cast<const T *>(s->ch);
-    const int N[3] = {s->g.NZ, s->g.NY, s->g.NX};
-    int off = 0;
     for (int ax = 0; ax < 3; ax++) {
+        const long long off = prof_offset(s->g, ax);
         a.E[ax] = s->d.bc == SIM_BC_SPONGE ? static_cast<const T *>(s->E) + off : nullptr;
         const bool on = s->d.bc == SIM_BC_CPML && s->psi[ax][0] != nullptr;
         a.ca[ax] = on ? static_cast<const T *>(s->ca) + off : nullptr;
@@ -485,7 +519,6 @@ StepArgs<T> step_args(sim_t s) {
         a.psi[ax][0] = static_cast<T *>(s->psi[ax][0]);
         a.psi[ax][1] = static_cast<T *>(s->psi[ax][1]);
         a.zeta[ax] = static_cast<T *>(s->zeta[ax]);
-        off += N[ax];
     }
     a.bc = s->d.bc;
     a.src_scale = T(s->g.ndim == 3 ? 1.0 / s->d.h : 1.0);
@@ -498,12 +531,14 @@ StepArgs<T> step_args(sim_t s) {
     a.snap_begin = s->d.snap_begin;
     a.snap_end = std::min(s->d.snap_end, s->d.nt);
     a.rec_start = s->rec_start;
-    a.rec = s->rec;
+    a.rec = static_cast<const RecEntryT<T> *>(s->rec);
     a.inj_start = s->inj_start;
     a.inj_grp = s->inj_grp;
-    a.inj_ent = s->inj_ent;
+    a.inj_ent = static_cast<const InjEntryT<T> *>(s->inj_ent);
     a.io = s->io;
     a.flags = s->flags;
+    a.sample = 1;
+    a.inj_reverse = 0;
     return a;
 }
 
@@ -528,12 +563,176 @@ sim_status reset_state(sim_t s, int nshots) {
     return SIM_OK;
 }
 
+// Per-launch facts of step n for the FP32 kernel (see StepTime).
+template <typename T>
+StepTime step_time(const sim_s *s, const StepArgs<T> &a, int n, int mode, void *qslot, float *qscale) {
+    StepTime t{};
+    t.n = n;
+    t.snap_k = t.max_k = -1;
+    auto snap_index = [&](int m) {
+        if (a.nsnap <= 0 || m < a.snap_begin || m >= a.snap_end || (m - a.snap_begin) % a.snap_every) return -1;
+        return (m - a.snap_begin) / a.snap_every;
+    };
+    if (mode == kModeForward) {
+        t.snap_k = snap_index(n);
+        if (s->d.snap_fp16) t.max_k = snap_index(n + 1);
+    }
+    const int row = a.inj_reverse ? a.nt - n : n;
+    t.inj_row = (row >= 0 && row < a.nt) ? row : -1;
+    t.qslot = qslot;
+    t.qscale = qscale;
+    return t;
+}
+
+template <typename T>
+cudaError_t launch_step(sim_t s, const StepArgs<T> &a, int n, int nshots, int mode, cudaStream_t st,
+                        void *qslot = nullptr, float *qscale = nullptr);
+template <>
+cudaError_t launch_step<float>(sim_t s, const StepArgs<float> &a, int n, int nshots, int mode, cudaStream_t st,
+                               void *qslot, float *qscale) {
+    return launch_step2d_f32(a, step_time(s, a, n, mode, qslot, qscale), s->tile_z, nshots, mode, st,
+                             s->use_graphs);
+}
+template <>
+cudaError_t launch_step<double>(sim_t s, const StepArgs<double> &a, int n, int nshots, int mode, cudaStream_t st,
+                                void *qslot, float *qscale) {
+    StepArgs<double> b = a;
+    b.qslot = qslot;
+    b.qscale = qscale;
+    return launch_step2d<double>(b, n, nshots, mode, st);
+}
+
+// Run `body(stream)` — a sequence of kernel launches whose arguments depend
+// only on handle-owned buffers — as a captured CUDA graph keyed by `key`
+// (captured on first use, replayed afterwards), ordered after everything
+// already queued on the handle's stream and before anything queued later.
+template <typename F>
+sim_status run_graph(sim_t s, long long key, F body) {
+    if (!s->use_graphs) {
+        cudaError_t e = body(s->st);
+        return s->cuda(e, "time loop");
+    }
+    cudaGraphExec_t exec = nullptr;
+    for (auto &kv : s->graphs)
+        if (kv.first == key) exec = kv.second;
+    if (!exec) {
+        cudaGraph_t graph = nullptr;
+        if (sim_status r = s->cuda(cudaStreamBeginCapture(s->cst, cudaStreamCaptureModeThreadLocal), "capture"))
+            return r;
+        cudaError_t e = body(s->cst);
+        cudaError_t e2 = cudaStreamEndCapture(s->cst, &graph);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (sim_status r = s->cuda(e, "graph capture")) return r;
+        s->graphs.push_back({key, exec});
+    }
+    if (sim_status r = s->cuda(cudaEventRecord(s->ev_in, s->st), "event")) return r;
+    if (sim_status r = s->cuda(cudaStreamWaitEvent(s->cst, s->ev_in, 0), "event")) return r;
+    if (sim_status r = s->cuda(cudaGraphLaunch(exec, s->cst), "graph launch")) return r;
+    if (sim_status r = s->cuda(cudaEventRecord(s->ev_out, s->cst), "event")) return r;
+    return s->cuda(cudaStreamWaitEvent(s->st, s->ev_out, 0), "event");
+}
+
+// ---------------------------------------------------------------- autotuner
+//
+// The FP32 step kernel comes in tile heights 8, 16 and 32 rows (x 128 cells).
+// Which is fastest depends on the grid (waves per launch, share of CPML
+// tiles) and on the shot count, so the first forward or adjoint call for a
+// (grid, boundary, shots) key times a short run of each on this GPU with CUDA
+// events and keeps the winner; the choice is cached for the process.
+// GSIM_TILE_Z forces a height; GSIM_AUTOTUNE=0 keeps the default (16).
+using TuneKey = std::tuple<int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune_cache;
+
+// Most tiles any tuned shape can produce (sizes the per-tile lists).
+long long max_tiles(const sim_s *s) {
+    if (s->d.precision == SIM_FP32) return (long long)((s->g.NX + kTileXF - 1) / kTileXF) * ((s->g.NZ + 7) / 8);
+    return (long long)((s->g.NX + kTileX2 - 1) / kTileX2) * ((s->g.NZ + kTileZ2 - 1) / kTileZ2);
+}
+
+void set_tile_z(sim_t s, int tz) {
+    s->tile_z = tz;
+    s->ntz = (s->g.NZ + tz - 1) / tz;
+}
+
+sim_status autotune(sim_t s, int nshots) {
+    if (s->d.precision != SIM_FP32 || s->tuned_nshots == nshots) return SIM_OK;
+    s->tuned_nshots = nshots;
+    if (const char *f = getenv("GSIM_TILE_Z")) {
+        const int tz = atoi(f);
+        if (tz == 8 || tz == 16 || tz == 32) set_tile_z(s, tz);
+        return SIM_OK;
+    }
+    const char *at = getenv("GSIM_AUTOTUNE");
+    if (at && at[0] == '0') return SIM_OK;
+    int dev_sms = 0;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, s->dev);
+    const TuneKey key{s->g.NZ, s->g.NX, s->d.bc, s->d.free_surface, nshots, dev_sms};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            set_tile_z(s, it->second);
+            return SIM_OK;
+        }
+    }
+    const int cand[3] = {8, 16, 32};
+    float best = 1e30f;
+    int best_tz = 16;
+    cudaEvent_t e0, e1;
+    if (sim_status r = s->cuda(cudaEventCreate(&e0), "tune event")) return r;
+    if (sim_status r = s->cuda(cudaEventCreate(&e1), "tune event")) return r;
+    sim_status rc = SIM_OK;
+    for (int tz : cand) {
+        set_tile_z(s, tz);
+        const int ntiles = s->ntx * s->ntz;
+        std::vector<int> zeros((size_t)nshots * ntiles + 1, 0);
+        rc = upload(s, s->rec_start, zeros, s->cap_start, "tune lists");
+        if (!rc) rc = upload(s, s->inj_start, zeros, s->cap_start, "tune lists");
+        if (!rc) rc = reset_state(s, nshots);
+        if (rc) break;
+        StepArgs<float> a = step_args<float>(s);
+        a.sample = 0;
+        a.nsnap = 0;
+        const int warm = 3, timed = 12;
+        cudaError_t e = cudaSuccess;
+        for (int n = 0; n < warm + timed && e == cudaSuccess; n++) {
+            if (n == warm) e = cudaEventRecord(e0, s->st);
+            if (e == cudaSuccess)
+                e = launch_step2d_f32(a, step_time(s, a, n, kModeForward, nullptr, nullptr), tz, nshots,
+                                      kModeForward, s->st, false);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s->st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if ((rc = s->cuda(e, "autotune"))) break;
+        if (getenv("GSIM_TUNE_LOG"))
+            fprintf(stderr, "[gsim autotune] grid %dx%d shots %d tile 128x%d: %.2f us/step\n", s->g.NZ, s->g.NX,
+                    nshots, tz, 1e3 * ms / timed);
+        if (ms < best) {
+            best = ms;
+            best_tz = tz;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    set_tile_z(s, best_tz);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best_tz;
+    return SIM_OK;
+}
+
 template <typename T>
 sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src_pos, int nrec,
                      const double *rec_pos, void *gather, void *snaps, float *snap_scale) {
     const sim_desc &d = s->d;
     const Geom &g = s->g;
     if (g.ndim != 2) return s->fail(SIM_ERR_UNSUPPORTED, "3D forward is not built yet");
+    if (sim_status r = autotune(s, nshots)) return r;
     const size_t nt = d.nt;
     // inputs
     const void *wav = wavelet;
@@ -567,20 +766,21 @@ sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src
 
     // geometry lists
     std::vector<int> rstart, istart;
-    std::vector<RecEntry> rent;
+    std::vector<RecEntryT<T>> rent;
     std::vector<InjGroup> igrp;
-    std::vector<InjEntry> ient;
-    if (sim_status r = build_receivers(s, nrec, rec_pos, rstart, rent)) return r;
+    std::vector<InjEntryT<T>> ient;
+    if (sim_status r = build_receivers<T>(s, nrec, rec_pos, rstart, rent)) return r;
     std::vector<InjPoint> pts;
     if (wavelet)
         if (sim_status r = collect_points(s, nshots, src_pos, true, pts, "source")) return r;
     const int ntiles = s->ntx * s->nty * s->ntz;
-    group_injection(pts, nshots * ntiles, istart, igrp, ient);
+    group_injection<T>(pts, nshots * ntiles, istart, igrp, ient);
     if (sim_status r = upload(s, s->rec_start, rstart, s->cap_start, "receiver start")) return r;
-    if (sim_status r = upload(s, s->rec, rent, s->cap_rec, "receiver")) return r;
+    if (sim_status r = upload(s, static_cast<RecEntryT<T> *>(s->rec), rent, s->cap_rec, "receiver")) return r;
     if (sim_status r = upload(s, s->inj_start, istart, s->cap_start, "injection start")) return r;
     if (sim_status r = upload(s, s->inj_grp, igrp, s->cap_grp, "injection group")) return r;
-    if (sim_status r = upload(s, s->inj_ent, ient, s->cap_grp, "injection entry")) return r;
+    if (sim_status r = upload(s, static_cast<InjEntryT<T> *>(s->inj_ent), ient, s->cap_grp, "injection entry"))
+        return r;
 
     SimIO io{};
     io.wavelet = wav;
@@ -598,8 +798,14 @@ sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src
     StepArgs<T> a = step_args<T>(s);
     a.inj_per_shot = 1;
     a.inj_kind = 0;
-    for (int n = 0; n < d.nt; n++)
-        if (sim_status r = s->cuda(launch_step2d<T>(a, n, nshots, s->st), "step kernel")) return r;
+    if (sim_status r = run_graph(s, ((long long)nshots << 8) | ((long long)s->tile_z << 2) | 1, [&](cudaStream_t st) {
+            for (int n = 0; n < d.nt; n++) {
+                cudaError_t e = launch_step<T>(s, a, n, nshots, kModeForward, st);
+                if (e != cudaSuccess) return e;
+            }
+            return cudaSuccess;
+        }))
+        return r;
     // the buffer written last holds p^nt
     if (sim_status r = s->cuda(launch_check_finite<T>(g, static_cast<const T *>(a.pbuf[d.nt & 1]), nshots, s->flags,
                                                       s->st), "finite check"))
@@ -625,6 +831,236 @@ sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src
         wait = true;
     }
     if (wait) return poll_flags(s, true);
+    return SIM_OK;
+}
+
+
+constexpr int kResidBlocks = 1024;
+
+sim_status ensure_adjoint(sim_t s) {
+    if (s->adj_ready) return SIM_OK;
+    const sim_desc &d = s->d;
+    const Geom &g = s->g;
+    s->seg = (int)std::ceil(std::sqrt((double)d.nt));
+    s->nseg = (d.nt + s->seg - 1) / s->seg;
+    const int ms = d.max_shots;
+    const size_t ncomp = (size_t)g.NZ * g.NY * g.NX;
+    const long long ntiles = max_tiles(s);
+    const size_t nrows = (size_t)ms * d.nt * std::max(1, d.max_rec);
+    sim_status rc = SIM_OK;
+    auto A = [&](size_t n) { return rc == SIM_OK ? s->alloc(n, &rc) : nullptr; };
+    s->ubuf = A(2 * (size_t)ms * g.fstride * s->esz);
+    s->Gbuf = A((size_t)ms * g.fstride * s->esz);
+    s->qbuf = A((size_t)s->seg * ms * g.fstride * s->esz);
+    s->qscale = static_cast<float *>(A((size_t)s->seg * ms * ntiles * sizeof(float)));
+    s->ckpt = A((size_t)s->nseg * 2 * ms * ncomp * s->esz);
+    const size_t ck_tiles = (size_t)((g.NX + kTileX2 - 1) / kTileX2) * ((g.NZ + kTileZ2 - 1) / kTileZ2);
+    s->ckscale = static_cast<float *>(A((size_t)s->nseg * 2 * ms * ck_tiles * sizeof(float)));
+    s->res = A(nrows * s->esz);
+    s->dobs = A(nrows * s->esz);
+    s->acc = static_cast<double *>(A((size_t)g.nz * g.ny * g.nx * sizeof(double)));
+    s->gradst = A((size_t)g.nz * g.ny * g.nx * s->esz);
+    s->mpart = static_cast<double *>(A(kResidBlocks * sizeof(double)));
+    s->inj2_start = static_cast<int *>(A(s->cap_start * sizeof(int)));
+    s->inj2_grp = static_cast<InjGroup *>(A(s->cap_grp * sizeof(InjGroup)));
+    s->inj2_ent = A(s->cap_grp * sizeof(InjEntryT<double>));
+    if (rc == SIM_OK) s->adj_ready = true;
+    return rc;
+}
+
+template <typename T>
+sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src_pos, int nrec,
+                     const double *rec_pos, const void *d_obs, void *gather_out, double *misfit_out, int ckpt_fp16,
+                     void *grad_v) {
+    const sim_desc &d = s->d;
+    const Geom &g = s->g;
+    if (g.ndim != 2) return s->fail(SIM_ERR_UNSUPPORTED, "the 3D adjoint is not built");
+    if (d.bc == SIM_BC_CPML) return s->fail(SIM_ERR_UNSUPPORTED, "the adjoint supports sponge or no absorption");
+    if (ckpt_fp16 && d.precision != SIM_FP32) return s->fail(SIM_ERR_ARG, "FP16 checkpoints need an FP32 handle");
+    if (nrec < 1) return s->fail(SIM_ERR_ARG, "the misfit needs receivers");
+    if (!d_obs || !wavelet || !grad_v) return s->fail(SIM_ERR_ARG, "d_obs, wavelet and grad_v are required");
+    if (sim_status r = ensure_adjoint(s)) return r;
+    if (sim_status r = autotune(s, nshots)) return r;
+    const size_t nt = d.nt;
+    const int ms = d.max_shots;
+    const long long ncomp = (long long)g.NZ * g.NY * g.NX;
+    const int ntiles = s->ntx * s->nty * s->ntz;
+    const long long nint = (long long)g.nz * g.ny * g.nx;
+    const size_t nrows = (size_t)nshots * nt * nrec;
+
+    // inputs
+    const void *wav = wavelet;
+    if (!is_device_ptr(wavelet)) {
+        if (sim_status r = s->cuda(cudaMemcpyAsync(s->wave, wavelet, nt * sizeof(T), cudaMemcpyHostToDevice, s->st),
+                                   "wavelet upload"))
+            return r;
+        wav = s->wave;
+    }
+    const void *dob = d_obs;
+    if (!is_device_ptr(d_obs)) {
+        if (sim_status r = s->cuda(cudaMemcpyAsync(s->dobs, d_obs, nrows * sizeof(T), cudaMemcpyHostToDevice, s->st),
+                                   "d_obs upload"))
+            return r;
+        dob = s->dobs;
+    }
+    const bool g_host = gather_out && !is_device_ptr(gather_out);
+    void *gdev = (gather_out && !g_host) ? gather_out : s->gath;
+    const bool gr_host = !is_device_ptr(grad_v);
+    void *grdev = gr_host ? s->gradst : grad_v;
+    if (gr_host)
+        if (sim_status r = s->cuda(cudaMemcpyAsync(grdev, grad_v, nint * sizeof(T), cudaMemcpyHostToDevice, s->st),
+                                   "gradient upload"))
+            return r;
+
+    // geometry: receivers sample the forward; sources drive the forward and the
+    // recompute; receivers inject the residual into the adjoint sweep
+    std::vector<int> rstart, istart, jstart;
+    std::vector<RecEntryT<T>> rent;
+    std::vector<InjGroup> igrp, jgrp;
+    std::vector<InjEntryT<T>> ient, jent;
+    if (sim_status r = build_receivers<T>(s, nrec, rec_pos, rstart, rent)) return r;
+    std::vector<InjPoint> pts, rpts;
+    if (sim_status r = collect_points(s, nshots, src_pos, true, pts, "source")) return r;
+    group_injection<T>(pts, nshots * ntiles, istart, igrp, ient);
+    if (sim_status r = collect_points(s, nrec, rec_pos, false, rpts, "receiver")) return r;
+    group_injection<T>(rpts, ntiles, jstart, jgrp, jent);
+    if (sim_status r = upload(s, s->rec_start, rstart, s->cap_start, "receiver start")) return r;
+    if (sim_status r = upload(s, static_cast<RecEntryT<T> *>(s->rec), rent, s->cap_rec, "receiver")) return r;
+    if (sim_status r = upload(s, s->inj_start, istart, s->cap_start, "injection start")) return r;
+    if (sim_status r = upload(s, s->inj_grp, igrp, s->cap_grp, "injection group")) return r;
+    if (sim_status r = upload(s, static_cast<InjEntryT<T> *>(s->inj_ent), ient, s->cap_grp, "injection entry"))
+        return r;
+    if (sim_status r = upload(s, s->inj2_start, jstart, s->cap_start, "residual start")) return r;
+    if (sim_status r = upload(s, s->inj2_grp, jgrp, s->cap_grp, "residual group")) return r;
+    if (sim_status r = upload(s, static_cast<InjEntryT<T> *>(s->inj2_ent), jent, s->cap_grp, "residual entry"))
+        return r;
+
+    SimIO io{};
+    io.wavelet = wav;
+    io.gather = gdev;
+    io.resid = s->res;
+    io.nrec = nrec;
+    io.nshots = nshots;
+    if (sim_status r = s->cuda(cudaMemcpyAsync(s->io, &io, sizeof io, cudaMemcpyHostToDevice, s->st), "io upload"))
+        return r;
+    if (sim_status r = reset_state(s, nshots)) return r;
+
+    const int L = s->seg;
+    const size_t ck_state = (size_t)ms * ncomp;  // elements of one checkpointed state (all shots)
+    const int ckx = (g.NX + kTileX2 - 1) / kTileX2, ckz = (g.NZ + kTileZ2 - 1) / kTileZ2;  // store-kernel tiles
+    const size_t ck_tiles = (size_t)ms * ckx * ckz;
+    const size_t q_tiles = (size_t)ms * ntiles;
+    auto ck_ptr = [&](int k, int which) {
+        return static_cast<char *>(s->ckpt) + ((size_t)k * 2 + which) * ck_state * (ckpt_fp16 ? 2 : sizeof(T));
+    };
+    auto ck_scale = [&](int k, int which) { return s->ckscale + ((size_t)k * 2 + which) * ck_tiles; };
+
+    // 1. forward pass, keeping (p^{n-1}, p^n) at every segment start
+    StepArgs<T> a = step_args<T>(s);
+    a.inj_per_shot = 1;
+    a.inj_kind = 0;
+    a.nsnap = 0;
+    for (int n = 0; n < d.nt; n++) {
+        if (n % L == 0) {
+            const int k = n / L;
+            if (sim_status r = s->cuda(launch_store_state<T>(g, a.pbuf[n & 1], ck_ptr(k, 1), ck_scale(k, 1), ckpt_fp16,
+                                                             nshots, ncomp, ckx, ckz, s->st), "checkpoint"))
+                return r;
+            if (sim_status r = s->cuda(launch_store_state<T>(g, a.pbuf[(n + 1) & 1], ck_ptr(k, 0), ck_scale(k, 0),
+                                                             ckpt_fp16, nshots, ncomp, ckx, ckz, s->st),
+                                       "checkpoint"))
+                return r;
+        }
+        if (sim_status r = s->cuda(launch_step<T>(s, a, n, nshots, kModeForward, s->st), "forward step")) return r;
+    }
+    // 2. residual and misfit
+    if (sim_status r = s->cuda(launch_residual<T>(static_cast<const T *>(gdev), static_cast<const T *>(dob),
+                                                  static_cast<T *>(s->res), (long long)nrows, s->mpart, kResidBlocks,
+                                                  s->st), "residual"))
+        return r;
+    // 3. segments in reverse: restore, recompute while recording Q', sweep the adjoint back
+    const size_t ub = (size_t)g.fstride * s->esz * nshots;
+    if (sim_status r = s->cuda(cudaMemsetAsync(s->ubuf, 0, ub, s->st), "adjoint reset")) return r;
+    if (sim_status r = s->cuda(cudaMemsetAsync(static_cast<char *>(s->ubuf) + (size_t)g.fstride * s->esz * ms, 0, ub,
+                                               s->st), "adjoint reset"))
+        return r;
+    if (sim_status r = s->cuda(cudaMemsetAsync(s->Gbuf, 0, (size_t)nshots * g.fstride * s->esz, s->st), "adjoint reset"))
+        return r;
+    StepArgs<T> rcp = a;
+    rcp.sample = 0;
+    rcp.q_fp16 = ckpt_fp16;
+    StepArgs<T> adj = a;
+    adj.pbuf[0] = static_cast<T *>(s->ubuf);
+    adj.pbuf[1] = static_cast<T *>(s->ubuf) + (long long)ms * g.fstride;
+    adj.sample = 0;
+    adj.inj_start = s->inj2_start;
+    adj.inj_grp = s->inj2_grp;
+    adj.inj_ent = static_cast<const InjEntryT<T> *>(s->inj2_ent);
+    adj.inj_per_shot = 0;
+    adj.inj_kind = 1;
+    adj.inj_reverse = 1;
+    adj.src_scale = T(d.h * d.h);
+    adj.q_fp16 = ckpt_fp16;
+    adj.G = static_cast<T *>(s->Gbuf);
+    const size_t qslot_bytes = (size_t)ms * g.fstride * (ckpt_fp16 ? 2 : sizeof(T));
+    for (int sgi = s->nseg - 1; sgi >= 0; sgi--) {
+        const int n0 = sgi * L, e = std::min(n0 + L, d.nt);
+        if (sim_status r = s->cuda(launch_load_state<T>(g, a.pbuf[n0 & 1], ck_ptr(sgi, 1), ck_scale(sgi, 1), ckpt_fp16,
+                                                        nshots, ncomp, ckx, ckz, s->st), "restore"))
+            return r;
+        if (sim_status r = s->cuda(launch_load_state<T>(g, a.pbuf[(n0 + 1) & 1], ck_ptr(sgi, 0), ck_scale(sgi, 0),
+                                                        ckpt_fp16, nshots, ncomp, ckx, ckz, s->st), "restore"))
+            return r;
+        for (int n = n0; n < e; n++) {
+            void *slot = static_cast<char *>(s->qbuf) + (size_t)(n - n0) * qslot_bytes;
+            float *scl = s->qscale + (size_t)(n - n0) * q_tiles;
+            if (sim_status r = s->cuda(launch_step<T>(s, rcp, n, nshots, kModeRecord, s->st, slot, scl),
+                                       "recompute step"))
+                return r;
+        }
+        for (int k = e; k >= n0 + 1; k--) {
+            void *slot = static_cast<char *>(s->qbuf) + (size_t)(k - 1 - n0) * qslot_bytes;
+            float *scl = s->qscale + (size_t)(k - 1 - n0) * q_tiles;
+            if (sim_status r = s->cuda(launch_step<T>(s, adj, d.nt - k, nshots, kModeAdjoint, s->st, slot, scl),
+                                       "adjoint step"))
+                return r;
+        }
+    }
+    // 4. gradient: FP64 sum over shots and replicated cells, added to grad_v
+    if (sim_status r = s->cuda(cudaMemsetAsync(s->acc, 0, nint * sizeof(double), s->st), "gradient reset")) return r;
+    if (sim_status r = s->cuda(launch_fold_gradient<T>(g, static_cast<const T *>(s->Gbuf), g.fstride, nshots,
+                                                       static_cast<const T *>(s->vpad), 1.0 / (d.h * d.h), s->acc,
+                                                       s->st), "gradient fold"))
+        return r;
+    if (sim_status r = s->cuda(launch_add_gradient<T>(s->acc, static_cast<T *>(grdev), nint, s->st), "gradient add"))
+        return r;
+    if (sim_status r = s->cuda(launch_check_finite<T>(g, a.pbuf[d.nt & 1], nshots, s->flags, s->st), "finite check"))
+        return r;
+    if (sim_status r = s->cuda(cudaMemcpyAsync(s->flags_host, s->flags, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                               s->st), "flag readback"))
+        return r;
+    if (gr_host)
+        if (sim_status r = s->cuda(cudaMemcpyAsync(grad_v, grdev, nint * sizeof(T), cudaMemcpyDeviceToHost, s->st),
+                                   "gradient download"))
+            return r;
+    if (g_host)
+        if (sim_status r = s->cuda(cudaMemcpyAsync(gather_out, gdev, nrows * sizeof(T), cudaMemcpyDeviceToHost, s->st),
+                                   "gather download"))
+            return r;
+    std::vector<double> part(kResidBlocks);
+    if (misfit_out) {
+        if (sim_status r = s->cuda(cudaMemcpyAsync(part.data(), s->mpart, part.size() * sizeof(double),
+                                                   cudaMemcpyDeviceToHost, s->st), "misfit readback"))
+            return r;
+    }
+    if (misfit_out || gr_host || g_host) {
+        if (sim_status r = poll_flags(s, true)) return r;
+        if (misfit_out) {
+            double J = 0;
+            for (double v : part) J += v;
+            *misfit_out = J;
+        }
+    }
     return SIM_OK;
 }
 
@@ -666,8 +1102,12 @@ sim_status sim_create(const sim_desc *din, const void *vel, void *cuda_stream, s
     s->st = static_cast<cudaStream_t>(cuda_stream);
     s->esz = d.precision == SIM_FP64 ? 8 : 4;
     s->nsnap = nsnap_of(d);
-    s->ntx = (s->g.NX + kTileX2 - 1) / kTileX2;
-    s->ntz = (s->g.NZ + kTileZ2 - 1) / kTileZ2;
+    if (d.precision == SIM_FP32) {
+        s->tile_x = kTileXF;
+        s->tile_z = 16;
+    }
+    s->ntx = (s->g.NX + s->tile_x - 1) / s->tile_x;
+    s->ntz = (s->g.NZ + s->tile_z - 1) / s->tile_z;
     s->nty = 1;
     sim_status rc = SIM_OK;
     if (cudaGetDevice(&s->dev) != cudaSuccess) {
@@ -679,8 +1119,7 @@ sim_status sim_create(const sim_desc *din, const void *vel, void *cuda_stream, s
     const size_t fb = (size_t)g.fstride * s->esz;
     const int ms = d.max_shots;
     const size_t nint = (size_t)g.nz * g.ny * g.nx;
-    const size_t nprof = (size_t)g.NZ + g.NY + g.NX;
-    const int ntiles = s->ntx * s->nty * s->ntz;
+    const size_t nprof = (size_t)prof_total(g);
     auto A = [&](size_t n) { return rc == SIM_OK ? s->alloc(n, &rc) : nullptr; };
     s->pbuf = A(2 * fb * ms);
     s->ch = A(fb);
@@ -706,14 +1145,20 @@ sim_status sim_create(const sim_desc *din, const void *vel, void *cuda_stream, s
     s->snap_scale = static_cast<float *>(A(sizeof(float) * std::max(1, s->nsnap * ms)));
     s->wave = A((size_t)d.nt * s->esz);
     s->gath = A((size_t)ms * d.nt * std::max(1, d.max_rec) * s->esz);
-    s->cap_start = (size_t)ms * ntiles + 1;
+    s->cap_start = (size_t)ms * max_tiles(s) + 1;
     s->cap_rec = std::max(1, d.max_rec);
     s->cap_grp = 8 * (size_t)std::max(ms, std::max(1, d.max_rec));
     s->rec_start = static_cast<int *>(A(s->cap_start * sizeof(int)));
-    s->rec = static_cast<RecEntry *>(A(s->cap_rec * sizeof(RecEntry)));
+    s->rec = A(s->cap_rec * sizeof(RecEntryT<double>));
     s->inj_start = static_cast<int *>(A(s->cap_start * sizeof(int)));
     s->inj_grp = static_cast<InjGroup *>(A(s->cap_grp * sizeof(InjGroup)));
-    s->inj_ent = static_cast<InjEntry *>(A(s->cap_grp * sizeof(InjEntry)));
+    s->inj_ent = A(s->cap_grp * sizeof(InjEntryT<double>));
+    const char *ge = getenv("GSIM_GRAPHS");
+    s->use_graphs = !(ge && ge[0] == '0');
+    if (rc == SIM_OK) rc = s->cuda(cudaStreamCreateWithFlags(&s->cst, cudaStreamNonBlocking), "stream");
+    if (rc == SIM_OK) rc = s->cuda(cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming), "event");
+    if (rc == SIM_OK) rc = s->cuda(cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming), "event");
+    if (rc == SIM_OK && d.precision == SIM_FP32) rc = s->cuda(configure_step2d_f32(), "kernel configuration");
     if (rc == SIM_OK && cudaMallocHost(&s->flags_host, sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
         rc = s->fail(SIM_ERR_OOM, "pinned host allocation failed");
@@ -767,10 +1212,22 @@ sim_status sim_forward(sim_t s, int nshots, const void *wavelet, const double *s
                : forward_t<float>(s, nshots, wavelet, src_pos, nrec, rec_pos, gather, snaps, snap_scale);
 }
 
-sim_status sim_adjoint(sim_t s, int, const void *, const double *, int, const double *, const void *, void *,
-                       double *, int, void *) {
+sim_status sim_adjoint(sim_t s, int nshots, const void *wavelet, const double *src_pos, int nrec,
+                       const double *rec_pos, const void *d_obs, void *gather_out, double *misfit_out, int ckpt_fp16,
+                       void *grad_v) {
     if (!s) return thread_fail(SIM_ERR_ARG, "NULL handle");
-    return s->fail(SIM_ERR_UNSUPPORTED, "adjoint not built yet");
+    if (sim_status r = poll_flags(s, false)) return r;
+    if (!s->model_set) return s->fail(SIM_ERR_STATE, "no velocity model set");
+    if (nshots < 1 || nshots > s->d.max_shots)
+        return s->fail(SIM_ERR_ARG, "nshots = %d outside [1, %d]", nshots, s->d.max_shots);
+    if (nrec < 0 || nrec > s->d.max_rec) return s->fail(SIM_ERR_ARG, "nrec = %d outside [0, %d]", nrec, s->d.max_rec);
+    if (!src_pos || !rec_pos) return s->fail(SIM_ERR_ARG, "positions are required");
+    cudaSetDevice(s->dev);
+    return s->d.precision == SIM_FP64
+               ? adjoint_t<double>(s, nshots, wavelet, src_pos, nrec, rec_pos, d_obs, gather_out, misfit_out,
+                                   ckpt_fp16, grad_v)
+               : adjoint_t<float>(s, nshots, wavelet, src_pos, nrec, rec_pos, d_obs, gather_out, misfit_out,
+                                  ckpt_fp16, grad_v);
 }
 
 sim_status sim_batch(int, const sim_batch_item *, void *) {
@@ -786,6 +1243,8 @@ sim_status sim_sync(sim_t s) {
 sim_status sim_get_info(sim_t s, sim_info *out) {
     if (!s || !out) return thread_fail(SIM_ERR_ARG, "NULL argument");
     fill_info(s->d, out);
+    out->tile_x = s->tile_x;
+    out->tile_z = s->tile_z;
     out->vmin = s->vmin;
     out->vmax = s->vmax;
     out->courant = s->vmax * s->d.dt / s->d.h;
@@ -802,6 +1261,11 @@ void sim_destroy(sim_t s) {
     if (!s) return;
     cudaSetDevice(s->dev);
     cudaStreamSynchronize(s->st);
+    if (s->cst) cudaStreamSynchronize(s->cst);
+    for (auto &kv : s->graphs) cudaGraphExecDestroy(kv.second);
+    if (s->cst) cudaStreamDestroy(s->cst);
+    if (s->ev_in) cudaEventDestroy(s->ev_in);
+    if (s->ev_out) cudaEventDestroy(s->ev_out);
     for (void *p : s->allocs) cudaFree(p);
     if (s->flags_host) cudaFreeHost(s->flags_host);
     cudaGetLastError();

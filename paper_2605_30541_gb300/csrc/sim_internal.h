@@ -24,9 +24,11 @@ namespace gsim {
 //     org + (z * PY + y) * P + x
 // where PY is the number of rows per z-plane (1 in 2D).
 constexpr int kGhost = 8;      // >= the widest halo any kernel reads (CPML recompute)
-constexpr int kTileX2 = 32;    // 2D tile (x) of the stencil kernels
-constexpr int kTileZ2 = 16;    // 2D tile (z)
-constexpr int kRoundX = 64;    // padded extents round up to these, so any tile
+constexpr int kTileX2 = 32;    // 2D tile (x) of the generic (any precision) stencil kernel
+constexpr int kTileZ2 = 16;    // 2D tile (z) of the generic kernel
+constexpr int kTileXF = 128;   // 2D tile (x) of the FP32 kernel; its z extent is tuned (8, 16, 32)
+constexpr int kProfAlign = 128; // per-axis profile segments: aligned starts, room for a whole last tile
+constexpr int kRoundX = 128;   // padded extents round up to these, so any tile
 constexpr int kRoundZ = 32;    //   of the tuned set stays inside the allocation
 constexpr int kRoundY = 32;
 constexpr int kMinmaxBlocks = 512;  // partial (min, max, bad) triples written by launch_minmax
@@ -51,10 +53,11 @@ __host__ __device__ inline long long cell_off(const Geom &g, int z, int y, int x
 // Receiver: base cell of its linear-interpolation stencil (local to the tile
 // that samples it) and the 4 (2D) or 8 (3D) corner weights, corner order
 // (dz, dy, dx) with dx fastest.
-struct RecEntry {
+template <typename W>
+struct RecEntryT {
     int rec;
     int lz, ly, lx;
-    double w[8];
+    W w[8];
 };
 
 // Injection: one group per target cell of a tile, summing its entries in a
@@ -64,10 +67,10 @@ struct InjGroup {
     int e0, e1; // entry range
     int pad;
 };
-struct InjEntry {
+template <typename W>
+struct InjEntryT {
     int pt;     // index of the input value (shot for a source, receiver for a residual)
-    int pad;
-    double w;
+    W w;
 };
 
 // Per-call I/O block, resident on the device and refreshed before each run,
@@ -103,20 +106,69 @@ struct StepArgs {
     int nsnap, snap_every, snap_begin, snap_end;
     // receivers (tile-local lists, shared by the shots)
     const int *rec_start;
-    const RecEntry *rec;
+    const RecEntryT<T> *rec;
     // injection (sources: per shot and tile; residuals: per tile)
     const int *inj_start;
     const InjGroup *inj_grp;
-    const InjEntry *inj_ent;
+    const InjEntryT<T> *inj_ent;
     int inj_per_shot;        // 1: inj lists are indexed by shot * ntiles + tile
     int inj_kind;            // 0: value = wavelet[n]; 1: value = resid[shot][n][pt]
     const SimIO *io;
     unsigned *flags;
+    int sample;              // 1: receivers sample p^n into io->gather
+    int inj_reverse;         // 1: injection row = nt - n (adjoint sweep), rows >= nt inject 0
+    // adjoint-state imaging term Q'^n = E (p^{n+1} - p^{n-1}) - h^2 (L p^n + s^n), per cell
+    void *qslot;             // this launch's slot, field layout per shot (T, or half when q_fp16)
+    float *qscale;           // FP16 slots: power-of-two scale per [shot][tile]
+    int q_fp16;
+    T *G;                    // adjoint sweep: G += u^{n+1} Q'^n, field layout per shot
 };
+
+// Per-launch facts of one step, resolved on the host (so the kernel does no
+// integer division on them): buffer parity / gather row, snapshot index to
+// write (-1: none), snapshot index whose FP16 scale this step's output feeds
+// (-1: none), injection row (-1: none), and the imaging-term slot.
+struct StepTime {
+    int n;
+    int snap_k;
+    int max_k;
+    int inj_row;
+    void *qslot;
+    float *qscale;
+};
+
+// Step kernel modes: plain forward; forward that records Q'^n; adjoint sweep
+// that accumulates G from the recorded Q'.
+enum StepMode { kModeForward = 0, kModeRecord = 1, kModeAdjoint = 2 };
 
 // Launchers (one translation unit each).
 template <typename T>
-cudaError_t launch_step2d(const StepArgs<T> &a, int n, int nshots, cudaStream_t st);
+cudaError_t launch_step2d(const StepArgs<T> &a, int n, int nshots, int mode, cudaStream_t st);
+
+// FP32 kernel with a 128 x tz tile (tz in {8, 16, 32}).
+// pdl: let step n+1 launch while step n drains (programmatic dependent launch);
+// the kernel waits for its predecessor before reading any field.
+cudaError_t launch_step2d_f32(const StepArgs<float> &a, const StepTime &t, int tz, int nshots, int mode,
+                              cudaStream_t st, bool pdl);
+cudaError_t configure_step2d_f32();
+
+// Checkpoint of one state (computational grid of each shot): FP32/FP64 copy
+// or FP16 with a power-of-two scale per 2D tile.
+template <typename T>
+cudaError_t launch_store_state(const Geom &g, const T *field, void *dst, float *scale, int fp16, int nshots,
+                               long long shot_stride, int ntx, int ntz, cudaStream_t st);
+template <typename T>
+cudaError_t launch_load_state(const Geom &g, T *field, const void *src, const float *scale, int fp16, int nshots,
+                              long long shot_stride, int ntx, int ntz, cudaStream_t st);
+// res = g - d (all shots), per-block partial sums of res^2 / 2 into part.
+template <typename T>
+cudaError_t launch_residual(const T *g, const T *d, T *res, long long n, double *part, int nblocks, cudaStream_t st);
+// acc[interior] += sum over shots and replicated padding cells of -2 G / (v h^2).
+template <typename T>
+cudaError_t launch_fold_gradient(const Geom &g, const T *G, long long gshot, int nshots, const T *vpad,
+                                 double inv_h2, double *acc, cudaStream_t st);
+template <typename T>
+cudaError_t launch_add_gradient(const double *acc, T *grad, long long n, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_setup_model(const Geom &g, const T *vel, T *ch, T *vpad, double dt_over_h,
