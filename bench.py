@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c2x32"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c2x32", "c5"])
     ap.add_argument("--nt", type=int, default=0, help="override nt (profiling runs only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -51,6 +51,8 @@ def dist_env():
 
 def workload(args):
     import synth
+    if args.workload == "c5":
+        return synth.config_c5(nt=args.nt or 2500), 1
     nt = args.nt or 8000
     cfg = synth.config_c2(nt=nt)
     nshots = 32 if args.workload == "c2x32" else 1
@@ -62,7 +64,8 @@ def workload(args):
 
 def padded_cells(cfg):
     nb = cfg["nb"]
-    return (nb[0] + cfg["nz"] + nb[1]) * (nb[4] + cfg["nx"] + nb[5])
+    ny = (nb[2] + cfg["ny"] + nb[3]) if cfg["ndim"] == 3 else 1
+    return (nb[0] + cfg["nz"] + nb[1]) * ny * (nb[4] + cfg["nx"] + nb[5])
 
 
 def algorithmic_bytes_per_launch(cfg, nshots):
@@ -72,18 +75,33 @@ def algorithmic_bytes_per_launch(cfg, nshots):
     snapshot steps (averaged over the launches)."""
     nb = cfg["nb"]
     NZ = nb[0] + cfg["nz"] + nb[1]
+    NY = nb[2] + cfg["ny"] + nb[3] if cfg["ndim"] == 3 else 1
     NX = nb[4] + cfg["nx"] + nb[5]
-    cells = NZ * NX
+    cells = NZ * NY * NX
     strip = 0
     if cfg.get("bc") == "cpml":
-        strip = (nb[4] + nb[5]) * NZ + (nb[0] + nb[1]) * NX
+        strip = (nb[4] + nb[5]) * NZ * NY + (nb[0] + nb[1]) * NX * NY
+        if cfg["ndim"] == 3:
+            strip += (nb[2] + nb[3]) * NZ * NX
     rec = len(cfg["rec"]) * 4
     nsnap = 0
     if cfg.get("snap_every", 0) > 0:
         end = min(cfg["snap_end"], cfg["nt"])
         nsnap = (end - cfg["snap_begin"] + cfg["snap_every"] - 1) // cfg["snap_every"]
-    snap = nsnap * cfg["nz"] * cfg["nx"] * 4 / cfg["nt"]
+    snap = nsnap * cfg["nz"] * cfg.get("ny", 1) * cfg["nx"] * 4 / cfg["nt"]
     return nshots * (16 * cells + 16 * strip + rec + snap)
+
+
+def launches_per_solve(cfg, nsnap):
+    """Kernels of ours one solve launches: the fused step kernel per step in 2D;
+    in 3D the z-march plus, per step, receiver sampling, source injection and
+    two CPML kernels per absorbing axis, plus snapshot kernels; plus the final
+    finite-value check."""
+    if cfg["ndim"] == 2:
+        return cfg["nt"] + 1
+    nb = cfg["nb"]
+    axes = sum(1 for a in range(3) if nb[2 * a] + nb[2 * a + 1] > 0) if cfg.get("bc") == "cpml" else 0
+    return cfg["nt"] * (1 + 2 * axes + 2) + nsnap + 1
 
 
 class Clocks:
@@ -247,7 +265,8 @@ def run_ours(args):
     vel_d = torch.as_tensor(cfg["vel"], device=dev)
     wav_d = torch.as_tensor(cfg["wavelet"], device=dev)
     gather_d = torch.empty((nshots, nt, len(rec)), dtype=torch.float32, device=dev)
-    snaps_d = torch.empty((nshots, nsnap, cfg["nz"], cfg["nx"]), dtype=torch.float32, device=dev) if nsnap else None
+    ishape = (cfg["nz"], cfg["ny"], cfg["nx"]) if cfg["ndim"] == 3 else (cfg["nz"], cfg["nx"])
+    snaps_d = torch.empty((nshots, nsnap) + ishape, dtype=torch.float32, device=dev) if nsnap else None
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def solve():
@@ -284,9 +303,10 @@ def run_ours(args):
     algo = algorithmic_bytes_per_launch(cfg, nshots)
     peak, peak_kind = read_peaks()
     achieved = algo / per_launch_s / 1e9
-    key = "step2d_%s" % args.workload
+    key = "step_%s" % args.workload
+    kfile, kname = ("fwd3d.cu", "k_step3d") if cfg["ndim"] == 3 else ("fwd2d_f32.cu", "k_step2d_f32")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": ncu_traffic("fwd2d.cu", key), "kernel": "k_step2d",
+            "traffic": ncu_traffic(kfile, key), "kernel": kname,
             "peak_kind": peak_kind + " (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind,
             "algorithmic_bytes_per_launch": algo, "avg_launch_us": per_launch_s * 1e6}
 
@@ -296,7 +316,7 @@ def run_ours(args):
         vel_h = torch.as_tensor(cfg["vel"]).pin_memory()
         wav_h = torch.as_tensor(cfg["wavelet"]).pin_memory()
         gather_h = torch.empty((nshots, nt, len(rec)), dtype=torch.float32).pin_memory()
-        snaps_h = torch.empty((nshots, nsnap, cfg["nz"], cfg["nx"]), dtype=torch.float32).pin_memory() if nsnap else None
+        snaps_h = torch.empty((nshots, nsnap) + ishape, dtype=torch.float32).pin_memory() if nsnap else None
         for _ in range(max(1, min(2, args.warmup))):
             pkg.sim_set_model(sim.handle, vel_h)
             pkg.sim_forward(sim.handle, nshots, wav_h, src, len(rec), rec, gather_h, snaps_h, None)
@@ -326,14 +346,17 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "Gcell/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": ("c2: 2D slice 619x1000 (+50-cell CPML left/right/bottom, free top), "
-                                        "nt=%d, %d receivers, %d FP32 snapshots, %d shot(s) per GPU"
-                                        % (nt, len(rec), nsnap, nshots)),
+                "config": {"workload": (("c5: 3D volume 619x1000x1000 (+30-cell CPML on x, y, bottom, free top), "
+                                         "dt=0.8 ms, nt=%d, %d receivers, %d shot(s) per GPU" % (nt, len(rec), nshots))
+                                        if cfg["ndim"] == 3 else
+                                        ("c2: 2D slice 619x1000 (+50-cell CPML left/right/bottom, free top), "
+                                         "nt=%d, %d receivers, %d FP32 snapshots, %d shot(s) per GPU"
+                                         % (nt, len(rec), nsnap, nshots))),
                            "padded_cells": cells, "l2": "flushed between timed solves (%d MB write)" %
                                                         (L2_FLUSH_BYTES >> 20),
                            "parallelism": "replicas x%d" % world},
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(), "e2e": e2e,
-                "gpu_launches": args.steps * (nt + 1)}
+                "gpu_launches": args.steps * launches_per_solve(cfg, nsnap)}
         print(json.dumps(line), flush=True)
     sim.close()
     if dist:

@@ -1,0 +1,408 @@
+// 3D time step of the acoustic scheme (FP32).
+//
+// Main kernel: a z-march over (x, y) tiles (2.5D blocking). A CTA of 8 warps
+// owns a 128 x TY column of the grid (TY = 8 RY); each lane owns 4
+// consecutive x cells in RY y-rows and keeps the 9 planes z-4 .. z+4 of those
+// cells in a register queue, so p^n is read from memory once per cell for the
+// z-derivative. The current plane with its radius-4 x/y halo is staged into a
+// double-buffered shared-memory tile by cp.async one plane ahead of use. The
+// update is the leapfrog step with the centred sponge term (Eq. cerjan_pde),
+// the free-surface plane z = 0 held at zero with an odd mirror above it
+// (Eq. free_surface), and no boundary arithmetic outside absorbing tiles.
+//
+// Side kernels of a step touch only small parts of the grid: the CPML memory
+// terms (psi before the update, zeta and the D1 psi + zeta addend after it,
+// strips only), point injection of the source, trilinear receiver sampling
+// and snapshot output.
+#include <cfloat>
+
+#include "sim_internal.h"
+#include "stencil.cuh"
+
+namespace gsim {
+namespace {
+
+constexpr int TX = kTileXF, NW = 8, NTH = NW * 32, SW3 = TX + 8;
+
+__device__ __forceinline__ float lane4(const float4 &v, int k) {
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void cp16(void *smem, const void *gmem) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <int RY>
+__global__ void __launch_bounds__(NTH, 2) k_step3d(const StepArgs<float> A, const int n, const int zchunk) {
+    constexpr int TY = NW * RY, NR = TY + 8;  // staged rows per plane
+    extern __shared__ float4 sm3[];
+    float *buf[2] = {reinterpret_cast<float *>(sm3), reinterpret_cast<float *>(sm3) + NR * SW3};
+
+    const Geom &g = A.g;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int nchunk = (g.NZ + zchunk - 1) / zchunk;
+    const int shot = blockIdx.z / nchunk, zb = (blockIdx.z % nchunk) * zchunk;
+    const int ze = min(zb + zchunk, g.NZ);
+    const long long PP = (long long)g.PY * g.P;  // plane pitch
+    const long long sh = (long long)shot * g.fstride;
+    const float *pc = A.pbuf[n & 1] + sh;
+    float *pn = A.pbuf[(n + 1) & 1] + sh;
+    const int gx0 = x0 + 4 * lane;
+    const bool xedge = x0 + TX > g.NX;
+    const bool spg = A.bc == SIM_BC_SPONGE &&
+                     ((g.nbx0 > 0 && x0 < g.nbx0) || (g.nbx1 > 0 && x0 + TX > g.NX - g.nbx1) ||
+                      (g.nby0 > 0 && y0 < g.nby0) || (g.nby1 > 0 && y0 + TY > g.NY - g.nby1) || g.nbz0 > 0 ||
+                      g.nbz1 > 0);
+    float4 Ex4 = make_float4(0, 0, 0, 0);
+    float Ey[RY];
+#pragma unroll
+    for (int r = 0; r < RY; r++) Ey[r] = 0.f;
+    if (spg) {
+        Ex4 = __ldg(reinterpret_cast<const float4 *>(A.E[2] + gx0));
+#pragma unroll
+        for (int r = 0; r < RY; r++) Ey[r] = __ldg(A.E[1] + y0 + w * RY + r);
+    }
+    // offset of (z = 0, y0 + w RY, gx0) and of the staged plane's corner
+    const long long own0 = cell_off(g, 0, y0 + w * RY, gx0);
+    const long long halo0 = cell_off(g, 0, y0 - 4, x0 - 4);
+
+    cudaGridDependencySynchronize();
+
+    // register queue: planes z-4 .. z+4 of this thread's cells
+    float4 q[9][RY];
+    auto load_plane = [&](int z, int r) -> float4 {
+        if (z < 0) {
+            if (!g.fs) return make_float4(0, 0, 0, 0);
+            const float4 v = *reinterpret_cast<const float4 *>(pc + own0 + (long long)(-z) * PP + r * g.P);
+            return make_float4(-v.x, -v.y, -v.z, -v.w);
+        }
+        return *reinterpret_cast<const float4 *>(pc + own0 + (long long)z * PP + r * g.P);
+    };
+#pragma unroll
+    for (int k = 0; k < 8; k++)
+#pragma unroll
+        for (int r = 0; r < RY; r++) q[k + 1][r] = load_plane(zb - 4 + k, r);
+
+    auto stage = [&](int z, float *dst) {  // plane z with its x/y halo
+        const float *src = pc + halo0 + (long long)z * PP;
+        for (int rr = w; rr < NR; rr += NW) {
+            cp16(dst + rr * SW3 + 4 * lane, src + rr * g.P + 4 * lane);
+            if (lane < 2) cp16(dst + rr * SW3 + 128 + 4 * lane, src + rr * g.P + 128 + 4 * lane);
+        }
+        cp_commit();
+    };
+    stage(zb, buf[0]);
+
+    for (int z = zb; z < ze; z++) {
+        float *cur = buf[(z - zb) & 1];
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+#pragma unroll
+            for (int r = 0; r < RY; r++) q[k][r] = q[k + 1][r];
+#pragma unroll
+        for (int r = 0; r < RY; r++) q[8][r] = load_plane(z + 4, r);
+        float4 pp4[RY], ch4[RY];
+#pragma unroll
+        for (int r = 0; r < RY; r++) {
+            const long long o = own0 + (long long)z * PP + r * g.P;
+            pp4[r] = *reinterpret_cast<const float4 *>(pn + o);
+            ch4[r] = __ldg(reinterpret_cast<const float4 *>(A.ch + o));
+        }
+        if (z + 1 < ze) {
+            stage(z + 1, buf[(z + 1 - zb) & 1]);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        __syncthreads();
+        const float ez = spg ? __ldg(A.E[0] + z) : 0.f;
+#pragma unroll
+        for (int r = 0; r < RY; r++) {
+            const int ly = w * RY + r, gy = y0 + ly;
+            const float *row = cur + (ly + 4) * SW3 + 4 + 4 * lane;  // this thread's float4 in the staged plane
+            const float4 L = *reinterpret_cast<const float4 *>(row - 4), C = *reinterpret_cast<const float4 *>(row),
+                         R = *reinterpret_cast<const float4 *>(row + 4);
+            const float v[12] = {L.x, L.y, L.z, L.w, C.x, C.y, C.z, C.w, R.x, R.y, R.z, R.w};
+            float4 yv[9];
+#pragma unroll
+            for (int m = 0; m < 9; m++) yv[m] = *reinterpret_cast<const float4 *>(row + (m - 4) * SW3);
+            float res[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const float p = v[4 + k];
+                const float d2x = float(kC0) * p + float(kC1) * (v[5 + k] + v[3 + k]) +
+                                  float(kC2) * (v[6 + k] + v[2 + k]) + float(kC3) * (v[7 + k] + v[1 + k]) +
+                                  float(kC4) * (v[8 + k] + v[k]);
+                const float d2y = float(kC0) * p + float(kC1) * (lane4(yv[5], k) + lane4(yv[3], k)) +
+                                  float(kC2) * (lane4(yv[6], k) + lane4(yv[2], k)) +
+                                  float(kC3) * (lane4(yv[7], k) + lane4(yv[1], k)) +
+                                  float(kC4) * (lane4(yv[8], k) + lane4(yv[0], k));
+                const float d2z = float(kC0) * p + float(kC1) * (lane4(q[5][r], k) + lane4(q[3][r], k)) +
+                                  float(kC2) * (lane4(q[6][r], k) + lane4(q[2][r], k)) +
+                                  float(kC3) * (lane4(q[7][r], k) + lane4(q[1][r], k)) +
+                                  float(kC4) * (lane4(q[8][r], k) + lane4(q[0][r], k));
+                const float rhs = d2x + d2y + d2z;
+                const float chv = lane4(ch4[r], k), pp = lane4(pp4[r], k);
+                float out;
+                if (spg) {
+                    const float a = chv * (ez + Ey[r] + lane4(Ex4, k));
+                    out = (2.f * p - (1.f - a) * pp + chv * rhs) / (1.f + a);
+                } else {
+                    out = 2.f * p - pp + chv * rhs;
+                }
+                res[k] = out;
+            }
+            if (xedge) {
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if (gx0 + k >= g.NX) res[k] = 0.f;
+            }
+            if (g.fs && z == 0) res[0] = res[1] = res[2] = res[3] = 0.f;
+            if (gy < g.NY)
+                *reinterpret_cast<float4 *>(pn + own0 + (long long)z * PP + r * g.P) =
+                    make_float4(res[0], res[1], res[2], res[3]);
+        }
+        __syncthreads();  // the buffer just used is restaged two planes later
+    }
+}
+
+// ---------------------------------------------------------------- CPML (3D)
+// psi^n = b psi^{n-1} + a D1 p^n on the cells of one axis' strips.
+__device__ __forceinline__ long long axis_stride(const Geom &g, int ax) {
+    return ax == 0 ? (long long)g.PY * g.P : (ax == 1 ? (long long)g.P : 1LL);
+}
+
+struct Box {
+    int z0, z1, y0, y1, x0, x1;
+};
+
+__device__ __forceinline__ bool box_cell(const Box &b, long long i, int &z, int &y, int &x) {
+    const int nx = b.x1 - b.x0, ny = b.y1 - b.y0;
+    const long long nzy = i / nx;
+    x = b.x0 + (int)(i - nzy * nx);
+    y = b.y0 + (int)(nzy % ny);
+    z = b.z0 + (int)(nzy / ny);
+    return z < b.z1;
+}
+
+__global__ void k_psi3d(const StepArgs<float> A, const int n, const int ax, const Box b0, const Box b1) {
+    const Geom &g = A.g;
+    const long long s = axis_stride(g, ax);
+    const long long n0 = (long long)(b0.z1 - b0.z0) * (b0.y1 - b0.y0) * (b0.x1 - b0.x0);
+    const long long n1 = (long long)(b1.z1 - b1.z0) * (b1.y1 - b1.y0) * (b1.x1 - b1.x0);
+    const int shot = blockIdx.y;
+    const long long sh = (long long)shot * g.fstride;
+    const float *p = A.pbuf[n & 1] + sh;
+    float *psi = A.psi[ax][0] + sh;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n0 + n1;
+         i += (long long)gridDim.x * blockDim.x) {
+        int z, y, x;
+        if (i < n0) box_cell(b0, i, z, y, x);
+        else box_cell(b1, i - n0, z, y, x);
+        const long long o = cell_off(g, z, y, x);
+        const int k = ax == 0 ? z : (ax == 1 ? y : x);
+        psi[o] = A.cb[ax][k] * psi[o] + A.ca[ax][k] * d1_row(p + o, (int)s);
+    }
+}
+
+// zeta^n = b zeta^{n-1} + a (D2 p^n + D1 psi^n); p^{n+1} += c (D1 psi^n + zeta^n)
+// on the strips of one axis widened by 4 cells (where D1 psi is non-zero).
+__global__ void k_cpml_add3d(const StepArgs<float> A, const int n, const int ax, const Box b0, const Box b1) {
+    const Geom &g = A.g;
+    const long long s = axis_stride(g, ax);
+    const long long n0 = (long long)(b0.z1 - b0.z0) * (b0.y1 - b0.y0) * (b0.x1 - b0.x0);
+    const long long n1 = (long long)(b1.z1 - b1.z0) * (b1.y1 - b1.y0) * (b1.x1 - b1.x0);
+    const int shot = blockIdx.y;
+    const long long sh = (long long)shot * g.fstride;
+    const float *p = A.pbuf[n & 1] + sh;
+    float *pn = A.pbuf[(n + 1) & 1] + sh;
+    const float *psi = A.psi[ax][0] + sh;
+    float *zeta = A.zeta[ax] + sh;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n0 + n1;
+         i += (long long)gridDim.x * blockDim.x) {
+        int z, y, x;
+        if (i < n0) box_cell(b0, i, z, y, x);
+        else box_cell(b1, i - n0, z, y, x);
+        if (g.fs && z == 0) continue;
+        const long long o = cell_off(g, z, y, x);
+        const int k = ax == 0 ? z : (ax == 1 ? y : x);
+        // D2 along the axis with the free-surface mirror for z-derivatives near the top
+        float d2;
+        if (ax == 0 && g.fs && z < 4) {
+            float c[9];
+            for (int m = -4; m <= 4; m++) {
+                const int zz = z + m;
+                c[m + 4] = zz < 0 ? -p[cell_off(g, -zz, y, x)] : p[cell_off(g, zz, y, x)];
+            }
+            d2 = float(kC0) * c[4] + float(kC1) * (c[5] + c[3]) + float(kC2) * (c[6] + c[2]) +
+                 float(kC3) * (c[7] + c[1]) + float(kC4) * (c[8] + c[0]);
+        } else {
+            d2 = d2_col(p + o, (int)s);
+        }
+        const float dps = d1_row(psi + o, (int)s);
+        const float zt = A.cb[ax][k] * zeta[o] + A.ca[ax][k] * (d2 + dps);
+        zeta[o] = zt;
+        pn[o] += A.ch[o] * (dps + zt);
+    }
+}
+
+// ---------------------------------------------------------------- points (3D)
+
+// p^{n+1} += c w[n] weight / h / (1 + a) at each source corner (one thread per shot and corner)
+__global__ void k_inject3d(const StepArgs<float> A, const StepTime t, const Pt3 *src, int nshots) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 8 * nshots || t.inj_row < 0) return;
+    const int shot = i >> 3, c = i & 7;
+    const Pt3 P = src[shot];
+    const long long o = P.cell[c];
+    if (o < 0) return;
+    const Geom &g = A.g;
+    float *pn = A.pbuf[(t.n + 1) & 1] + (long long)shot * g.fstride;
+    const float w = static_cast<const float *>(A.io->wavelet)[t.inj_row];
+    float a = 0.f;
+    if (A.bc == SIM_BC_SPONGE) {
+        const long long r = o - g.org;
+        const long long PP = (long long)g.PY * g.P;
+        const int z = (int)(r / PP), y = (int)((r % PP) / g.P), x = (int)(r % g.P);
+        a = A.ch[o] * (A.E[0][z] + A.E[1][y] + A.E[2][x]);
+    }
+    pn[o] += A.ch[o] * A.src_scale * P.w[c] * w / (1.f + a);
+}
+
+__global__ void k_sample3d(const StepArgs<float> A, const StepTime t, const Pt3 *rec, int nrec, int nshots) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)nrec * nshots) return;
+    const int shot = (int)(i / nrec), r = (int)(i % nrec);
+    const Pt3 P = rec[r];
+    const float *p = A.pbuf[t.n & 1] + (long long)shot * A.g.fstride;
+    float v = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; c++)
+        if (P.cell[c] >= 0) v += P.w[c] * p[P.cell[c]];
+    static_cast<float *>(A.io->gather)[((long long)shot * A.nt + t.n) * nrec + r] = v;
+    if (!isfinite(v)) atomicOr(A.flags, kFlagUnstable);
+}
+
+// interior of p^n into the snapshot stack (FP32), or its max |p| (FP16 pass 1)
+__global__ void k_snap3d(const StepArgs<float> A, const StepTime t, int pass) {
+    const Geom &g = A.g;
+    const int shot = blockIdx.y;
+    const float *p = A.pbuf[t.n & 1] + (long long)shot * g.fstride;
+    const long long nint = (long long)g.nz * g.ny * g.nx;
+    const SimIO *io = A.io;
+    const long long base = ((long long)shot * A.nsnap + t.snap_k) * nint;
+    const float s = (pass == 2) ? pow2_scale(__uint_as_float(io->snap_max[shot * A.nsnap + t.snap_k])) : 1.f;
+    float m = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nint; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.nx);
+        const long long zy = i / g.nx;
+        const int y = (int)(zy % g.ny), z = (int)(zy / g.ny);
+        const float v = p[cell_off(g, z + g.oz, y + g.oy, x + g.ox)];
+        if (pass == 0) static_cast<float *>(io->snaps)[base + i] = v;
+        else if (pass == 1) m = fmaxf(m, fabsf(v));
+        else static_cast<__half *>(io->snaps)[base + i] = __float2half_rn(v / s);
+    }
+    if (pass == 1) {
+        m = warp_max(m);
+        if ((threadIdx.x & 31) == 0) {
+            if (!(m <= FLT_MAX)) atomicOr(A.flags, kFlagUnstable);
+            else atomicMax(&io->snap_max[shot * A.nsnap + t.snap_k], __float_as_uint(m));
+        }
+    }
+    if (pass == 2 && blockIdx.x == 0 && threadIdx.x == 0) io->snap_scale[shot * A.nsnap + t.snap_k] = s;
+}
+
+template <int RY>
+size_t smem3d() {
+    return 2 * (size_t)(NW * RY + 8) * SW3 * sizeof(float);
+}
+
+}  // namespace
+
+cudaError_t configure_step3d() {
+    cudaError_t e = cudaFuncSetAttribute(k_step3d<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3d<1>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step3d<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3d<2>());
+    return e;
+}
+
+cudaError_t launch_step3d(const StepArgs<float> &a, int n, int ry, int zchunk, int nshots, cudaStream_t st,
+                          bool pdl) {
+    const int nchunk = (a.g.NZ + zchunk - 1) / zchunk;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.ntx, (a.g.NY + NW * ry - 1) / (NW * ry), nchunk * nshots);
+    cfg.blockDim = dim3(NTH);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    if (ry == 1) {
+        cfg.dynamicSmemBytes = smem3d<1>();
+        return cudaLaunchKernelEx(&cfg, k_step3d<1>, a, n, zchunk);
+    }
+    cfg.dynamicSmemBytes = smem3d<2>();
+    return cudaLaunchKernelEx(&cfg, k_step3d<2>, a, n, zchunk);
+}
+
+// CPML side kernels for one axis: boxes = the two strips (psi) or the two
+// strips widened by 4 cells along the axis (zeta and the update addend).
+cudaError_t launch_cpml3d(const StepArgs<float> &a, int n, int ax, int phase, int nshots, cudaStream_t st) {
+    const Geom &g = a.g;
+    const int N[3] = {g.NZ, g.NY, g.NX};
+    const int lo[3] = {g.nbz0, g.nby0, g.nbx0}, hi[3] = {g.nbz1, g.nby1, g.nbx1};
+    const int widen = phase == 0 ? 0 : 4;
+    int a0 = 0, a1 = lo[ax] > 0 ? std::min(N[ax], lo[ax] + widen) : 0;
+    int b0 = hi[ax] > 0 ? std::max(0, N[ax] - hi[ax] - widen) : N[ax], b1 = N[ax];
+    if (a1 > b0) {  // strips meet: one box
+        a1 = b1;
+        b0 = b1;
+    }
+    Box B0{0, g.NZ, 0, g.NY, 0, g.NX}, B1 = B0;
+    auto set = [&](Box &b, int s0, int s1) {
+        if (ax == 0) { b.z0 = s0; b.z1 = s1; }
+        else if (ax == 1) { b.y0 = s0; b.y1 = s1; }
+        else { b.x0 = s0; b.x1 = s1; }
+    };
+    set(B0, a0, a1);
+    set(B1, b0, b1);
+    const long long cells = (long long)(B0.z1 - B0.z0) * (B0.y1 - B0.y0) * (B0.x1 - B0.x0) +
+                            (long long)(B1.z1 - B1.z0) * (B1.y1 - B1.y0) * (B1.x1 - B1.x0);
+    if (cells <= 0) return cudaSuccess;
+    const int blocks = (int)std::min<long long>((cells + 255) / 256, 152 * 16);
+    if (phase == 0) k_psi3d<<<dim3(blocks, nshots), 256, 0, st>>>(a, n, ax, B0, B1);
+    else k_cpml_add3d<<<dim3(blocks, nshots), 256, 0, st>>>(a, n, ax, B0, B1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample3d(const StepArgs<float> &a, const StepTime &t, const void *rec, int nrec, int nshots,
+                            cudaStream_t st) {
+    if (!rec || nrec <= 0) return cudaSuccess;
+    const long long tot = (long long)nrec * nshots;
+    k_sample3d<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(a, t, static_cast<const Pt3 *>(rec), nrec, nshots);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject3d(const StepArgs<float> &a, const StepTime &t, const void *src, int nshots,
+                            cudaStream_t st) {
+    if (!src || nshots <= 0) return cudaSuccess;
+    k_inject3d<<<(8 * nshots + 63) / 64, 64, 0, st>>>(a, t, static_cast<const Pt3 *>(src), nshots);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_snap3d(const StepArgs<float> &a, const StepTime &t, int fp16, int nshots, cudaStream_t st) {
+    if (fp16) {
+        k_snap3d<<<dim3(608, nshots), 256, 0, st>>>(a, t, 1);
+        k_snap3d<<<dim3(608, nshots), 256, 0, st>>>(a, t, 2);
+    } else {
+        k_snap3d<<<dim3(608, nshots), 256, 0, st>>>(a, t, 0);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gsim

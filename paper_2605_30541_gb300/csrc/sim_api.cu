@@ -233,6 +233,8 @@ struct sim_s {
     std::vector<std::pair<long long, cudaGraphExec_t>> graphs;
     bool use_graphs = true;
     int tuned_nshots = 0;  // shot count the tile shape was tuned for (0: not yet)
+    Pt3 *src3 = nullptr, *rec3 = nullptr;  // 3D point tables
+    int zchunk = 0;                        // z-march chunk of the 3D kernel
     // adjoint-state buffers, allocated by the first sim_adjoint call
     bool adj_ready = false;
     int seg = 0, nseg = 0;
@@ -726,13 +728,102 @@ sim_status autotune(sim_t s, int nshots) {
     return SIM_OK;
 }
 
+// 3D points: the 8 trilinear corners of each point as field offsets.
+sim_status points3d(sim_t s, int npts, const double *pos, std::vector<Pt3> &out, bool drop_surface,
+                    const char *what) {
+    const Geom &g = s->g;
+    out.resize(npts);
+    for (int q = 0; q < npts; q++) {
+        int i0[3];
+        double t[3];
+        if (!locate(g, s->d.h, pos + (size_t)q * 3, i0, t))
+            return s->fail(SIM_ERR_ARG, "%s %d lies outside the interior", what, q);
+        Pt3 &P = out[q];
+        int k = 0;
+        for (int dz = 0; dz < 2; dz++)
+            for (int dy = 0; dy < 2; dy++)
+                for (int dx = 0; dx < 2; dx++, k++) {
+                    const double w = corner_weight(t, dz, dy, dx);
+                    const int z = i0[0] + dz;
+                    if (w == 0.0 || (drop_surface && g.fs && z == 0)) {
+                        P.cell[k] = -1;
+                        P.w[k] = 0.f;
+                        continue;
+                    }
+                    P.cell[k] = cell_off(g, z, i0[1] + dy, i0[2] + dx);
+                    P.w[k] = (float)w;
+                }
+    }
+    return SIM_OK;
+}
+
+sim_status forward3d(sim_t s, int nshots, const void *wav, const double *src_pos, int nrec, const double *rec_pos,
+                     void *gdev, void *sdev, float *scdev) {
+    const sim_desc &d = s->d;
+    const Geom &g = s->g;
+    if (d.precision != SIM_FP32) return s->fail(SIM_ERR_UNSUPPORTED, "the 3D path runs in FP32");
+    std::vector<Pt3> src, rec;
+    if (wav)
+        if (sim_status r = points3d(s, nshots, src_pos, src, true, "source")) return r;
+    if (sim_status r = points3d(s, nrec, rec_pos, rec, false, "receiver")) return r;
+    if (!src.empty())
+        if (sim_status r = s->cuda(cudaMemcpyAsync(s->src3, src.data(), src.size() * sizeof(Pt3),
+                                                   cudaMemcpyHostToDevice, s->st), "source upload"))
+            return r;
+    if (!rec.empty())
+        if (sim_status r = s->cuda(cudaMemcpyAsync(s->rec3, rec.data(), rec.size() * sizeof(Pt3),
+                                                   cudaMemcpyHostToDevice, s->st), "receiver upload"))
+            return r;
+    SimIO io{};
+    io.wavelet = wav;
+    io.gather = nrec > 0 ? gdev : nullptr;
+    io.snaps = s->nsnap > 0 ? sdev : nullptr;
+    io.snap_scale = scdev;
+    io.snap_max = s->snap_max;
+    io.nrec = nrec;
+    io.nshots = nshots;
+    io.snap_fp16 = d.snap_fp16;
+    if (sim_status r = s->cuda(cudaMemcpyAsync(s->io, &io, sizeof io, cudaMemcpyHostToDevice, s->st), "io upload"))
+        return r;
+    if (sim_status r = reset_state(s, nshots)) return r;
+    StepArgs<float> a = step_args<float>(s);
+    a.inj_per_shot = 1;
+    a.inj_kind = 0;
+    a.sample = nrec > 0 && gdev != nullptr;
+    // z-chunks: enough CTAs for two per SM, at least 64 planes per chunk
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->dev);
+    const long long cols = (long long)s->ntx * ((g.NY + 7) / 8) * nshots;
+    int chunks = (int)std::max<long long>(1, std::min<long long>((2LL * sms + cols - 1) / cols, g.NZ / 64));
+    s->zchunk = (g.NZ + chunks - 1) / chunks;
+    const bool cpml = d.bc == SIM_BC_CPML;
+    const int on[3] = {s->psi[0][0] != nullptr, s->psi[1][0] != nullptr, s->psi[2][0] != nullptr};
+    const bool has_src = !src.empty(), has_snap = io.snaps != nullptr;
+    const Pt3 *s3 = s->src3, *r3 = s->rec3;
+    return run_graph(s, ((long long)nshots << 8) | (3 << 2) | 2, [&](cudaStream_t st) {
+        cudaError_t e = cudaSuccess;
+        for (int n = 0; n < d.nt && e == cudaSuccess; n++) {
+            const StepTime t = step_time(s, a, n, kModeForward, nullptr, nullptr);
+            if (has_snap && t.snap_k >= 0) e = launch_snap3d(a, t, d.snap_fp16, nshots, st);
+            if (e == cudaSuccess && a.sample) e = launch_sample3d(a, t, r3, nrec, nshots, st);
+            for (int ax = 0; ax < 3 && cpml && e == cudaSuccess; ax++)
+                if (on[ax]) e = launch_cpml3d(a, n, ax, 0, nshots, st);
+            if (e == cudaSuccess) e = launch_step3d(a, n, 1, s->zchunk, nshots, st, false);
+            for (int ax = 0; ax < 3 && cpml && e == cudaSuccess; ax++)
+                if (on[ax]) e = launch_cpml3d(a, n, ax, 1, nshots, st);
+            if (e == cudaSuccess && has_src) e = launch_inject3d(a, t, s3, nshots, st);
+        }
+        return e;
+    });
+}
+
 template <typename T>
 sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src_pos, int nrec,
                      const double *rec_pos, void *gather, void *snaps, float *snap_scale) {
     const sim_desc &d = s->d;
     const Geom &g = s->g;
-    if (g.ndim != 2) return s->fail(SIM_ERR_UNSUPPORTED, "3D forward is not built yet");
-    if (sim_status r = autotune(s, nshots)) return r;
+    if (g.ndim == 2)
+        if (sim_status r = autotune(s, nshots)) return r;
     const size_t nt = d.nt;
     // inputs
     const void *wav = wavelet;
@@ -764,6 +855,9 @@ sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src
     if (d.snap_fp16 && snaps && s->nsnap > 0 && !snap_scale)
         return s->fail(SIM_ERR_ARG, "FP16 snapshots need a snap_scale array");
 
+    if (g.ndim == 3) {
+        if (sim_status r = forward3d(s, nshots, wav, src_pos, nrec, rec_pos, gdev, sdev, scdev)) return r;
+    } else {
     // geometry lists
     std::vector<int> rstart, istart;
     std::vector<RecEntryT<T>> rent;
@@ -806,9 +900,10 @@ sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src
             return cudaSuccess;
         }))
         return r;
+    }
     // the buffer written last holds p^nt
-    if (sim_status r = s->cuda(launch_check_finite<T>(g, static_cast<const T *>(a.pbuf[d.nt & 1]), nshots, s->flags,
-                                                      s->st), "finite check"))
+    const T *last = static_cast<const T *>(s->pbuf) + ((d.nt & 1) ? (long long)d.max_shots * g.fstride : 0);
+    if (sim_status r = s->cuda(launch_check_finite<T>(g, last, nshots, s->flags, s->st), "finite check"))
         return r;
     if (sim_status r = s->cuda(cudaMemcpyAsync(s->flags_host, s->flags, sizeof(unsigned), cudaMemcpyDeviceToHost,
                                                s->st), "flag readback"))
@@ -1159,6 +1254,11 @@ sim_status sim_create(const sim_desc *din, const void *vel, void *cuda_stream, s
     if (rc == SIM_OK) rc = s->cuda(cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming), "event");
     if (rc == SIM_OK) rc = s->cuda(cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming), "event");
     if (rc == SIM_OK && d.precision == SIM_FP32) rc = s->cuda(configure_step2d_f32(), "kernel configuration");
+    if (rc == SIM_OK && d.ndim == 3) {
+        rc = s->cuda(configure_step3d(), "kernel configuration");
+        s->src3 = static_cast<Pt3 *>(A(sizeof(Pt3) * ms));
+        s->rec3 = static_cast<Pt3 *>(A(sizeof(Pt3) * std::max(1, d.max_rec)));
+    }
     if (rc == SIM_OK && cudaMallocHost(&s->flags_host, sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
         rc = s->fail(SIM_ERR_OOM, "pinned host allocation failed");

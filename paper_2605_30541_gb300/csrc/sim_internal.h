@@ -141,6 +141,25 @@ struct StepTime {
 // that accumulates G from the recorded Q'.
 enum StepMode { kModeForward = 0, kModeRecord = 1, kModeAdjoint = 2 };
 
+// A point of the 3D path: field offsets of its 8 trilinear corners (-1 where
+// the weight is zero or the corner is a held free-surface cell) and weights.
+struct Pt3 {
+    long long cell[8];
+    float w[8];
+};
+
+// 3D launchers (fwd3d.cu). Per step: snapshot, sample, CPML psi, z-march
+// update, CPML zeta + addend, source injection.
+cudaError_t configure_step3d();
+cudaError_t launch_step3d(const StepArgs<float> &a, int n, int ry, int zchunk, int nshots, cudaStream_t st,
+                          bool pdl);
+cudaError_t launch_cpml3d(const StepArgs<float> &a, int n, int ax, int phase, int nshots, cudaStream_t st);
+cudaError_t launch_sample3d(const StepArgs<float> &a, const StepTime &t, const void *rec, int nrec, int nshots,
+                            cudaStream_t st);
+cudaError_t launch_inject3d(const StepArgs<float> &a, const StepTime &t, const void *src, int nshots,
+                            cudaStream_t st);
+cudaError_t launch_snap3d(const StepArgs<float> &a, const StepTime &t, int fp16, int nshots, cudaStream_t st);
+
 // Launchers (one translation unit each).
 template <typename T>
 cudaError_t launch_step2d(const StepArgs<T> &a, int n, int nshots, int mode, cudaStream_t st);
