@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c2x32", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c2x32", "c3", "c5"])
     ap.add_argument("--nt", type=int, default=0, help="override nt (profiling runs only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -243,6 +243,52 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """Batched workload: every (slice, shot) of the 17-slice set in one sim_batch."""
+    import torch
+    import synth
+    import paper_2605_30541_gb300 as pkg
+    torch.cuda.set_device(0)
+    nt = args.nt or 4000
+    slices = synth.config_c3(nt=nt)
+    sims = [pkg.Simulator(c, c["vel"], max_shots=len(c["src"]), max_rec=len(c["rec"])) for c in slices]
+    cells = sum(padded_cells(c) * len(c["src"]) for c in slices)
+    gathers = [torch.empty((len(c["src"]), nt, len(c["rec"])), dtype=torch.float32, device="cuda") for c in slices]
+    entries = [dict(sim=s, wavelet=torch.as_tensor(c["wavelet"], device="cuda"), src=c["src"], rec=c["rec"],
+                    gather=g) for s, c, g in zip(sims, slices, gathers)]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        pkg.batch(entries)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(0) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            pkg.batch(entries)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    total = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    value = args.steps * nt * cells / total / 1e9
+    peak, peak_kind = read_peaks()
+    algo = sum(algorithmic_bytes_per_launch(c, len(c["src"])) for c in slices) * nt
+    line = {"metric": METRIC, "value": value, "unit": "Gcell/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c3: 64 shots on a 619x1000 slice + 16 uneven slices x 8 shots, nt=%d, "
+                                   "one persistent launch per solve" % nt, "padded_cells_x_shots": cells,
+                       "l2": "flushed between timed solves"},
+            "roofline": {"bound": "hbm", "achieved": algo / (total / args.steps) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": algo / (total / args.steps) / 1e9 / peak, "traffic": None,
+                         "kernel": "k_batch2d", "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_solve": algo},
+            "clocks": clk.summary(), "gpu_launches": args.steps}
+    print(json.dumps(line), flush=True)
+    for s in sims:
+        s.close()
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -367,6 +413,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c3":
+        run_batch(args)
     else:
         run_ours(args)
 

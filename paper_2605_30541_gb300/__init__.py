@@ -16,7 +16,7 @@ from .abi import SIM_BC, SIM_FP32, SIM_FP64, SimBatchItem, SimDesc, SimInfo
 
 __all__ = ["SimError", "make_desc", "sim_plan", "sim_create", "sim_set_model", "sim_forward",
            "sim_adjoint", "sim_batch", "sim_sync", "sim_get_info", "sim_last_error", "sim_destroy",
-           "Simulator"]
+           "Simulator", "batch"]
 
 
 class SimError(RuntimeError):
@@ -127,8 +127,32 @@ def sim_adjoint(handle, nshots, wavelet, src_pos, nrec, rec_pos, d_obs, gather_o
 
 
 def sim_batch(items, stream=None):
+    """items: sequence of SimBatchItem (see batch() for a friendlier form)."""
     arr = (SimBatchItem * len(items))(*items)
     _check(abi.load().sim_batch(len(items), arr, _stream(stream)))
+
+
+def batch(entries, stream=None):
+    """Run many shots on many grids in one persistent launch. entries: list of
+    dicts with keys sim (Simulator), wavelet, src [nshots, ndim], rec [nrec, ndim]
+    and optionally gather (output tensor [nshots, nt, nrec]; allocated if absent).
+    Returns the list of gather tensors."""
+    import torch
+    keep, items, outs = [], [], []
+    for e in entries:
+        sim = e["sim"]
+        d = sim.desc
+        src, nshots = _positions(e["src"], d.ndim)
+        rec, nrec = _positions(e["rec"], d.ndim)
+        w = sim._tensor(e["wavelet"])
+        g = e.get("gather")
+        if g is None and nrec:
+            g = torch.empty((nshots, d.nt, nrec), dtype=sim.dtype, device="cuda")
+        keep += [src, rec, w, g]
+        items.append(SimBatchItem(sim.handle, nshots, _ptr(w), _ptr(src), nrec, _ptr(rec), _ptr(g)))
+        outs.append(g)
+    sim_batch(items, stream)
+    return outs
 
 
 def sim_sync(handle):

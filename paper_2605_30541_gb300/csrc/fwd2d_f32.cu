@@ -75,20 +75,22 @@ constexpr size_t smem_floats(bool cpml) {
     return (size_t)(TZ + 2 * HM) * SW + (size_t)TZ * TX + (cpml ? (size_t)TZ * (TX + 8) + (size_t)(TZ + 8) * TX : 0);
 }
 
-template <int TZ, int MODE>
-__global__ void __launch_bounds__(NTH, 2) k_step2d_f32(const StepArgs<float> A, const StepTime t) {
+// One tile of one step: the whole CTA updates the 128 x TZ tile (bx, bz) of
+// `shot`. Shared by the per-step kernel (one tile per CTA) and the persistent
+// batch kernel (a work list of tiles). With PDL the fields of the previous
+// step are touched only after cudaGridDependencySynchronize().
+template <int TZ, int MODE, bool PDL>
+__device__ __forceinline__ void tile_step(const StepArgs<float> &A, const StepTime &t, const int bx, const int bz,
+                                          const int shot, float *S, float *red) {
     constexpr int RZ = TZ / NW;
-    extern __shared__ float4 smem4[];
-    float *S = reinterpret_cast<float *>(smem4);   // (TZ + 2 HM) x SW, tile origin at (HM, HM)
     float *INJ = S + (TZ + 2 * HM) * SW;           // TZ x TX
     float *PX = INJ + TZ * TX;                     // TZ x (TX + 8), CPML launches only
     float *PZ = PX + TZ * (TX + 8);                // (TZ + 8) x TX
-    __shared__ float red[NW];
 
     const Geom &g = A.g;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ, shot = blockIdx.z;
-    const int tile = blockIdx.y * A.ntx + blockIdx.x;
+    const int x0 = bx * TX, z0 = bz * TZ;
+    const int tile = bz * A.ntx + bx;
     const int P = g.P;
     const long long sh = (long long)shot * g.fstride;
     const long long org = cell_off(g, z0, 0, x0);           // tile origin within one field
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(NTH, 2) k_step2d_f32(const StepArgs<float> A, 
     const int r0 = A.sample ? A.rec_start[tile] : 0, r1 = A.sample ? A.rec_start[tile + 1] : 0;
 
     // ================= the previous step's fields are needed from here on
-    cudaGridDependencySynchronize();
+    if (PDL) cudaGridDependencySynchronize();
 
     {   // stage p^n: TZ + 2H rows of TX + 2H floats
         const float *src = pcb - H * g.PY * P - H;
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(NTH, 2) k_step2d_f32(const StepArgs<float> A, 
             if (fp16) {
                 const float s = pow2_scale(__uint_as_float(io->snap_max[shot * A.nsnap + t.snap_k]));
                 sinv = 1.f / s;
-                if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) io->snap_scale[shot * A.nsnap + t.snap_k] = s;
+                if (bx == 0 && bz == 0 && tid == 0) io->snap_scale[shot * A.nsnap + t.snap_k] = s;
             }
         }
     }
@@ -451,6 +453,107 @@ __global__ void __launch_bounds__(NTH, 2) k_step2d_f32(const StepArgs<float> A, 
 }
 
 template <int TZ, int MODE>
+__global__ void __launch_bounds__(NTH, 2) k_step2d_f32(const StepArgs<float> A, const StepTime t) {
+    extern __shared__ float4 smem4[];
+    __shared__ float red[NW];
+    tile_step<TZ, MODE, true>(A, t, blockIdx.x, blockIdx.y, blockIdx.z, reinterpret_cast<float *>(smem4), red);
+}
+
+// ---------------------------------------------------------------- batch
+//
+// Persistent dataflow execution of many shots on many grids. Work items are
+// (group, step, member, tile), taken in order from a global counter; a group
+// is a set of (slice, shot) members whose fields fit in L2 together, so a
+// group advances through all its steps while resident. An item waits until
+// its own tile and the 8 neighbouring tiles of its shot (earlier items, maybe
+// on other CTAs) have finished the previous step
+// (per-tile step counters, acquire/release), which also guarantees that none
+// of them still reads the buffer it is about to overwrite. Every item was
+// queued after the items it waits on, so progress never depends on which
+// CTAs are resident. Each wait is bounded: on timeout the kernel raises a
+// flag and every CTA returns.
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int TZ>
+__global__ void __launch_bounds__(NTH, 2) k_batch2d(const BatchArgs B) {
+    extern __shared__ float4 smem4[];
+    __shared__ float red[NW];
+    __shared__ StepArgs<float> sA;
+    __shared__ long long s_item;
+    __shared__ int s_abort, s_slice;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_slice = -1;
+    for (;;) {
+        if (tid == 0) {
+            s_item = (long long)atomicAdd(B.head, 1ULL);
+            s_abort = (*reinterpret_cast<volatile unsigned *>(B.flags) & kFlagTimeout) != 0;
+        }
+        __syncthreads();
+        const long long i = s_item;
+        if (i >= B.total || s_abort) return;
+        int gi = 0;
+        while (gi + 1 < B.ngroups && B.groups[gi + 1].base <= i) gi++;
+        const BatchGroup G = B.groups[gi];
+        const long long r = i - G.base;
+        const int n = (int)(r / G.T), ri = (int)(r % G.T);
+        int lo = G.m0, hi = G.m1 - 1;  // member whose tile range holds ri
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (B.members[mid].tile0 <= ri) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchMember M = B.members[lo];
+        if (M.slice != s_slice) {  // the member's grid arguments, once per change of grid
+            __syncthreads();
+            static_assert(sizeof(StepArgs<float>) % 8 == 0, "copied in 8-byte units");
+            const long long *src = reinterpret_cast<const long long *>(B.slices + M.slice);
+            long long *dst = reinterpret_cast<long long *>(&sA);
+            for (int k = tid; k < (int)(sizeof(StepArgs<float>) / 8); k += NTH) dst[k] = src[k];
+            if (tid == 0) s_slice = M.slice;
+            __syncthreads();
+        }
+        const int tile = ri - M.tile0, ntx = sA.ntx, ntz = sA.ntz;
+        const int bz = tile / ntx, bx = tile - bz * ntx;
+        int *done = B.done + M.done0;
+        if (n > 0 && tid < 32) {  // wait for the tile and its 8 neighbours to finish step n-1
+            const int dz = tid / 3 - 1, dx = tid % 3 - 1;
+            const int nz = bz + dz, nx = bx + dx;
+            bool need = tid < 9 && nz >= 0 && nz < ntz && nx >= 0 && nx < ntx;
+            long long spins = 0;
+            while (__any_sync(0xffffffffu, need)) {
+                if (need && ld_acquire(done + nz * ntx + nx) >= n) need = false;
+                if (++spins > B.spin_limit) {
+                    if (tid == 0) atomicOr(B.flags, kFlagTimeout);
+                    break;
+                }
+                if (need) __nanosleep(32);
+                if ((spins & 1023) == 0 && (*reinterpret_cast<volatile unsigned *>(B.flags) & kFlagTimeout)) break;
+            }
+            if (tid == 0) s_abort = (*reinterpret_cast<volatile unsigned *>(B.flags) & kFlagTimeout) != 0;
+        }
+        __syncthreads();
+        if (s_abort) return;
+        StepTime t{};
+        t.n = n;
+        t.snap_k = t.max_k = -1;
+        t.inj_row = n;
+        tile_step<TZ, kModeForward, false>(sA, t, bx, bz, M.shot, reinterpret_cast<float *>(smem4), red);
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            st_release(done + tile, n + 1);
+        }
+    }
+}
+
+template <int TZ, int MODE>
 cudaError_t launch_mode(const StepArgs<float> &a, const StepTime &t, int nshots, cudaStream_t st, bool pdl) {
     const bool cp = a.bc == SIM_BC_CPML;
     cudaLaunchConfig_t cfg = {};
@@ -495,7 +598,35 @@ cudaError_t configure_step2d_f32() {
     cudaError_t e = configure_tz<8>();
     if (e == cudaSuccess) e = configure_tz<16>();
     if (e == cudaSuccess) e = configure_tz<32>();
+    for (int tz : {8, 16, 32}) {
+        if (e != cudaSuccess) break;
+        const int bytes = (int)(tz == 8 ? smem_floats<8>(true) : tz == 16 ? smem_floats<16>(true) : smem_floats<32>(true)) *
+                          (int)sizeof(float);
+        e = tz == 8 ? cudaFuncSetAttribute(k_batch2d<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+            : tz == 16 ? cudaFuncSetAttribute(k_batch2d<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+                       : cudaFuncSetAttribute(k_batch2d<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    }
     return e;
+}
+
+cudaError_t launch_batch2d(const BatchArgs &b, int tz, bool cpml, int grid, cudaStream_t st) {
+    const size_t bytes = (tz == 8 ? smem_floats<8>(cpml) : tz == 16 ? smem_floats<16>(cpml) : smem_floats<32>(cpml)) *
+                         sizeof(float);
+    if (tz == 8) k_batch2d<8><<<grid, NTH, bytes, st>>>(b);
+    else if (tz == 16) k_batch2d<16><<<grid, NTH, bytes, st>>>(b);
+    else if (tz == 32) k_batch2d<32><<<grid, NTH, bytes, st>>>(b);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+int batch_blocks_per_sm(int tz, bool cpml) {
+    int nb = 0;
+    const size_t bytes = (tz == 8 ? smem_floats<8>(cpml) : tz == 16 ? smem_floats<16>(cpml) : smem_floats<32>(cpml)) *
+                         sizeof(float);
+    if (tz == 8) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch2d<8>, NTH, bytes);
+    else if (tz == 16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch2d<16>, NTH, bytes);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch2d<32>, NTH, bytes);
+    return nb;
 }
 
 cudaError_t launch_step2d_f32(const StepArgs<float> &a, const StepTime &t, int tz, int nshots, int mode,

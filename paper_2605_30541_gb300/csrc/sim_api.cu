@@ -1159,6 +1159,266 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
     return SIM_OK;
 }
 
+
+// ---------------------------------------------------------------- batch
+//
+// One persistent launch for many (slice, shot) members (k_batch2d). Members
+// are grouped so that a group's fields fit in a share of L2; the device work
+// list runs group after group, each through all its steps. The per-device
+// context below owns the work-list tables and the captured graph of
+// (counter resets + kernel); handles keep owning their fields and lists.
+struct BatchCtx {
+    int dev = -1;
+    void *slices = nullptr, *groups = nullptr, *members = nullptr, *done = nullptr;
+    unsigned long long *head = nullptr;
+    unsigned *flags = nullptr, *flags_host = nullptr;
+    size_t cap_slices = 0, cap_groups = 0, cap_members = 0, cap_done = 0;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<char> key;
+    cudaEvent_t ev = nullptr;
+};
+std::mutex g_batch_mu;
+std::vector<BatchCtx> g_batch;
+
+cudaError_t grow(void **p, size_t *cap, size_t need) {
+    if (*cap >= need) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(p, need);
+    if (e == cudaSuccess) *cap = need;
+    return e;
+}
+
+sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst) {
+    if (nitems < 1 || !items) return thread_fail(SIM_ERR_ARG, "empty batch");
+    sim_t s0 = items[0].sim;
+    if (!s0) return thread_fail(SIM_ERR_ARG, "batch item 0 has no handle");
+    for (int i = 0; i < nitems; i++) {
+        sim_t s = items[i].sim;
+        if (!s || !s->model_set) return thread_fail(SIM_ERR_STATE, "batch item %d: no handle or no model", i);
+        if (s->sticky) return s->sticky;
+        if (s->d.ndim != 2 || s->d.precision != SIM_FP32)
+            return thread_fail(SIM_ERR_UNSUPPORTED, "batch item %d: the batch runs 2D FP32 handles", i);
+        if (s->d.nt != s0->d.nt) return thread_fail(SIM_ERR_ARG, "batch item %d: nt differs", i);
+        if (s->dev != s0->dev) return thread_fail(SIM_ERR_ARG, "batch item %d: another device", i);
+        if (items[i].nshots < 1 || items[i].nshots > s->d.max_shots)
+            return thread_fail(SIM_ERR_ARG, "batch item %d: nshots outside [1, max_shots]", i);
+        if (items[i].nrec < 0 || items[i].nrec > s->d.max_rec || (items[i].nrec > 0 && !items[i].rec_pos))
+            return thread_fail(SIM_ERR_ARG, "batch item %d: bad receivers", i);
+        if (!items[i].wavelet || !items[i].src_pos) return thread_fail(SIM_ERR_ARG, "batch item %d: no source", i);
+        for (int j = 0; j < i; j++)
+            if (items[j].sim == s) return thread_fail(SIM_ERR_ARG, "batch items %d and %d share a handle", j, i);
+    }
+    cudaSetDevice(s0->dev);
+    const int nt = s0->d.nt;
+    int tz = 16;
+    if (const char *f = getenv("GSIM_TILE_Z")) {
+        const int v = atoi(f);
+        if (v == 8 || v == 16 || v == 32) tz = v;
+    }
+    bool any_cpml = false;
+    std::vector<StepArgs<float>> slices(nitems);
+    std::vector<void *> gdev(nitems, nullptr);
+    // per handle: lists, io and a clean state, on the handle's own stream
+    for (int i = 0; i < nitems; i++) {
+        sim_t s = items[i].sim;
+        const sim_batch_item &it = items[i];
+        set_tile_z(s, tz);
+        any_cpml |= s->d.bc == SIM_BC_CPML;
+        const void *wav = it.wavelet;
+        if (!is_device_ptr(wav)) {
+            if (sim_status r = s->cuda(cudaMemcpyAsync(s->wave, wav, (size_t)nt * sizeof(float),
+                                                       cudaMemcpyHostToDevice, s->st), "wavelet upload"))
+                return r;
+            wav = s->wave;
+        }
+        gdev[i] = it.gather && is_device_ptr(it.gather) ? it.gather : (it.gather ? s->gath : nullptr);
+        std::vector<int> rstart, istart;
+        std::vector<RecEntryT<float>> rent;
+        std::vector<InjGroup> igrp;
+        std::vector<InjEntryT<float>> ient;
+        std::vector<InjPoint> pts;
+        if (sim_status r = build_receivers<float>(s, it.nrec, it.rec_pos, rstart, rent)) return r;
+        if (sim_status r = collect_points(s, it.nshots, it.src_pos, true, pts, "source")) return r;
+        const int ntiles = s->ntx * s->ntz;
+        group_injection<float>(pts, it.nshots * ntiles, istart, igrp, ient);
+        if (sim_status r = upload(s, s->rec_start, rstart, s->cap_start, "receiver start")) return r;
+        if (sim_status r = upload(s, static_cast<RecEntryT<float> *>(s->rec), rent, s->cap_rec, "receiver")) return r;
+        if (sim_status r = upload(s, s->inj_start, istart, s->cap_start, "injection start")) return r;
+        if (sim_status r = upload(s, s->inj_grp, igrp, s->cap_grp, "injection group")) return r;
+        if (sim_status r = upload(s, static_cast<InjEntryT<float> *>(s->inj_ent), ient, s->cap_grp,
+                                  "injection entry"))
+            return r;
+        SimIO io{};
+        io.wavelet = wav;
+        io.gather = it.nrec > 0 ? gdev[i] : nullptr;
+        io.nrec = it.nrec;
+        io.nshots = it.nshots;
+        if (sim_status r = s->cuda(cudaMemcpyAsync(s->io, &io, sizeof io, cudaMemcpyHostToDevice, s->st), "io"))
+            return r;
+        if (sim_status r = reset_state(s, it.nshots)) return r;
+        StepArgs<float> a = step_args<float>(s);
+        a.inj_per_shot = 1;
+        a.inj_kind = 0;
+        a.nsnap = 0;
+        a.sample = it.nrec > 0 && gdev[i] != nullptr;
+        slices[i] = a;
+    }
+    // members and L2-sized groups
+    int l2 = 0, sms = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, s0->dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s0->dev);
+    double budget = 0.6 * l2;
+    if (const char *f = getenv("GSIM_BATCH_GROUP_MB")) budget = atof(f) * 1048576.0;
+    std::vector<BatchMember> members;
+    std::vector<BatchGroup> groups;
+    long long total = 0, done_total = 0;
+    BatchGroup cur{0, 0, 0, 0};
+    double bytes = 0;
+    int last_slice = -1;
+    for (int i = 0; i < nitems; i++) {
+        sim_t s = items[i].sim;
+        const Geom &g = s->g;
+        const int ntiles = s->ntx * s->ntz;
+        const double cells = (double)g.NZ * g.NX;
+        const double strip = s->d.bc == SIM_BC_CPML ? (double)(g.nbx0 + g.nbx1) * g.NZ + (double)(g.nbz0 + g.nbz1) * g.NX : 0;
+        for (int k = 0; k < items[i].nshots; k++) {
+            double mb = 8.0 * cells + 12.0 * strip + (last_slice != i ? 4.0 * cells : 0.0);
+            if (cur.T > 0 && bytes + mb > budget) {
+                cur.m1 = (int)members.size();
+                groups.push_back(cur);
+                total += (long long)nt * cur.T;
+                cur = BatchGroup{total, 0, (int)members.size(), 0};
+                bytes = 0;
+                mb = 12.0 * cells + 12.0 * strip;
+            }
+            BatchMember m{i, k, cur.T, (int)(done_total + (long long)k * ntiles)};
+            members.push_back(m);
+            cur.T += ntiles;
+            bytes += mb;
+            last_slice = i;
+        }
+        done_total += (long long)items[i].nshots * ntiles;
+    }
+    cur.m1 = (int)members.size();
+    groups.push_back(cur);
+    total += (long long)nt * cur.T;
+
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    BatchCtx *ctx = nullptr;
+    for (auto &c : g_batch)
+        if (c.dev == s0->dev) ctx = &c;
+    if (!ctx) {
+        g_batch.emplace_back();
+        ctx = &g_batch.back();
+        ctx->dev = s0->dev;
+    }
+    auto fail = [&](cudaError_t e, const char *what) {
+        cudaGetLastError();
+        return thread_fail(e == cudaErrorMemoryAllocation ? SIM_ERR_OOM : SIM_ERR_CUDA, "batch %s: %s", what,
+                           cudaGetErrorString(e));
+    };
+    cudaError_t e = cudaSuccess;
+    if (!ctx->head) {
+        e = cudaMalloc(&ctx->head, sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->flags, sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMallocHost(&ctx->flags_host, sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return fail(e, "allocation");
+    }
+    if ((e = grow(&ctx->slices, &ctx->cap_slices, slices.size() * sizeof(StepArgs<float>))) ||
+        (e = grow(&ctx->groups, &ctx->cap_groups, groups.size() * sizeof(BatchGroup))) ||
+        (e = grow(&ctx->members, &ctx->cap_members, members.size() * sizeof(BatchMember))) ||
+        (e = grow(&ctx->done, &ctx->cap_done, (size_t)done_total * sizeof(int)))) {
+        if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+        ctx->exec = nullptr;
+        return fail(e, "allocation");
+    }
+    // order the handles' preparation before the batch stream
+    for (int i = 0; i < nitems; i++) {
+        if ((e = cudaEventRecord(ctx->ev, items[i].sim->st)) || (e = cudaStreamWaitEvent(bst, ctx->ev, 0)))
+            return fail(e, "ordering");
+    }
+    if ((e = cudaMemcpyAsync(ctx->slices, slices.data(), slices.size() * sizeof(StepArgs<float>),
+                             cudaMemcpyHostToDevice, bst)) ||
+        (e = cudaMemcpyAsync(ctx->groups, groups.data(), groups.size() * sizeof(BatchGroup), cudaMemcpyHostToDevice,
+                             bst)) ||
+        (e = cudaMemcpyAsync(ctx->members, members.data(), members.size() * sizeof(BatchMember),
+                             cudaMemcpyHostToDevice, bst)))
+        return fail(e, "upload");
+    BatchArgs b{};
+    b.slices = static_cast<const StepArgs<float> *>(ctx->slices);
+    b.groups = static_cast<const BatchGroup *>(ctx->groups);
+    b.ngroups = (int)groups.size();
+    b.members = static_cast<const BatchMember *>(ctx->members);
+    b.done = static_cast<int *>(ctx->done);
+    b.head = ctx->head;
+    b.total = total;
+    b.spin_limit = 1LL << 22;
+    if (const char *f = getenv("GSIM_SPIN_LIMIT")) b.spin_limit = atoll(f);
+    b.flags = ctx->flags;
+    const int grid = sms * std::max(1, batch_blocks_per_sm(tz, any_cpml));
+    // counters reset + the persistent kernel, replayed as one graph
+    std::vector<char> key(sizeof b + 3 * sizeof(int) + sizeof(long long));
+    memcpy(key.data(), &b, sizeof b);
+    const int kk[3] = {tz, (int)any_cpml, grid};
+    memcpy(key.data() + sizeof b, kk, sizeof kk);
+    memcpy(key.data() + sizeof b + sizeof kk, &done_total, sizeof done_total);
+    if (!ctx->exec || key != ctx->key || bst == nullptr) {
+        if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+        ctx->exec = nullptr;
+    }
+    auto body = [&](cudaStream_t st) {
+        cudaError_t r = cudaMemsetAsync(ctx->done, 0, (size_t)done_total * sizeof(int), st);
+        if (r == cudaSuccess) r = cudaMemsetAsync(ctx->head, 0, sizeof(unsigned long long), st);
+        if (r == cudaSuccess) r = cudaMemsetAsync(ctx->flags, 0, sizeof(unsigned), st);
+        if (r == cudaSuccess) r = launch_batch2d(b, tz, any_cpml, grid, st);
+        return r;
+    };
+    if (bst == nullptr) {  // the legacy stream cannot be captured: launch directly
+        if ((e = body(bst))) return fail(e, "launch");
+    } else {
+        if (!ctx->exec) {
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamBeginCapture(bst, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t e1 = body(bst);
+                e = cudaStreamEndCapture(bst, &graph);
+                if (e1 != cudaSuccess) e = e1;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return fail(e, "graph capture");
+            ctx->key = key;
+        }
+        if ((e = cudaGraphLaunch(ctx->exec, bst))) return fail(e, "graph launch");
+    }
+    // the handles' later work waits for the batch; outputs to host
+    if ((e = cudaEventRecord(ctx->ev, bst))) return fail(e, "ordering");
+    bool wait = false;
+    for (int i = 0; i < nitems; i++) {
+        sim_t s = items[i].sim;
+        if ((e = cudaStreamWaitEvent(s->st, ctx->ev, 0))) return fail(e, "ordering");
+        const sim_batch_item &it = items[i];
+        if (it.gather && gdev[i] == s->gath && it.nrec > 0) {
+            if ((e = cudaMemcpyAsync(it.gather, s->gath, (size_t)it.nshots * nt * it.nrec * sizeof(float),
+                                     cudaMemcpyDeviceToHost, s->st)))
+                return fail(e, "gather download");
+            wait = true;
+        }
+        if ((e = cudaMemcpyAsync(s->flags_host, s->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st)))
+            return fail(e, "flags");
+    }
+    if ((e = cudaMemcpyAsync(ctx->flags_host, ctx->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, bst)) ||
+        (e = cudaStreamSynchronize(bst)))
+        return fail(e, "completion");
+    if (*ctx->flags_host & kFlagTimeout) return thread_fail(SIM_ERR_TIMEOUT, "a bounded wait in the batch kernel gave up");
+    for (int i = 0; i < nitems; i++)
+        if (sim_status r = poll_flags(items[i].sim, wait)) return r;
+    return SIM_OK;
+}
+
 }  // namespace
 
 // ============================================================== C ABI
@@ -1330,8 +1590,8 @@ sim_status sim_adjoint(sim_t s, int nshots, const void *wavelet, const double *s
                                   ckpt_fp16, grad_v);
 }
 
-sim_status sim_batch(int, const sim_batch_item *, void *) {
-    return thread_fail(SIM_ERR_UNSUPPORTED, "batch not built yet");
+sim_status sim_batch(int nitems, const sim_batch_item *items, void *cuda_stream) {
+    return batch_impl(nitems, items, static_cast<cudaStream_t>(cuda_stream));
 }
 
 sim_status sim_sync(sim_t s) {

@@ -148,6 +148,32 @@ struct Pt3 {
     float w[8];
 };
 
+// Batch (persistent) execution: see k_batch2d in fwd2d_f32.cu.
+struct BatchMember {
+    int slice;       // index into BatchArgs::slices
+    int shot;
+    int tile0;       // first of this member's tiles within one step of its group
+    int done0;       // offset of this member's per-tile step counters
+};
+struct BatchGroup {
+    long long base;  // first item of the group
+    int T;           // tiles per step over the group's members
+    int m0, m1;      // member range
+};
+struct BatchArgs {
+    const StepArgs<float> *slices;
+    const BatchGroup *groups;
+    int ngroups;
+    const BatchMember *members;
+    int *done;                 // per (slice, shot, tile): steps completed
+    unsigned long long *head;  // work counter
+    long long total;           // items
+    long long spin_limit;      // polls before a wait gives up
+    unsigned *flags;           // kFlagTimeout on a wait that gave up
+};
+cudaError_t launch_batch2d(const BatchArgs &b, int tz, bool cpml, int grid, cudaStream_t st);
+int batch_blocks_per_sm(int tz, bool cpml);
+
 // 3D launchers (fwd3d.cu). Per step: snapshot, sample, CPML psi, z-march
 // update, CPML zeta + addend, source injection.
 cudaError_t configure_step3d();

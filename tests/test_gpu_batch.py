@@ -1,0 +1,100 @@
+"""sim_batch: many shots on uneven grids in one persistent launch. Results must
+equal per-handle sim_forward bit for bit (each cell's arithmetic does not
+depend on the schedule) and match the FP64 oracle; a bounded wait that runs
+out reports SIM_ERR_TIMEOUT instead of hanging."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2605_30541_gb300 as p
+    p.abi.load()
+    return p
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def uneven_slices(nt=300):
+    out = []
+    for j, (nz, nx, bc, fs, ns) in enumerate([(60, 150, "cpml", 1, 3), (41, 97, "sponge", 1, 2),
+                                              (75, 260, "cpml", 0, 4)]):
+        nb = 12
+        cfg = dict(ndim=2, nz=nz, ny=1, nx=nx, h=10.0, dt=1e-3, nt=nt, bc=bc,
+                   nb=[0 if fs else nb, nb, 0, 0, nb, nb], free_surface=fs, f_ref=12.0)
+        cfg["vel"] = synth.procedural_2d(nz, nx, 10.0, 900 + j)
+        cfg["wavelet"] = synth.ricker(12.0, 0.08, 1e-3, nt)
+        cfg["src"] = np.stack([np.linspace(50.0, (nx - 5) * 10.0, ns), np.full(ns, 10.0 + 5 * j)], axis=1)
+        cfg["rec"] = synth.line(0.0, (nx - 1) * 10.0, nx // 3, 20.0)
+        out.append(cfg)
+    return out
+
+
+def sims_for(pkg, slices):
+    return [pkg.Simulator(c, c["vel"], max_shots=len(c["src"]), max_rec=len(c["rec"])) for c in slices]
+
+
+def test_batch_equals_forward_and_oracle(pkg):
+    slices = uneven_slices()
+    sims = sims_for(pkg, slices)
+    gb = pkg.batch([dict(sim=s, wavelet=c["wavelet"], src=c["src"], rec=c["rec"]) for s, c in zip(sims, slices)])
+    torch.cuda.synchronize()
+    for s, c, g in zip(sims, slices, gb):
+        ref = s.forward(c["wavelet"], c["src"], c["rec"])["gather"]
+        assert torch.equal(g, ref)
+        o = oracle.forward(c, c["vel"].astype(np.float64), c["wavelet"].astype(np.float64), src=c["src"][-1],
+                           rec=c["rec"])["gather"]
+        assert rel(g[-1].cpu().numpy(), o) <= 1e-4
+    for s in sims:
+        s.close()
+
+
+def test_batch_timeout_is_reported_and_recoverable(pkg):
+    slices = uneven_slices(nt=40)
+    sims = sims_for(pkg, slices)
+    entries = [dict(sim=s, wavelet=c["wavelet"], src=c["src"], rec=c["rec"]) for s, c in zip(sims, slices)]
+    os.environ["GSIM_SPIN_LIMIT"] = "0"   # every wait on a neighbour gives up at once
+    try:
+        with pytest.raises(pkg.SimError) as e:
+            pkg.batch(entries)
+        assert e.value.code == pkg.abi.SIM_ERR_TIMEOUT
+    finally:
+        del os.environ["GSIM_SPIN_LIMIT"]
+    gb = pkg.batch(entries)   # the GPU and the handles stay usable
+    ref = sims[0].forward(slices[0]["wavelet"], slices[0]["src"], slices[0]["rec"])["gather"]
+    assert torch.equal(gb[0], ref)
+    for s in sims:
+        s.close()
+
+
+def test_c3_batched_workload_sampled(pkg):
+    # 64 shots on the field-scale slice + 16 uneven slices with 8 shots each, one launch
+    nt = 4000
+    slices = synth.config_c3(nt=nt)
+    sims = sims_for(pkg, slices)
+    gb = pkg.batch([dict(sim=s, wavelet=c["wavelet"], src=c["src"], rec=c["rec"]) for s, c in zip(sims, slices)])
+    torch.cuda.synchronize()
+    # bitwise against per-handle forwards on three slices
+    for k in (0, 5, 16):
+        ref = sims[k].forward(slices[k]["wavelet"], slices[k]["src"], slices[k]["rec"])["gather"]
+        assert torch.equal(gb[k], ref), k
+    # FP64 oracle on sampled shots over the first 600 steps
+    for k, shot in ((0, 31), (9, 7)):
+        c = dict(slices[k], nt=600)
+        o = oracle.forward(c, c["vel"].astype(np.float64), c["wavelet"][:600].astype(np.float64),
+                           src=c["src"][shot], rec=c["rec"])["gather"]
+        assert rel(gb[k][shot, :600].cpu().numpy(), o) <= 1e-4
+    for s in sims:
+        s.close()
