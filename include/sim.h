@@ -179,6 +179,27 @@ typedef struct {
  * `cuda_stream` as in sim_create. */
 sim_status sim_batch(int nitems, const sim_batch_item *items, void *cuda_stream);
 
+/* No counterpart in the paper. A forward solve for callers that cannot
+ * allocate device memory at the time they call: code running while their own
+ * application records a CUDA graph (an allocation there would not be
+ * replayed), processes whose device memory is already reserved in full by a
+ * framework's pool, and latency-critical paths where cudaMalloc / cudaFree,
+ * which may synchronise the device, are not acceptable.
+ * 2D, FP32, one shot, gather only: vel [nz][nx], wavelet [nt] and
+ * gather [nt][nrec] are device pointers; src_pos [2] and rec_pos [nrec][2]
+ * are host arrays as in sim_forward. Every intermediate lives in one 32 MiB
+ * array built into the library (each GPU that loads the library holds it
+ * until the process exits); a problem that does not fit returns SIM_ERR_ARG
+ * before any GPU work. Nothing is allocated. The first call on a device looks
+ * up that array's address with the device current and configures the step
+ * kernel: make that first call before any stream capture. All calls share the
+ * array: each clears what must start at zero, and calls whose GPU work
+ * overlaps (other streams or threads) race on it. Returns after the solve
+ * has completed on cuda_stream (NULL: legacy stream). Errors: sim_last_error(NULL). */
+sim_status sim_forward_noalloc(const sim_desc *d, const float *vel, const float *wavelet,
+                               const double *src_pos, int nrec, const double *rec_pos, float *gather,
+                               void *cuda_stream);
+
 /* Wait for the handle's stream and report any device-side failure. */
 sim_status sim_sync(sim_t s);
 

@@ -16,7 +16,7 @@ from .abi import SIM_BC, SIM_FP32, SIM_FP64, SimBatchItem, SimDesc, SimInfo
 
 __all__ = ["SimError", "make_desc", "sim_plan", "sim_create", "sim_set_model", "sim_forward",
            "sim_adjoint", "sim_batch", "sim_sync", "sim_get_info", "sim_last_error", "sim_destroy",
-           "Simulator", "batch"]
+           "Simulator", "batch", "sim_forward_noalloc"]
 
 
 class SimError(RuntimeError):
@@ -153,6 +153,12 @@ def batch(entries, stream=None):
         outs.append(g)
     sim_batch(items, stream)
     return outs
+
+
+def sim_forward_noalloc(desc, vel, wavelet, src_pos, nrec, rec_pos, gather, stream=None):
+    """Forward solve that allocates no device memory (see include/sim.h)."""
+    _check(abi.load().sim_forward_noalloc(ctypes.byref(desc), _ptr(vel), _ptr(wavelet), _ptr(src_pos), nrec,
+                                          _ptr(rec_pos), _ptr(gather), _stream(stream)))
 
 
 def sim_sync(handle):

@@ -194,6 +194,8 @@ double corner_weight(const double t[3], int dz, int dy, int dx) {
 
 }  // namespace
 
+void gsim::set_thread_error(const char *msg) { t_err = msg; }
+
 // ============================================================== handle
 
 struct sim_s {

@@ -186,6 +186,9 @@ cudaError_t launch_inject3d(const StepArgs<float> &a, const StepTime &t, const v
                             cudaStream_t st);
 cudaError_t launch_snap3d(const StepArgs<float> &a, const StepTime &t, int fp16, int nshots, cudaStream_t st);
 
+// Message returned by sim_last_error(NULL) for failures of this thread.
+void set_thread_error(const char *msg);
+
 // Launchers (one translation unit each).
 template <typename T>
 cudaError_t launch_step2d(const StepArgs<T> &a, int n, int nshots, int mode, cudaStream_t st);
