@@ -38,10 +38,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c2x32", "c3", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c2x32", "c3", "c5", "c5s"])
     ap.add_argument("--nt", type=int, default=0, help="override nt (profiling runs only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
     return ap.parse_args()
 
 
@@ -53,6 +54,9 @@ def workload(args):
     import synth
     if args.workload == "c5":
         return synth.config_c5(nt=args.nt or 2500), 1
+    if args.workload == "c5s":
+        # reduced 3D volume for counter captures (about 1 GB on the device)
+        return synth.config_c5(nt=args.nt or 200, n=(190, 400, 400), nrec_side=101), 1
     nt = args.nt or 8000
     cfg = synth.config_c2(nt=nt)
     nshots = 32 if args.workload == "c2x32" else 1
@@ -60,6 +64,9 @@ def workload(args):
         cfg["src"] = np.stack([500.0 + 280.0 * np.arange(nshots), np.full(nshots, 10.0)], axis=1)
         cfg.update(snap_every=0, snap_end=0)
     return cfg, nshots
+
+
+PATH_STEP, PATH_RESIDENT = 1, 2  # sim_info.last_path
 
 
 def padded_cells(cfg):
@@ -92,11 +99,14 @@ def algorithmic_bytes_per_launch(cfg, nshots):
     return nshots * (16 * cells + 16 * strip + rec + snap)
 
 
-def launches_per_solve(cfg, nsnap):
-    """Kernels of ours one solve launches: the fused step kernel per step in 2D;
-    in 3D the z-march plus, per step, receiver sampling, source injection and
-    two CPML kernels per absorbing axis, plus snapshot kernels; plus the final
+def launches_per_solve(cfg, nsnap, path):
+    """Kernels of ours one solve launches: on the resident path one launch for
+    the whole time loop; else the fused step kernel per step in 2D; in 3D the
+    z-march plus, per step, receiver sampling, source injection and two CPML
+    kernels per absorbing axis, plus snapshot kernels; plus the final
     finite-value check."""
+    if path == PATH_RESIDENT:
+        return 2
     if cfg["ndim"] == 2:
         return cfg["nt"] + 1
     nb = cfg["nb"]
@@ -289,6 +299,56 @@ def run_batch(args):
         s.close()
 
 
+def gradient_timing(reps=2):
+    """FWI gradient workload (201 x 201 procedural model, 16 shots, 4 s): seconds
+    per shot of (a) all 16 shots in one sim_adjoint with FP16-scaled checkpoints
+    and imaging terms and (b) one shot per call with FP32 storage, plus their
+    relative difference (the tests bound them against the FP64 oracle gradient:
+    FP32 <= 1e-4, FP16 <= 1e-2 relative L2)."""
+    import torch
+    import synth
+    import paper_2605_30541_gb300 as pkg
+    c = synth.config_c4()
+    ns, nt, nrec = len(c["src"]), c["nt"], len(c["rec"])
+    true = pkg.Simulator(c, c["vel_true"], max_shots=ns, max_rec=nrec)
+    d = true.forward(c["wavelet"], c["src"], c["rec"])["gather"].contiguous()
+    true.close()
+    sim = pkg.Simulator(c, c["vel"], max_shots=ns, max_rec=nrec)
+    w = torch.as_tensor(c["wavelet"], device="cuda")
+    src, rec = np.ascontiguousarray(c["src"]), np.ascontiguousarray(c["rec"])
+
+    def batched():
+        g = torch.zeros(c["vel"].shape, device="cuda")
+        pkg.sim_adjoint(sim.handle, ns, w, src, nrec, rec, d, None, None, 1, g)
+        return g
+
+    def one_by_one():
+        g = torch.zeros(c["vel"].shape, device="cuda")
+        for k in range(ns):
+            pkg.sim_adjoint(sim.handle, 1, w, np.ascontiguousarray(src[k:k + 1]), nrec, rec, d[k:k + 1].contiguous(),
+                            None, None, 0, g)
+        return g
+
+    out = {}
+    for name, fn in (("batched_fp16", batched), ("one_shot_fp32", one_by_one)):
+        g = fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            g = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = (e0.elapsed_time(e1) / 1e3 / reps / ns, g)
+    sim.close()
+    g16, g32 = out["batched_fp16"][1], out["one_shot_fp32"][1]
+    return {"workload": "c4: 201x201 + 20-cell sponge, 16 shots, nt=4000, sqrt(nt) checkpoints",
+            "s_per_shot_batched_fp16": out["batched_fp16"][0], "s_per_shot_one_shot_fp32": out["one_shot_fp32"][0],
+            "speedup": out["one_shot_fp32"][0] / out["batched_fp16"][0],
+            "rel_l2_fp16_vs_fp32": float(torch.linalg.norm(g16 - g32) / torch.linalg.norm(g32)),
+            "tolerance_vs_fp64_oracle": {"fp32": 1e-4, "fp16": 1e-2}}
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -344,17 +404,23 @@ def run_ours(args):
     units = world * args.steps * nshots * nt * cells
     value = units / tmax / 1e9
 
-    # roofline of the step kernel: nt launches per solve (gaps included in the duration)
-    per_launch_s = (total / args.steps) / nt
-    algo = algorithmic_bytes_per_launch(cfg, nshots)
+    # roofline of the dominant kernel: the per-step kernel runs nt launches per
+    # solve (gaps included in the duration); the resident kernel runs the whole
+    # time loop in one launch
+    path = pkg.sim_get_info(sim.handle).last_path
+    launches = 1 if path == PATH_RESIDENT else nt
+    per_launch_s = (total / args.steps) / launches
+    algo = algorithmic_bytes_per_launch(cfg, nshots) * (nt if path == PATH_RESIDENT else 1)
     peak, peak_kind = read_peaks()
     achieved = algo / per_launch_s / 1e9
-    key = "step_%s" % args.workload
-    kfile, kname = ("fwd3d.cu", "k_step3d") if cfg["ndim"] == 3 else ("fwd2d_f32.cu", "k_step2d_f32")
+    key = "%s_%s" % ("resident" if path == PATH_RESIDENT else "step", args.workload)
+    kfile, kname = (("fwd3d.cu", "k_step3d") if cfg["ndim"] == 3 else
+                    ("resident2d.cu", "k_resident2d") if path == PATH_RESIDENT else ("fwd2d_f32.cu", "k_step2d_f32"))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": ncu_traffic(kfile, key), "kernel": kname,
             "peak_kind": peak_kind + " (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind,
-            "algorithmic_bytes_per_launch": algo, "avg_launch_us": per_launch_s * 1e6}
+            "algorithmic_bytes_per_launch": algo, "avg_launch_us": per_launch_s * 1e6,
+            "path": "resident" if path == PATH_RESIDENT else "per-step"}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -387,13 +453,17 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_oracle_rate(cfg)
+    grad = None
+    if rank == 0 and not args.no_grad and cfg["ndim"] == 2:
+        grad = gradient_timing()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Gcell/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": (("c5: 3D volume 619x1000x1000 (+30-cell CPML on x, y, bottom, free top), "
-                                         "dt=0.8 ms, nt=%d, %d receivers, %d shot(s) per GPU" % (nt, len(rec), nshots))
+                "config": {"workload": (("%s: 3D volume %dx%dx%d (+30-cell CPML on x, y, bottom, free top), "
+                                         "dt=0.8 ms, nt=%d, %d receivers, %d shot(s) per GPU"
+                                         % (args.workload, cfg["nz"], cfg["ny"], cfg["nx"], nt, len(rec), nshots))
                                         if cfg["ndim"] == 3 else
                                         ("c2: 2D slice 619x1000 (+50-cell CPML left/right/bottom, free top), "
                                          "nt=%d, %d receivers, %d FP32 snapshots, %d shot(s) per GPU"
@@ -401,8 +471,8 @@ def run_ours(args):
                            "padded_cells": cells, "l2": "flushed between timed solves (%d MB write)" %
                                                         (L2_FLUSH_BYTES >> 20),
                            "parallelism": "replicas x%d" % world},
-                "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(), "e2e": e2e,
-                "gpu_launches": args.steps * launches_per_solve(cfg, nsnap)}
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(), "e2e": e2e, "gradient": grad,
+                "gpu_launches": args.steps * launches_per_solve(cfg, nsnap, path)}
         print(json.dumps(line), flush=True)
     sim.close()
     if dist:

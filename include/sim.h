@@ -103,6 +103,11 @@ typedef struct {
     long long cells_per_shot; /* padded cells updated per shot per step */
     size_t device_bytes;      /* device memory the handle owns (0 from sim_plan) */
     int tile_x, tile_y, tile_z; /* tile of the stencil kernels the autotuner chose */
+    int last_path;            /* how the last sim_forward ran: 0 none yet, 1 one kernel launch per
+                                 step (captured as a CUDA graph), 2 resident: the whole time loop in
+                                 one cooperative launch that keeps the wavefield on chip (2D FP32
+                                 runs whose subdomains all fit on the GPU at once), 3 the 3D path */
+    int last_rows;            /* path 2: rows per resident subdomain (x 128 columns) */
 } sim_info;
 
 typedef struct sim_s *sim_t;

@@ -43,7 +43,7 @@ class SimInfo(ctypes.Structure):
         ("courant_exact", ctypes.c_double), ("vmin", ctypes.c_double), ("vmax", ctypes.c_double),
         ("c_damp", ctypes.c_double * 6), ("cells_per_shot", ctypes.c_longlong),
         ("device_bytes", ctypes.c_size_t), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
-        ("tile_z", ctypes.c_int),
+        ("tile_z", ctypes.c_int), ("last_path", ctypes.c_int), ("last_rows", ctypes.c_int),
     ]
 
 

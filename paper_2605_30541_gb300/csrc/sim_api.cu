@@ -11,6 +11,7 @@
 #include <mutex>
 #include <new>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "sim_internal.h"
@@ -236,6 +237,8 @@ struct sim_s {
     bool use_graphs = true;
     int tuned_nshots = 0;  // shot count the tile shape was tuned for (0: not yet)
     Pt3 *src3 = nullptr, *rec3 = nullptr;  // 3D point tables
+    int *rdone = nullptr;                  // resident path: step counter per (shot, subdomain)
+    int last_path = 0, last_rows = 0;      // see sim_info
     int zchunk = 0;                        // z-march chunk of the 3D kernel
     // adjoint-state buffers, allocated by the first sim_adjoint call
     bool adj_ready = false;
@@ -819,12 +822,60 @@ sim_status forward3d(sim_t s, int nshots, const void *wav, const double *src_pos
     });
 }
 
+// Polls a dataflow wait makes before it gives up (GSIM_SPIN_LIMIT overrides).
+long long spin_limit() {
+    long long v = 1LL << 22;
+    if (const char *f = getenv("GSIM_SPIN_LIMIT")) v = atoll(f);
+    return v;
+}
+
+// Resident forward path (resident2d.cu): the subdomain height unit RZ
+// (subdomains of 128 x 16 RZ cells) when every (shot, subdomain) of this run
+// fits on the GPU at once, else 0 and the per-step kernel runs. Smallest RZ
+// first: more, smaller subdomains shorten each step. 2D FP32 forward runs
+// with FP32 (or no) snapshots only; GSIM_RESIDENT=0 turns the path off.
+int resident_rz(sim_t s, int nshots) {
+    if (s->g.ndim != 2 || s->d.precision != SIM_FP32 || s->d.snap_fp16 || !s->rdone) return 0;
+    const char *f = getenv("GSIM_RESIDENT");
+    if (f && f[0] == '0') return 0;
+    int sms = 0, coop = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->dev);
+    if (!coop || sms <= 0) return 0;
+    const long long ntx = (s->g.NX + kTileXF - 1) / kTileXF;
+    for (int rz = 1; rz <= 4; rz++) {
+        const int wz = kResidentWarps * rz;
+        const long long blocks = ntx * ((s->g.NZ + wz - 1) / wz) * nshots;
+        if (blocks > (long long)s->d.max_shots * max_tiles(s)) continue;  // step counters
+        const int bps = resident2d_blocks_per_sm(rz, s->d.bc);
+        if (bps > 0 && blocks <= (long long)bps * sms) return rz;
+    }
+    return 0;
+}
+
+// One cooperative launch for the whole time loop, after zeroing the step
+// counters; ordered on the handle's stream like any other work.
+template <typename T>
+sim_status run_resident(sim_t s, const StepArgs<T> &a, int rz, int nshots);
+template <>
+sim_status run_resident<double>(sim_t s, const StepArgs<double> &, int, int) {
+    return s->fail(SIM_ERR_UNSUPPORTED, "the resident path is FP32 only");
+}
+template <>
+sim_status run_resident<float>(sim_t s, const StepArgs<float> &a, int rz, int nshots) {
+    const size_t n = (size_t)a.ntx * a.ntz * nshots;
+    if (sim_status r = s->cuda(cudaMemsetAsync(s->rdone, 0, n * sizeof(int), s->st), "step counters")) return r;
+    ResidentArgs r{s->rdone, spin_limit()};
+    return s->cuda(launch_resident2d(a, r, rz, nshots, s->st), "resident launch");
+}
+
 template <typename T>
 sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src_pos, int nrec,
                      const double *rec_pos, void *gather, void *snaps, float *snap_scale) {
     const sim_desc &d = s->d;
     const Geom &g = s->g;
-    if (g.ndim == 2)
+    const int rz = std::is_same<T, float>::value ? resident_rz(s, nshots) : 0;
+    if (g.ndim == 2 && !rz)
         if (sim_status r = autotune(s, nshots)) return r;
     const size_t nt = d.nt;
     // inputs
@@ -858,9 +909,18 @@ sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src
         return s->fail(SIM_ERR_ARG, "FP16 snapshots need a snap_scale array");
 
     if (g.ndim == 3) {
+        s->last_path = 3;
         if (sim_status r = forward3d(s, nshots, wav, src_pos, nrec, rec_pos, gdev, sdev, scdev)) return r;
     } else {
-    // geometry lists
+    // geometry lists, per tile of the kernel that runs (the resident
+    // subdomains are tiles of 128 x 16 RZ; the handle's tuned tile height is
+    // restored when this scope ends)
+    struct TileScope {
+        sim_t s;
+        int tz;
+        ~TileScope() { set_tile_z(s, tz); }
+    } tile_scope{s, s->tile_z};
+    if (rz) set_tile_z(s, kResidentWarps * rz);
     std::vector<int> rstart, istart;
     std::vector<RecEntryT<T>> rent;
     std::vector<InjGroup> igrp;
@@ -894,14 +954,20 @@ sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src
     StepArgs<T> a = step_args<T>(s);
     a.inj_per_shot = 1;
     a.inj_kind = 0;
-    if (sim_status r = run_graph(s, ((long long)nshots << 8) | ((long long)s->tile_z << 2) | 1, [&](cudaStream_t st) {
-            for (int n = 0; n < d.nt; n++) {
-                cudaError_t e = launch_step<T>(s, a, n, nshots, kModeForward, st);
-                if (e != cudaSuccess) return e;
-            }
-            return cudaSuccess;
-        }))
+    s->last_path = rz ? 2 : 1;
+    s->last_rows = rz ? kResidentWarps * rz : 0;
+    if (rz) {
+        if (sim_status r = run_resident(s, a, rz, nshots)) return r;
+    } else if (sim_status r = run_graph(s, ((long long)nshots << 8) | ((long long)s->tile_z << 2) | 1,
+                                        [&](cudaStream_t st) {
+                                            for (int n = 0; n < d.nt; n++) {
+                                                cudaError_t e = launch_step<T>(s, a, n, nshots, kModeForward, st);
+                                                if (e != cudaSuccess) return e;
+                                            }
+                                            return cudaSuccess;
+                                        })) {
         return r;
+    }
     }
     // the buffer written last holds p^nt
     const T *last = static_cast<const T *>(s->pbuf) + ((d.nt & 1) ? (long long)d.max_shots * g.fstride : 0);
@@ -1357,8 +1423,7 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
     b.done = static_cast<int *>(ctx->done);
     b.head = ctx->head;
     b.total = total;
-    b.spin_limit = 1LL << 22;
-    if (const char *f = getenv("GSIM_SPIN_LIMIT")) b.spin_limit = atoll(f);
+    b.spin_limit = spin_limit();
     b.flags = ctx->flags;
     const int grid = sms * std::max(1, batch_blocks_per_sm(tz, any_cpml));
     // counters reset + the persistent kernel, replayed as one graph
@@ -1516,6 +1581,10 @@ sim_status sim_create(const sim_desc *din, const void *vel, void *cuda_stream, s
     if (rc == SIM_OK) rc = s->cuda(cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming), "event");
     if (rc == SIM_OK) rc = s->cuda(cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming), "event");
     if (rc == SIM_OK && d.precision == SIM_FP32) rc = s->cuda(configure_step2d_f32(), "kernel configuration");
+    if (rc == SIM_OK && d.precision == SIM_FP32 && d.ndim == 2) {
+        rc = s->cuda(configure_resident2d(), "kernel configuration");
+        s->rdone = static_cast<int *>(A(sizeof(int) * ms * max_tiles(s)));
+    }
     if (rc == SIM_OK && d.ndim == 3) {
         rc = s->cuda(configure_step3d(), "kernel configuration");
         s->src3 = static_cast<Pt3 *>(A(sizeof(Pt3) * ms));
@@ -1607,6 +1676,8 @@ sim_status sim_get_info(sim_t s, sim_info *out) {
     fill_info(s->d, out);
     out->tile_x = s->tile_x;
     out->tile_z = s->tile_z;
+    out->last_path = s->last_path;
+    out->last_rows = s->last_rows;
     out->vmin = s->vmin;
     out->vmax = s->vmax;
     out->courant = s->vmax * s->d.dt / s->d.h;

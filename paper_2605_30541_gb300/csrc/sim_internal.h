@@ -186,6 +186,21 @@ cudaError_t launch_inject3d(const StepArgs<float> &a, const StepTime &t, const v
                             cudaStream_t st);
 cudaError_t launch_snap3d(const StepArgs<float> &a, const StepTime &t, int fp16, int nshots, cudaStream_t st);
 
+// Resident execution (resident2d.cu): one cooperative launch runs the whole
+// forward time loop of a 2D FP32 problem whose state fits on chip; each CTA
+// of kResidentWarps warps owns a 128 x (16 RZ) subdomain. done[] holds one
+// step counter per (shot, subdomain), zeroed before the launch.
+constexpr int kResidentWarps = 16;
+constexpr size_t kResidentMaxSmem = 227 * 1024;
+struct ResidentArgs {
+    int *done;
+    long long spin_limit;
+};
+cudaError_t configure_resident2d();
+int resident2d_blocks_per_sm(int rz, int bc);  // 0: does not fit
+cudaError_t launch_resident2d(const StepArgs<float> &a, const ResidentArgs &r, int rz, int nshots,
+                              cudaStream_t st);
+
 // Message returned by sim_last_error(NULL) for failures of this thread.
 void set_thread_error(const char *msg);
 

@@ -14,6 +14,19 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
+@pytest.fixture(autouse=True)
+def per_step_forward():
+    # the bit-for-bit comparisons below are against the per-step kernel path,
+    # whose per-tile function the batch kernel shares
+    old = os.environ.get("GSIM_RESIDENT")
+    os.environ["GSIM_RESIDENT"] = "0"
+    yield
+    if old is None:
+        os.environ.pop("GSIM_RESIDENT", None)
+    else:
+        os.environ["GSIM_RESIDENT"] = old
+
+
 @pytest.fixture(scope="module")
 def pkg():
     if not torch.cuda.is_available():
