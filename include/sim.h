@@ -107,7 +107,7 @@ typedef struct {
                                  step (captured as a CUDA graph), 2 resident: the whole time loop in
                                  one cooperative launch that keeps the wavefield on chip (2D FP32
                                  runs whose subdomains all fit on the GPU at once), 3 the 3D path */
-    int last_rows;            /* path 2: rows per resident subdomain (x 128 columns) */
+    int last_rows;            /* path 2: rows of the tallest resident subdomain (x 128 columns) */
 } sim_info;
 
 typedef struct sim_s *sim_t;

@@ -4,8 +4,11 @@
 // The per-step kernel (fwd2d_f32.cu) pays, every step, a launch, a grid-wide
 // dependency and a reload of p^n, p^{n-1} and c from L2. On a slice of a few
 // hundred thousand to about a million cells the whole state fits in the SMs'
-// shared memory and registers, so here each CTA owns one 128 x WZ
-// subdomain (WZ = 16 RZ rows) for the entire run:
+// shared memory and registers, so here each CTA owns one subdomain of 128
+// columns and at most WZ = 16 RZ rows for the entire run. Subdomain heights
+// vary (RTile descriptors from the host): subdomains with absorbing work get
+// fewer rows, so every CTA takes about as long per step; warps take
+// ceil(rows / 16) consecutive rows each.
 //   - p^n with an 8-cell halo lives in shared memory in two buffers; the
 //     other buffer's own cells still hold p^{n-1}, which each thread reads
 //     and overwrites with p^{n+1} in place; c stays in registers;
@@ -23,9 +26,10 @@
 //     step has no division;
 //   - after each step a CTA publishes the 8 (4 without CPML) border rows and
 //     columns of p^{n+1} to the global pressure buffer and raises its step
-//     counter (release); a CTA starts step n once its four edge neighbours'
-//     counters reach n (acquire) and copies their borders in as its halo.
-//     The stencil is a cross, so corner neighbours are never needed.
+//     counter (release); a CTA starts step n once the counters of the
+//     subdomains above, below and beside it (its descriptor lists them)
+//     reach n (acquire), and copies their borders in as its halo. The
+//     stencil is a cross, so corner neighbours are never needed.
 // The launch is cooperative, so all CTAs are co-resident and the waits
 // always end; each wait is still bounded (spin_limit polls), after which the
 // kernel raises kFlagTimeout and every CTA returns.
@@ -66,24 +70,24 @@ constexpr size_t rsmem_x(int bc) {
 template <int RZ>
 constexpr size_t rsmem_floats(int bc) {
     constexpr size_t WZ = (size_t)NWR * RZ;
-    return 2 * (WZ + 2 * HM) * SW + WZ * TX + rsmem_x<RZ>(bc) + 6 * (size_t)kRecCache;
+    const size_t coef = bc == SIM_BC_CPML ? 2 * (TX + 8) + 2 * (WZ + 8) : 0;  // CPML a, b slices
+    return 2 * (WZ + 2 * HM) * SW + WZ * TX + rsmem_x<RZ>(bc) + coef + 6 * (size_t)kRecCache;
 }
 
-// Tile-local hull [lo, hi) of the absorbing strips [0, nb0) and [N - nb1, N)
-// of one axis, clipped to [clip0, clip1); lo >= hi when it is empty.
+// Tile-local hull [lo, hi) of the parts of the absorbing strips [0, nb0) and
+// [N - nb1, N) of one axis that fall in [clip0, clip1) (tile coordinates,
+// origin o); lo >= hi when neither strip reaches the window.
 __device__ __forceinline__ void strip_hull(int o, int N, int nb0, int nb1, int clip0, int clip1, int &lo, int &hi) {
     lo = 1 << 30;
     hi = -(1 << 30);
     if (nb0 > 0) {
-        lo = min(lo, -o);
-        hi = max(hi, nb0 - o);
+        const int a = max(-o, clip0), b = min(nb0 - o, clip1);
+        if (a < b) lo = min(lo, a), hi = max(hi, b);
     }
     if (nb1 > 0) {
-        lo = min(lo, N - nb1 - o);
-        hi = max(hi, N - o);
+        const int a = max(N - nb1 - o, clip0), b = min(N - o, clip1);
+        if (a < b) lo = min(lo, a), hi = max(hi, b);
     }
-    lo = max(lo, clip0);
-    hi = min(hi, clip1);
 }
 
 template <int RZ>
@@ -104,17 +108,21 @@ __global__ void __launch_bounds__(NTR, 1) k_resident2d(const StepArgs<float> A, 
     float *const AX = ZZ + WZ * TX;                // WZ x TX: D1x psi_x + zeta_x
     // sponge update weights
     float *const KA = X0, *const KB = X0 + WZ * TX, *const KC = X0 + 2 * WZ * TX;
+    // CPML recursion coefficients of the subdomain: x in [-4, TX + 4), rows [-4, WZ + 4)
+    float *const CAX = X0 + rsmem_x<RZ>(A.bc), *const CBX = CAX + TX + 8;
+    float *const CAZ = CBX + TX + 8, *const CBZ = CAZ + WZ + 8;
     // receiver cache
-    int *const RIDX = reinterpret_cast<int *>(X0 + rsmem_x<RZ>(A.bc));
+    int *const RIDX = reinterpret_cast<int *>(X0 + rsmem_x<RZ>(A.bc) + (cpml ? 2 * (TX + 8) + 2 * (WZ + 8) : 0));
     int *const ROFF = RIDX + kRecCache;
     float *const RW = reinterpret_cast<float *>(ROFF + kRecCache);
 
     const Geom &g = A.g;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, tid = threadIdx.x;
-    const int ntiles = A.ntx * A.ntz;
+    const int ntiles = R.ntiles;
     const int shot = blockIdx.x / ntiles, tile = blockIdx.x - shot * ntiles;
-    const int bz = tile / A.ntx, bx = tile - bz * A.ntx;
-    const int x0 = bx * TX, z0 = bz * WZ, P = g.P;
+    const RTile *const D = R.tiles + tile;
+    const int bx = D->bx, x0 = bx * TX, z0 = D->z0, rows = D->rows, rpw = D->rpw, P = g.P;
+    const int my_nbr = lane < D->nnbr ? D->nbr[lane] : -1;  // the subdomain lane polls (warp 0)
     const long long sh = (long long)shot * g.fstride;
     const long long org = cell_off(g, z0, 0, x0);
     float *const gb0 = A.pbuf[0] + sh + org;
@@ -124,21 +132,20 @@ __global__ void __launch_bounds__(NTR, 1) k_resident2d(const StepArgs<float> A, 
     const bool cpx = cpml && A.ca[2] &&
                      ((g.nbx0 > 0 && x0 - 4 < g.nbx0) || (g.nbx1 > 0 && x0 + TX + 4 > g.NX - g.nbx1));
     const bool cpz = cpml && A.ca[0] &&
-                     ((g.nbz0 > 0 && z0 - 4 < g.nbz0) || (g.nbz1 > 0 && z0 + WZ + 4 > g.NZ - g.nbz1));
+                     ((g.nbz0 > 0 && z0 - 4 < g.nbz0) || (g.nbz1 > 0 && z0 + rows + 4 > g.NZ - g.nbz1));
     const bool spg = A.bc == SIM_BC_SPONGE &&
                      ((g.nbx0 > 0 && x0 < g.nbx0) || (g.nbx1 > 0 && x0 + TX > g.NX - g.nbx1) ||
-                      (g.nbz0 > 0 && z0 < g.nbz0) || (g.nbz1 > 0 && z0 + WZ > g.NZ - g.nbz1));
+                      (g.nbz0 > 0 && z0 < g.nbz0) || (g.nbz1 > 0 && z0 + rows > g.NZ - g.nbz1));
     const bool xedge = x0 + TX > g.NX;
-    const bool zedge = z0 + WZ > g.NZ;
     const bool top = g.fs && z0 == 0;
     const int H = cpml ? 8 : 4;                   // exchanged border depth
-    const bool hasN = bz > 0, hasS = bz + 1 < A.ntz, hasW = bx > 0, hasE = bx + 1 < A.ntx;
-    const int c0 = HM + 4 * lane, gx0 = x0 + 4 * lane, rb = HM + w * RZ;
-    const int lo = w * RZ * P + 4 * lane;
+    const bool hasN = z0 > 0, hasS = z0 + rows < g.NZ, hasW = bx > 0, hasE = x0 + TX < g.NX;
+    const int c0 = HM + 4 * lane, gx0 = x0 + 4 * lane, rb = HM + w * rpw;
+    const int lo = w * rpw * P + 4 * lane;
 
     // CPML work ranges. x: psi on float4 chunks cx0 <= c < cx1 of PX (chunk c
     // holds cells [4c - 4, 4c)), zeta_x / addend on own chunks [ax0, ax1).
-    // z: psi on rows [zp0, zp1) of [-4, WZ + 4), zeta_z on rows [zz0, zz1).
+    // z: psi on rows [zp0, zp1) of [-4, rows + 4), zeta_z on rows [zz0, zz1).
     int cx0 = 0, cx1 = 0, ax0 = 0, ax1 = 0, zp0 = 0, zp1 = 0, zz0 = 0, zz1 = 0;
     if (cpx) {
         int plo, phi;
@@ -151,10 +158,10 @@ __global__ void __launch_bounds__(NTR, 1) k_resident2d(const StepArgs<float> A, 
         }
     }
     if (cpz) {
-        strip_hull(z0, g.NZ, g.nbz0, g.nbz1, -4, WZ + 4, zp0, zp1);
+        strip_hull(z0, g.NZ, g.nbz0, g.nbz1, -4, rows + 4, zp0, zp1);
         if (zp0 < zp1) {
             zz0 = max(0, zp0 - 4);
-            zz1 = min(WZ, zp1 + 4);
+            zz1 = min(rows, zp1 + 4);
         } else {
             zp0 = zp1 = 0;
         }
@@ -173,16 +180,28 @@ __global__ void __launch_bounds__(NTR, 1) k_resident2d(const StepArgs<float> A, 
     float4 ch4[RZ];
 #pragma unroll
     for (int j = 0; j < RZ; j++) {
-        const bool in = z0 + w * RZ + j < g.NZ;
+        const bool in = j < rpw && w * rpw + j < rows;
         ch4[j] = in ? __ldg(reinterpret_cast<const float4 *>(A.ch + org + lo + j * P)) : make_float4(0, 0, 0, 0);
+    }
+    if (cpml) {
+        for (int i = tid; i < TX + 8; i += NTR) {
+            CAX[i] = A.ca[2] ? A.ca[2][x0 - 4 + i] : 0.f;
+            CBX[i] = A.cb[2] ? A.cb[2][x0 - 4 + i] : 0.f;
+        }
+        for (int i = tid; i < WZ + 8; i += NTR) {
+            const int gz = z0 - 4 + i;
+            const bool in = A.ca[0] && gz >= 0 && gz < g.NZ;
+            CAZ[i] = in ? A.ca[0][gz] : 0.f;
+            CBZ[i] = in ? A.cb[0][gz] : 0.f;
+        }
     }
     __syncthreads();
     if (spg) {  // sponge: out = KA p - KB p^{n-1} + KC rhs, a = c (eta_z + eta_x)
         const float4 E4 = __ldg(reinterpret_cast<const float4 *>(A.E[2] + gx0));
 #pragma unroll
         for (int j = 0; j < RZ; j++) {
-            const int lz = w * RZ + j, gz = z0 + lz;
-            if (gz >= g.NZ) continue;
+            const int lz = w * rpw + j, gz = z0 + lz;
+            if (j >= rpw || lz >= rows) continue;
             const float ez = A.E[0][gz];
             float ka[4], kb[4], kc[4];
 #pragma unroll
@@ -237,17 +256,13 @@ __global__ void __launch_bounds__(NTR, 1) k_resident2d(const StepArgs<float> A, 
         if (has_inj && n + 1 < A.nt) wnext = wav[n + 1];
 
         if (n > 0) {
-            // the four edge neighbours must have published p^n
+            // the subdomains whose borders form the halo must have published p^n
             if (w == 0) {
-                const int nb = lane == 0   ? (hasN ? tile - A.ntx : -1)
-                               : lane == 1 ? (hasS ? tile + A.ntx : -1)
-                               : lane == 2 ? (hasW ? tile - 1 : -1)
-                               : lane == 3 ? (hasE ? tile + 1 : -1)
-                                           : -1;
+                const int nb = my_nbr;
                 bool need = nb >= 0, quit = false;
                 long long spins = 0;
                 for (;;) {
-                    if (need && ld_relaxed(done + nb) >= n) need = false;
+                    if (need && ld_acquire(done + nb) >= n) need = false;
                     if (!__any_sync(0xffffffffu, need)) break;
                     if (++spins > R.spin_limit) {
                         quit = true;
@@ -262,7 +277,6 @@ __global__ void __launch_bounds__(NTR, 1) k_resident2d(const StepArgs<float> A, 
                         }
                     }
                 }
-                if (nb >= 0 && !quit) fence_acq_rel();
                 if (lane == 0) s_abort = quit;
             }
             __syncthreads();
@@ -275,19 +289,19 @@ __global__ void __launch_bounds__(NTR, 1) k_resident2d(const StepArgs<float> A, 
                 }
             if (hasS)
                 for (int i = tid; i < H * 32; i += NTR) {
-                    const int r = WZ + (i >> 5), c = 4 * (i & 31);
+                    const int r = rows + (i >> 5), c = 4 * (i & 31);
                     cp_async16(cur + (HM + r) * SW + HM + c, gcur + r * P + c);
                 }
             const int hq = H / 4;
             if (hasW)
-                for (int i = tid; i < WZ * hq; i += NTR) {
+                for (int i = tid; i < rows * hq; i += NTR) {
                     const int r = i / hq, q = i - r * hq;
-                    if (z0 + r < g.NZ) cp_async16(cur + (HM + r) * SW + HM - H + 4 * q, gcur + r * P - H + 4 * q);
+                    cp_async16(cur + (HM + r) * SW + HM - H + 4 * q, gcur + r * P - H + 4 * q);
                 }
             if (hasE)
-                for (int i = tid; i < WZ * hq; i += NTR) {
+                for (int i = tid; i < rows * hq; i += NTR) {
                     const int r = i / hq, q = i - r * hq;
-                    if (z0 + r < g.NZ) cp_async16(cur + (HM + r) * SW + HM + TX + 4 * q, gcur + r * P + TX + 4 * q);
+                    cp_async16(cur + (HM + r) * SW + HM + TX + 4 * q, gcur + r * P + TX + 4 * q);
                 }
             cp_async_wait_all();
         }
@@ -307,13 +321,12 @@ __global__ void __launch_bounds__(NTR, 1) k_resident2d(const StepArgs<float> A, 
 
         // CPML psi^n = b psi^{n-1} + a D1 p^n (scaled by h) on the strips
         if (ncx > 0) {
-            for (int i = tid; i < WZ * ncx; i += NTR) {
+            for (int i = tid; i < rows * ncx; i += NTR) {
                 const int lz = i / ncx, c = cx0 + (i - lz * ncx), gz = z0 + lz, gx = x0 + 4 * c - 4;
                 const float *row = cur + (HM + lz) * SW + HM + 4 * c - 4;
                 float v[12];
                 unpack3(ld4(row - 4), ld4(row), ld4(row + 4), v);
-                const float4 a4 = __ldg(reinterpret_cast<const float4 *>(A.ca[2] + gx));
-                const float4 b4 = __ldg(reinterpret_cast<const float4 *>(A.cb[2] + gx));
+                const float4 a4 = ld4(CAX + 4 * c), b4 = ld4(CBX + 4 * c);
                 float *px = PX + lz * (TX + 8) + 4 * c;
                 const float4 old = ld4(px);
                 float o4[4];
@@ -333,7 +346,7 @@ __global__ void __launch_bounds__(NTR, 1) k_resident2d(const StepArgs<float> A, 
 #pragma unroll
                 for (int m = 0; m < 9; m++) q[m] = ld4(col + (m - 4) * SW);
                 const bool zin = gz >= 0 && gz < g.NZ;
-                const float az = zin ? __ldg(A.ca[0] + gz) : 0.f, bz = zin ? __ldg(A.cb[0] + gz) : 0.f;
+                const float az = CAZ[lzz + 4], bz = CBZ[lzz + 4];
                 float *pz = PZ + (lzz + 4) * TX + 4 * lane;
                 const float4 old = ld4(pz);
                 float o4[4];
@@ -353,16 +366,14 @@ __global__ void __launch_bounds__(NTR, 1) k_resident2d(const StepArgs<float> A, 
         // zeta_x^n = b zeta_x^{n-1} + a (D2x p^n + D1x psi_x^n) and the addend
         // D1x psi_x^n + zeta_x^n on the widened x-strips
         if (nax > 0) {
-            for (int i = tid; i < WZ * nax; i += NTR) {
-                const int lz = i / nax, c = ax0 + (i - lz * nax), gz = z0 + lz, gx = x0 + 4 * c;
-                if (gz >= g.NZ) continue;
+            for (int i = tid; i < rows * nax; i += NTR) {
+                const int lz = i / nax, c = ax0 + (i - lz * nax);
                 float v[12], px[12];
                 const float *row = cur + (HM + lz) * SW + HM + 4 * c;
                 unpack3(ld4(row - 4), ld4(row), ld4(row + 4), v);
                 const float *pr = PX + lz * (TX + 8) + 4 * c;
                 unpack3(ld4(pr), ld4(pr + 4), ld4(pr + 8), px);
-                const float4 a4 = __ldg(reinterpret_cast<const float4 *>(A.ca[2] + gx));
-                const float4 b4 = __ldg(reinterpret_cast<const float4 *>(A.cb[2] + gx));
+                const float4 a4 = ld4(CAX + 4 * c + 4), b4 = ld4(CBX + 4 * c + 4);
                 float *zp = ZX + lz * TX + 4 * c;
                 const float4 z4 = ld4(zp);
                 float zo[4], ad[4];
@@ -384,8 +395,8 @@ __global__ void __launch_bounds__(NTR, 1) k_resident2d(const StepArgs<float> A, 
         for (int j = 0; j < RZ + 8; j++) zw[j] = ld4(cur + (rb - 4 + j) * SW + c0);
 #pragma unroll
         for (int j = 0; j < RZ; j++) {
-            const int lz = w * RZ + j, gz = z0 + lz;
-            if (zedge && gz >= g.NZ) continue;
+            const int lz = w * rpw + j, gz = z0 + lz;
+            if (j >= rpw || lz >= rows) continue;
             float v[12];
             unpack3(ld4(cur + (rb + j) * SW + c0 - 4), zw[j + 4], ld4(cur + (rb + j) * SW + c0 + 4), v);
             const float4 pp4 = ld4(nxt + (rb + j) * SW + c0);  // p^{n-1}
@@ -413,8 +424,8 @@ __global__ void __launch_bounds__(NTR, 1) k_resident2d(const StepArgs<float> A, 
                 for (int k = 0; k < 4; k++) d[k] += float(kD4) * (lane_of(a, k) - lane_of(b, k));
                 dz4 = make_float4(d[0], d[1], d[2], d[3]);
                 zz4 = ld4(ZZ + lz * TX + 4 * lane);
-                az = __ldg(A.ca[0] + gz);
-                bzc = __ldg(A.cb[0] + gz);
+                az = CAZ[lz + 4];
+                bzc = CBZ[lz + 4];
             }
             float4 ka4 = make_float4(0, 0, 0, 0), kb4 = ka4, kc4 = ka4;
             if (spg) {
@@ -452,7 +463,7 @@ __global__ void __launch_bounds__(NTR, 1) k_resident2d(const StepArgs<float> A, 
             if (top && lz == 0) res[0] = res[1] = res[2] = res[3] = 0.f;
             const float4 r4 = make_float4(res[0], res[1], res[2], res[3]);
             st4(nxt + (rb + j) * SW + c0, r4);
-            const bool border = (hasN && lz < H) || (hasS && lz >= WZ - H) || (hasW && 4 * lane < H) ||
+            const bool border = (hasN && lz < H) || (hasS && lz >= rows - H) || (hasW && 4 * lane < H) ||
                                 (hasE && 4 * lane >= TX - H);
             if (border) st4(gnxt + lo + j * P, r4);
         }
@@ -491,8 +502,8 @@ __global__ void __launch_bounds__(NTR, 1) k_resident2d(const StepArgs<float> A, 
             const long long sbase = ((long long)shot * A.nsnap + snap_k) * g.nz * g.nx;
 #pragma unroll
             for (int j = 0; j < RZ; j++) {
-                const int gz = z0 + w * RZ + j;
-                if (gz < g.oz || gz >= g.oz + g.nz) continue;
+                const int gz = z0 + w * rpw + j;
+                if (j >= rpw || w * rpw + j >= rows || gz < g.oz || gz >= g.oz + g.nz) continue;
                 const float4 p4 = ld4(cur + (rb + j) * SW + c0);
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
@@ -512,7 +523,7 @@ __global__ void __launch_bounds__(NTR, 1) k_resident2d(const StepArgs<float> A, 
         float *gl = (A.nt & 1) ? gb1 : gb0, *gp = (A.nt & 1) ? gb0 : gb1;
 #pragma unroll
         for (int j = 0; j < RZ; j++) {
-            if (z0 + w * RZ + j >= g.NZ) continue;
+            if (j >= rpw || w * rpw + j >= rows) continue;
             st4(gl + lo + j * P, ld4(fin + (rb + j) * SW + c0));
             st4(gp + lo + j * P, ld4(prv + (rb + j) * SW + c0));
         }
@@ -522,7 +533,7 @@ __global__ void __launch_bounds__(NTR, 1) k_resident2d(const StepArgs<float> A, 
 template <int RZ>
 cudaError_t launch_rz(const StepArgs<float> &a, const ResidentArgs &r, int nshots, cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(a.ntx * a.ntz * nshots);
+    cfg.gridDim = dim3(r.ntiles * nshots);
     cfg.blockDim = dim3(NTR);
     cfg.dynamicSmemBytes = rsmem_floats<RZ>(a.bc) * sizeof(float);
     cfg.stream = st;

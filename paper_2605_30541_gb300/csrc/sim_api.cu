@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <list>
 #include <map>
 #include <mutex>
 #include <new>
@@ -199,6 +200,21 @@ void gsim::set_thread_error(const char *msg) { t_err = msg; }
 
 // ============================================================== handle
 
+// Non-uniform 2D tiling (resident path): tile of each (column, row) and the
+// first row of each tile. Columns are kTileXF wide.
+struct TileMap {
+    int NZ = 0, ntiles = 0;
+    std::vector<int> tile;  // [bx * NZ + z]
+    std::vector<int> z0;    // [tile]
+};
+
+// Resident-path decomposition for one shot count (see plan_resident).
+struct ResidentPlan {
+    int rz = 0;  // 0: the run does not fit on chip
+    std::vector<RTile> tiles;
+    TileMap map;
+};
+
 struct sim_s {
     sim_desc d{};
     Geom g{};
@@ -238,6 +254,9 @@ struct sim_s {
     int tuned_nshots = 0;  // shot count the tile shape was tuned for (0: not yet)
     Pt3 *src3 = nullptr, *rec3 = nullptr;  // 3D point tables
     int *rdone = nullptr;                  // resident path: step counter per (shot, subdomain)
+    RTile *rtiles = nullptr;               // resident path: subdomain descriptors
+    const TileMap *tmap = nullptr;         // set while lists are built for a non-uniform tiling
+    std::list<std::pair<int, ResidentPlan>> rplans;  // per shot count
     int last_path = 0, last_rows = 0;      // see sim_info
     int zchunk = 0;                        // z-march chunk of the 3D kernel
     // adjoint-state buffers, allocated by the first sim_adjoint call
@@ -399,13 +418,29 @@ sim_status set_model_t(sim_t s, const void *vel) {
     return chk;
 }
 
+// Tile holding 2D cell (z, x) and the cell's tile-local coordinates, for
+// the uniform tiling of the handle or the non-uniform one being listed.
+int tiles_of(const sim_s *s) { return s->tmap ? s->tmap->ntiles : s->ntx * s->nty * s->ntz; }
+void tile_of(const sim_s *s, int z, int x, int &t, int &lz, int &lx) {
+    const int bx = x / s->tile_x;
+    if (s->tmap) {
+        t = s->tmap->tile[(size_t)bx * s->tmap->NZ + z];
+        lz = z - s->tmap->z0[t];
+    } else {
+        const int bz = z / s->tile_z;
+        t = bz * s->ntx + bx;
+        lz = z - bz * s->tile_z;
+    }
+    lx = x - bx * s->tile_x;
+}
+
 // Receivers: one entry per receiver, in the list of the tile that holds its
 // base cell; the stencil corners lie within that tile's radius-4 halo.
 template <typename T>
 sim_status build_receivers(sim_t s, int nrec, const double *rec_pos, std::vector<int> &start,
                            std::vector<RecEntryT<T>> &ent) {
     const Geom &g = s->g;
-    const int ntiles = s->ntx * s->nty * s->ntz;
+    const int ntiles = tiles_of(s);
     std::vector<std::pair<int, RecEntryT<T>>> tmp;
     tmp.reserve(nrec);
     for (int r = 0; r < nrec; r++) {
@@ -415,15 +450,14 @@ sim_status build_receivers(sim_t s, int nrec, const double *rec_pos, std::vector
             return s->fail(SIM_ERR_ARG, "receiver %d lies outside the interior", r);
         RecEntryT<T> e{};
         e.rec = r;
-        const int tz = i0[0] / s->tile_z, tx = i0[2] / s->tile_x;
-        e.lz = i0[0] - tz * s->tile_z;
+        int tl;
+        tile_of(s, i0[0], i0[2], tl, e.lz, e.lx);
         e.ly = 0;
-        e.lx = i0[2] - tx * s->tile_x;
         int k = 0;
         for (int dz = 0; dz < 2; dz++)
             for (int dy = 0; dy < (g.ndim == 3 ? 2 : 1); dy++)
                 for (int dx = 0; dx < 2; dx++) e.w[k++] = T(corner_weight(t, dz, dy, dx));
-        tmp.push_back({tz * s->ntx + tx, e});
+        tmp.push_back({tl, e});
     }
     std::stable_sort(tmp.begin(), tmp.end(), [](const auto &a, const auto &b) { return a.first < b.first; });
     start.assign(ntiles + 1, 0);
@@ -478,7 +512,7 @@ void group_injection(std::vector<InjPoint> &pts, int nlists, std::vector<int> &s
 sim_status collect_points(sim_t s, int npts, const double *pos, bool per_shot, std::vector<InjPoint> &out,
                           const char *what) {
     const Geom &g = s->g;
-    const int ntiles = s->ntx * s->nty * s->ntz;
+    const int ntiles = tiles_of(s);
     for (int q = 0; q < npts; q++) {
         int i0[3];
         double t[3];
@@ -491,10 +525,11 @@ sim_status collect_points(sim_t s, int npts, const double *pos, bool per_shot, s
                     if (w == 0.0) continue;
                     const int z = i0[0] + dz, x = i0[2] + dx;
                     if (g.fs && z == 0) continue;
-                    const int tz = z / s->tile_z, tx = x / s->tile_x;
+                    int tl, lz, lx;
+                    tile_of(s, z, x, tl, lz, lx);
                     InjPoint p;
-                    p.tile = (per_shot ? q * ntiles : 0) + tz * s->ntx + tx;
-                    p.cell = (z - tz * s->tile_z) * s->tile_x + (x - tx * s->tile_x);
+                    p.tile = (per_shot ? q * ntiles : 0) + tl;
+                    p.cell = lz * s->tile_x + lx;
                     p.pt = q;
                     p.w = w;
                     out.push_back(p);
@@ -829,44 +864,155 @@ long long spin_limit() {
     return v;
 }
 
-// Resident forward path (resident2d.cu): the subdomain height unit RZ
-// (subdomains of 128 x 16 RZ cells) when every (shot, subdomain) of this run
-// fits on the GPU at once, else 0 and the per-step kernel runs. Smallest RZ
-// first: more, smaller subdomains shorten each step. 2D FP32 forward runs
-// with FP32 (or no) snapshots only; GSIM_RESIDENT=0 turns the path off.
-int resident_rz(sim_t s, int nshots) {
-    if (s->g.ndim != 2 || s->d.precision != SIM_FP32 || s->d.snap_fp16 || !s->rdone) return 0;
-    const char *f = getenv("GSIM_RESIDENT");
-    if (f && f[0] == '0') return 0;
+// Resident forward path (resident2d.cu). The slice is cut into columns of
+// kTileXF cells and each column into subdomains of at most 16 RZ rows, as
+// even in time per step as the GPU allows. Cost model (fitted to per-CTA
+// phase timings of this kernel, in units of one interior row): a subdomain
+// costs 50 (halo exchange and barriers) plus, per row, 1, plus 0.039 per
+// CPML x-strip float4 chunk its column updates, plus 1.34 within 4 rows of a
+// CPML z-strip. The smallest target cost whose subdomains (times the shots)
+// all fit on the GPU at once is chosen, trying RZ = 1, 2, ... 2D FP32 forward
+// runs with FP32 (or no) snapshots only; GSIM_RESIDENT=0 turns the path off.
+// CPML x-strip float4 chunks (psi and zeta) a column updates, as the kernel counts them.
+int strip_chunks(const Geom &g, int bx) {
+    const int x0 = bx * kTileXF;
+    int lo = 1 << 30, hi = -(1 << 30);
+    auto part = [&](int a, int b) {
+        a = std::max(a - x0, -4);
+        b = std::min(b - x0, kTileXF + 4);
+        if (a < b) lo = std::min(lo, a), hi = std::max(hi, b);
+    };
+    if (g.nbx0 > 0) part(0, g.nbx0);
+    if (g.nbx1 > 0) part(g.NX - g.nbx1, g.NX);
+    if (lo >= hi) return 0;
+    const int ncx = ((hi + 7) >> 2) - ((lo + 4) >> 2);
+    const int nax = ((std::min(kTileXF, hi + 4) + 3) >> 2) - (std::max(0, lo - 4) >> 2);
+    return ncx + nax;
+}
+
+bool cut_columns(const sim_s *s, int wz, double target, std::vector<RTile> &tiles) {
+    const Geom &g = s->g;
+    const bool cp = s->d.bc == SIM_BC_CPML;
+    const int ntx = (g.NX + kTileXF - 1) / kTileXF, hmin = 8;
+    tiles.clear();
+    for (int bx = 0; bx < ntx; bx++) {
+        const double cx = cp ? 0.039 * strip_chunks(g, bx) : 0.0;
+        int z = 0;
+        while (z < g.NZ) {
+            RTile t{};
+            t.bx = bx;
+            t.z0 = z;
+            double acc = 50.0;
+            while (z < g.NZ && t.rows < wz) {
+                const bool zs = cp && ((g.nbz0 > 0 && z < g.nbz0 + 4) || (g.nbz1 > 0 && z >= g.NZ - g.nbz1 - 4));
+                const double c = 1.0 + cx + (zs ? 1.34 : 0.0);
+                if (t.rows >= hmin && acc + c > target) break;
+                acc += c;
+                t.rows++;
+                z++;
+            }
+            tiles.push_back(t);
+        }
+        // a short last subdomain joins the one above when both fit in wz rows
+        const size_t k = tiles.size();
+        if (k >= 2 && tiles[k - 1].bx == bx && tiles[k - 2].bx == bx && tiles[k - 1].rows < hmin &&
+            tiles[k - 2].rows + tiles[k - 1].rows <= wz) {
+            tiles[k - 2].rows += tiles[k - 1].rows;
+            tiles.pop_back();
+        }
+    }
+    for (RTile &t : tiles) t.rpw = (t.rows + kResidentWarps - 1) / kResidentWarps;
+    return true;
+}
+
+// Neighbours of each subdomain: above and below in its column, and those of
+// the adjacent columns whose rows overlap its rows.
+bool link_tiles(std::vector<RTile> &tiles) {
+    for (size_t i = 0; i < tiles.size(); i++) {
+        RTile &t = tiles[i];
+        auto add = [&](size_t j) {
+            if (t.nnbr >= kResidentMaxNbr) return false;
+            t.nbr[t.nnbr++] = (int)j;
+            return true;
+        };
+        for (size_t j = 0; j < tiles.size(); j++) {
+            const RTile &u = tiles[j];
+            bool nb = false;
+            if (u.bx == t.bx) nb = u.z0 + u.rows == t.z0 || t.z0 + t.rows == u.z0;
+            else if (u.bx == t.bx - 1 || u.bx == t.bx + 1) nb = u.z0 < t.z0 + t.rows && t.z0 < u.z0 + u.rows;
+            if (nb && !add(j)) return false;
+        }
+    }
+    return true;
+}
+
+bool plan_resident_uncached(sim_t s, int nshots, ResidentPlan &plan) {
     int sms = 0, coop = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->dev);
-    if (!coop || sms <= 0) return 0;
-    const long long ntx = (s->g.NX + kTileXF - 1) / kTileXF;
+    if (!coop || sms <= 0) return false;
+    const long long cap_tiles = max_tiles(s);  // step counters and descriptors
     for (int rz = 1; rz <= 4; rz++) {
-        const int wz = kResidentWarps * rz;
-        const long long blocks = ntx * ((s->g.NZ + wz - 1) / wz) * nshots;
-        if (blocks > (long long)s->d.max_shots * max_tiles(s)) continue;  // step counters
         const int bps = resident2d_blocks_per_sm(rz, s->d.bc);
-        if (bps > 0 && blocks <= (long long)bps * sms) return rz;
+        if (bps <= 0) continue;
+        const long long cap = std::min((long long)bps * sms / nshots, cap_tiles);
+        const int wz = kResidentWarps * rz;
+        std::vector<RTile> t;
+        // the largest target gives uniform wz-row subdomains (the fewest)
+        if (!cut_columns(s, wz, 1e30, t) || (long long)t.size() > cap) continue;
+        double lo = 50, hi = 50 + 4.0 * wz;
+        for (int it = 0; it < 40; it++) {
+            const double mid = 0.5 * (lo + hi);
+            if (cut_columns(s, wz, mid, t) && (long long)t.size() <= cap) hi = mid;
+            else lo = mid;
+        }
+        if (!cut_columns(s, wz, hi, t) || (long long)t.size() > cap || !link_tiles(t)) continue;
+        plan.rz = rz;
+        plan.tiles = t;
+        TileMap &m = plan.map;
+        m.NZ = s->g.NZ;
+        m.ntiles = (int)t.size();
+        m.tile.assign((size_t)((s->g.NX + kTileXF - 1) / kTileXF) * m.NZ, -1);
+        m.z0.resize(t.size());
+        for (size_t i = 0; i < t.size(); i++) {
+            m.z0[i] = t[i].z0;
+            for (int r = 0; r < t[i].rows; r++) m.tile[(size_t)t[i].bx * m.NZ + t[i].z0 + r] = (int)i;
+        }
+        return true;
     }
-    return 0;
+    return false;
+}
+
+// The plan depends only on the grid and the shot count: kept per handle.
+const ResidentPlan *plan_resident(sim_t s, int nshots) {
+    if (s->g.ndim != 2 || s->d.precision != SIM_FP32 || s->d.snap_fp16 || !s->rdone) return nullptr;
+    const char *f = getenv("GSIM_RESIDENT");
+    if (f && f[0] == '0') return nullptr;
+    for (const auto &p : s->rplans)
+        if (p.first == nshots) return p.second.rz ? &p.second : nullptr;
+    s->rplans.emplace_back(nshots, ResidentPlan{});
+    ResidentPlan &p = s->rplans.back().second;
+    if (!plan_resident_uncached(s, nshots, p)) p = ResidentPlan{};
+    return p.rz ? &p : nullptr;
 }
 
 // One cooperative launch for the whole time loop, after zeroing the step
 // counters; ordered on the handle's stream like any other work.
 template <typename T>
-sim_status run_resident(sim_t s, const StepArgs<T> &a, int rz, int nshots);
+sim_status run_resident(sim_t s, const StepArgs<T> &a, const ResidentPlan &plan, int nshots);
 template <>
-sim_status run_resident<double>(sim_t s, const StepArgs<double> &, int, int) {
+sim_status run_resident<double>(sim_t s, const StepArgs<double> &, const ResidentPlan &, int) {
     return s->fail(SIM_ERR_UNSUPPORTED, "the resident path is FP32 only");
 }
 template <>
-sim_status run_resident<float>(sim_t s, const StepArgs<float> &a, int rz, int nshots) {
-    const size_t n = (size_t)a.ntx * a.ntz * nshots;
-    if (sim_status r = s->cuda(cudaMemsetAsync(s->rdone, 0, n * sizeof(int), s->st), "step counters")) return r;
-    ResidentArgs r{s->rdone, spin_limit()};
-    return s->cuda(launch_resident2d(a, r, rz, nshots, s->st), "resident launch");
+sim_status run_resident<float>(sim_t s, const StepArgs<float> &a, const ResidentPlan &plan, int nshots) {
+    const int nt = (int)plan.tiles.size();
+    if (sim_status r = upload(s, s->rtiles, plan.tiles, (size_t)max_tiles(s), "subdomains")) return r;
+    if (sim_status r = s->cuda(cudaMemsetAsync(s->rdone, 0, (size_t)nt * nshots * sizeof(int), s->st),
+                               "step counters"))
+        return r;
+    ResidentArgs r{s->rdone, spin_limit(), s->rtiles, nt};
+    return s->cuda(launch_resident2d(a, r, plan.rz, nshots, s->st), "resident launch");
 }
 
 template <typename T>
@@ -874,7 +1020,8 @@ sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src
                      const double *rec_pos, void *gather, void *snaps, float *snap_scale) {
     const sim_desc &d = s->d;
     const Geom &g = s->g;
-    const int rz = std::is_same<T, float>::value ? resident_rz(s, nshots) : 0;
+    const ResidentPlan *plan = std::is_same<T, float>::value ? plan_resident(s, nshots) : nullptr;
+    const int rz = plan ? plan->rz : 0;
     if (g.ndim == 2 && !rz)
         if (sim_status r = autotune(s, nshots)) return r;
     const size_t nt = d.nt;
@@ -913,14 +1060,12 @@ sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src
         if (sim_status r = forward3d(s, nshots, wav, src_pos, nrec, rec_pos, gdev, sdev, scdev)) return r;
     } else {
     // geometry lists, per tile of the kernel that runs (the resident
-    // subdomains are tiles of 128 x 16 RZ; the handle's tuned tile height is
-    // restored when this scope ends)
-    struct TileScope {
+    // subdomains while this scope lasts)
+    struct MapScope {
         sim_t s;
-        int tz;
-        ~TileScope() { set_tile_z(s, tz); }
-    } tile_scope{s, s->tile_z};
-    if (rz) set_tile_z(s, kResidentWarps * rz);
+        ~MapScope() { s->tmap = nullptr; }
+    } map_scope{s};
+    s->tmap = rz ? &plan->map : nullptr;
     std::vector<int> rstart, istart;
     std::vector<RecEntryT<T>> rent;
     std::vector<InjGroup> igrp;
@@ -929,8 +1074,7 @@ sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src
     std::vector<InjPoint> pts;
     if (wavelet)
         if (sim_status r = collect_points(s, nshots, src_pos, true, pts, "source")) return r;
-    const int ntiles = s->ntx * s->nty * s->ntz;
-    group_injection<T>(pts, nshots * ntiles, istart, igrp, ient);
+    group_injection<T>(pts, nshots * tiles_of(s), istart, igrp, ient);
     if (sim_status r = upload(s, s->rec_start, rstart, s->cap_start, "receiver start")) return r;
     if (sim_status r = upload(s, static_cast<RecEntryT<T> *>(s->rec), rent, s->cap_rec, "receiver")) return r;
     if (sim_status r = upload(s, s->inj_start, istart, s->cap_start, "injection start")) return r;
@@ -955,9 +1099,11 @@ sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src
     a.inj_per_shot = 1;
     a.inj_kind = 0;
     s->last_path = rz ? 2 : 1;
-    s->last_rows = rz ? kResidentWarps * rz : 0;
+    s->last_rows = 0;
+    if (rz)
+        for (const RTile &t : plan->tiles) s->last_rows = std::max(s->last_rows, t.rows);
     if (rz) {
-        if (sim_status r = run_resident(s, a, rz, nshots)) return r;
+        if (sim_status r = run_resident(s, a, *plan, nshots)) return r;
     } else if (sim_status r = run_graph(s, ((long long)nshots << 8) | ((long long)s->tile_z << 2) | 1,
                                         [&](cudaStream_t st) {
                                             for (int n = 0; n < d.nt; n++) {
@@ -1584,6 +1730,7 @@ sim_status sim_create(const sim_desc *din, const void *vel, void *cuda_stream, s
     if (rc == SIM_OK && d.precision == SIM_FP32 && d.ndim == 2) {
         rc = s->cuda(configure_resident2d(), "kernel configuration");
         s->rdone = static_cast<int *>(A(sizeof(int) * ms * max_tiles(s)));
+        s->rtiles = static_cast<RTile *>(A(sizeof(RTile) * max_tiles(s)));
     }
     if (rc == SIM_OK && d.ndim == 3) {
         rc = s->cuda(configure_step3d(), "kernel configuration");

@@ -188,13 +188,23 @@ cudaError_t launch_snap3d(const StepArgs<float> &a, const StepTime &t, int fp16,
 
 // Resident execution (resident2d.cu): one cooperative launch runs the whole
 // forward time loop of a 2D FP32 problem whose state fits on chip; each CTA
-// of kResidentWarps warps owns a 128 x (16 RZ) subdomain. done[] holds one
-// step counter per (shot, subdomain), zeroed before the launch.
+// of kResidentWarps warps owns one subdomain: columns [128 bx, 128 bx + 128),
+// rows [z0, z0 + rows) with rows <= 16 RZ, warps taking rpw rows each.
+// nbr lists the subdomains whose borders form its halo (same shot). done[]
+// holds one step counter per (shot, subdomain), zeroed before the launch.
 constexpr int kResidentWarps = 16;
 constexpr size_t kResidentMaxSmem = 227 * 1024;
+constexpr int kResidentMaxNbr = 11;
+struct RTile {
+    int bx, z0, rows, rpw;
+    int nnbr;
+    int nbr[kResidentMaxNbr];
+};
 struct ResidentArgs {
     int *done;
     long long spin_limit;
+    const RTile *tiles;  // device array, per shot
+    int ntiles;
 };
 cudaError_t configure_resident2d();
 int resident2d_blocks_per_sm(int rz, int bc);  // 0: does not fit

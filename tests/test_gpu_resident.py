@@ -107,7 +107,7 @@ def test_c2_field_slice(pkg):
     c = synth.config_c2(nt=1500)
     c.update(snap_every=50, snap_end=1500)
     res, info = check_case(pkg, c, c["vel"], c["wavelet"], c["src"], c["rec"], snaps=True)
-    assert info.last_rows == 48
+    assert 8 <= info.last_rows <= 48
 
 
 def test_repeat_calls_start_from_rest(pkg):
