@@ -287,13 +287,14 @@ def run_batch(args):
             "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "c3: 64 shots on a 619x1000 slice + 16 uneven slices x 8 shots, nt=%d, "
-                                   "one persistent launch per solve" % nt, "padded_cells_x_shots": cells,
+                                   "one launch per step over all slices and shots (stepped batch)" % nt,
+                       "padded_cells_x_shots": cells,
                        "l2": "flushed between timed solves"},
             "roofline": {"bound": "hbm", "achieved": algo / (total / args.steps) / 1e9, "peak": peak,
                          "unit": "GB/s", "frac": algo / (total / args.steps) / 1e9 / peak, "traffic": None,
-                         "kernel": "k_batch2d", "peak_kind": peak_kind,
+                         "kernel": "k_multi2d", "peak_kind": peak_kind,
                          "algorithmic_bytes_per_solve": algo},
-            "clocks": clk.summary(), "gpu_launches": args.steps}
+            "clocks": clk.summary(), "gpu_launches": args.steps * nt}
     print(json.dumps(line), flush=True)
     for s in sims:
         s.close()

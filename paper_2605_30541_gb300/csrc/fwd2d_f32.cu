@@ -553,6 +553,45 @@ __global__ void __launch_bounds__(NTH, 2) k_batch2d(const BatchArgs B) {
     }
 }
 
+// ---------------------------------------------------------------- stepped batch
+//
+// One step of every (slice, shot) member of a batch in one launch: block i
+// updates tile i - tile0 of the member whose tile range holds i (members
+// sorted by tile0), with that slice's arguments. A kernel boundary per step
+// orders the steps, so no waits are needed; launched with programmatic
+// dependent launch, the member lookup and the slice's run constants overlap
+// the previous step's tail.
+template <int TZ>
+__global__ void __launch_bounds__(NTH, 2) k_multi2d(const BatchArgs B, const int n) {
+    extern __shared__ float4 smem4[];
+    __shared__ float red[NW];
+    __shared__ StepArgs<float> sA;
+    __shared__ int s_m;
+    const int tid = threadIdx.x, i = blockIdx.x;
+    if (tid == 0) {
+        int lo = 0, hi = B.nmembers - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (B.members[mid].tile0 <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        s_m = lo;
+    }
+    __syncthreads();
+    const BatchMember M = B.members[s_m];
+    static_assert(sizeof(StepArgs<float>) % 8 == 0, "copied in 8-byte units");
+    const long long *src = reinterpret_cast<const long long *>(B.slices + M.slice);
+    long long *dst = reinterpret_cast<long long *>(&sA);
+    for (int k = tid; k < (int)(sizeof(StepArgs<float>) / 8); k += NTH) dst[k] = src[k];
+    __syncthreads();
+    const int tile = i - M.tile0, bz = tile / sA.ntx, bx = tile - bz * sA.ntx;
+    StepTime t{};
+    t.n = n;
+    t.snap_k = t.max_k = -1;
+    t.inj_row = n;
+    tile_step<TZ, kModeForward, true>(sA, t, bx, bz, M.shot, reinterpret_cast<float *>(smem4), red);
+}
+
 template <int TZ, int MODE>
 cudaError_t launch_mode(const StepArgs<float> &a, const StepTime &t, int nshots, cudaStream_t st, bool pdl) {
     const bool cp = a.bc == SIM_BC_CPML;
@@ -605,8 +644,31 @@ cudaError_t configure_step2d_f32() {
         e = tz == 8 ? cudaFuncSetAttribute(k_batch2d<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
             : tz == 16 ? cudaFuncSetAttribute(k_batch2d<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
                        : cudaFuncSetAttribute(k_batch2d<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess)
+            e = tz == 8 ? cudaFuncSetAttribute(k_multi2d<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+                : tz == 16 ? cudaFuncSetAttribute(k_multi2d<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+                           : cudaFuncSetAttribute(k_multi2d<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     }
     return e;
+}
+
+cudaError_t launch_multi2d(const BatchArgs &b, int tz, bool cpml, int nblocks, int n, cudaStream_t st, bool pdl) {
+    const size_t bytes = (tz == 8 ? smem_floats<8>(cpml) : tz == 16 ? smem_floats<16>(cpml) : smem_floats<32>(cpml)) *
+                         sizeof(float);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblocks);
+    cfg.blockDim = dim3(NTH);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    if (tz == 8) return cudaLaunchKernelEx(&cfg, k_multi2d<8>, b, n);
+    if (tz == 16) return cudaLaunchKernelEx(&cfg, k_multi2d<16>, b, n);
+    if (tz == 32) return cudaLaunchKernelEx(&cfg, k_multi2d<32>, b, n);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_batch2d(const BatchArgs &b, int tz, bool cpml, int grid, cudaStream_t st) {

@@ -1426,7 +1426,13 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
     }
     cudaSetDevice(s0->dev);
     const int nt = s0->d.nt;
-    int tz = 16;
+    // Two schedules: "stepped" (default) launches step n of every member at
+    // once, nt launches replayed as a graph (streams the batch through HBM at
+    // the per-step kernel's rate); "persistent" (GSIM_BATCH=persistent) runs
+    // the dataflow kernel k_batch2d, one launch for all steps.
+    const char *bm = getenv("GSIM_BATCH");
+    const bool stepped = !(bm && strcmp(bm, "persistent") == 0);
+    int tz = stepped ? 32 : 16;
     if (const char *f = getenv("GSIM_TILE_Z")) {
         const int v = atoi(f);
         if (v == 8 || v == 16 || v == 32) tz = v;
@@ -1561,10 +1567,21 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
         (e = cudaMemcpyAsync(ctx->members, members.data(), members.size() * sizeof(BatchMember),
                              cudaMemcpyHostToDevice, bst)))
         return fail(e, "upload");
+    if (stepped) {  // members with global tile offsets
+        long long t0 = 0;
+        for (BatchMember &m : members) {
+            m.tile0 = (int)t0;
+            t0 += items[m.slice].sim->ntx * items[m.slice].sim->ntz;
+        }
+        if ((e = cudaMemcpyAsync(ctx->members, members.data(), members.size() * sizeof(BatchMember),
+                                 cudaMemcpyHostToDevice, bst)))
+            return fail(e, "upload");
+    }
     BatchArgs b{};
     b.slices = static_cast<const StepArgs<float> *>(ctx->slices);
     b.groups = static_cast<const BatchGroup *>(ctx->groups);
     b.ngroups = (int)groups.size();
+    b.nmembers = (int)members.size();
     b.members = static_cast<const BatchMember *>(ctx->members);
     b.done = static_cast<int *>(ctx->done);
     b.head = ctx->head;
@@ -1575,7 +1592,7 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
     // counters reset + the persistent kernel, replayed as one graph
     std::vector<char> key(sizeof b + 3 * sizeof(int) + sizeof(long long));
     memcpy(key.data(), &b, sizeof b);
-    const int kk[3] = {tz, (int)any_cpml, grid};
+    const int kk[3] = {tz, (int)any_cpml | (stepped ? 2 : 0), grid};
     memcpy(key.data() + sizeof b, kk, sizeof kk);
     memcpy(key.data() + sizeof b + sizeof kk, &done_total, sizeof done_total);
     if (!ctx->exec || key != ctx->key || bst == nullptr) {
@@ -1583,6 +1600,12 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
         ctx->exec = nullptr;
     }
     auto body = [&](cudaStream_t st) {
+        if (stepped) {
+            cudaError_t r = cudaMemsetAsync(ctx->flags, 0, sizeof(unsigned), st);
+            for (int n = 0; n < nt && r == cudaSuccess; n++)
+                r = launch_multi2d(b, tz, any_cpml, (int)done_total, n, st, st != nullptr);
+            return r;
+        }
         cudaError_t r = cudaMemsetAsync(ctx->done, 0, (size_t)done_total * sizeof(int), st);
         if (r == cudaSuccess) r = cudaMemsetAsync(ctx->head, 0, sizeof(unsigned long long), st);
         if (r == cudaSuccess) r = cudaMemsetAsync(ctx->flags, 0, sizeof(unsigned), st);

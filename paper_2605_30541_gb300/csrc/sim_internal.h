@@ -164,6 +164,7 @@ struct BatchArgs {
     const StepArgs<float> *slices;
     const BatchGroup *groups;
     int ngroups;
+    int nmembers;
     const BatchMember *members;
     int *done;                 // per (slice, shot, tile): steps completed
     unsigned long long *head;  // work counter
@@ -172,6 +173,9 @@ struct BatchArgs {
     unsigned *flags;           // kFlagTimeout on a wait that gave up
 };
 cudaError_t launch_batch2d(const BatchArgs &b, int tz, bool cpml, int grid, cudaStream_t st);
+// Stepped batch (k_multi2d): step n of every member in one launch of
+// nblocks = all members' tiles; members' tile0 is global (prefix over members).
+cudaError_t launch_multi2d(const BatchArgs &b, int tz, bool cpml, int nblocks, int n, cudaStream_t st, bool pdl);
 int batch_blocks_per_sm(int tz, bool cpml);
 
 // 3D launchers (fwd3d.cu). Per step: snapshot, sample, CPML psi, z-march

@@ -1,7 +1,8 @@
-"""sim_batch: many shots on uneven grids in one persistent launch. Results must
-equal per-handle sim_forward bit for bit (each cell's arithmetic does not
-depend on the schedule) and match the FP64 oracle; a bounded wait that runs
-out reports SIM_ERR_TIMEOUT instead of hanging."""
+"""sim_batch: many shots on uneven grids, stepped (one launch per step over all
+members, the default) or persistent (one dataflow launch). Results must equal
+per-handle sim_forward bit for bit in both schedules (each cell's arithmetic
+does not depend on the schedule) and match the FP64 oracle; a bounded wait of
+the persistent schedule that runs out reports SIM_ERR_TIMEOUT, not a hang."""
 import os
 
 import numpy as np
@@ -74,17 +75,35 @@ def test_batch_equals_forward_and_oracle(pkg):
         s.close()
 
 
+def test_stepped_and_persistent_schedules_agree(pkg):
+    slices = uneven_slices(nt=200)
+    sims = sims_for(pkg, slices)
+    entries = [dict(sim=s, wavelet=c["wavelet"], src=c["src"], rec=c["rec"]) for s, c in zip(sims, slices)]
+    stepped = [g.clone() for g in pkg.batch(entries)]
+    os.environ["GSIM_BATCH"] = "persistent"
+    try:
+        persistent = pkg.batch(entries)
+    finally:
+        del os.environ["GSIM_BATCH"]
+    for a, b in zip(stepped, persistent):
+        assert torch.equal(a, b)
+    for s in sims:
+        s.close()
+
+
 def test_batch_timeout_is_reported_and_recoverable(pkg):
     slices = uneven_slices(nt=40)
     sims = sims_for(pkg, slices)
     entries = [dict(sim=s, wavelet=c["wavelet"], src=c["src"], rec=c["rec"]) for s, c in zip(sims, slices)]
     os.environ["GSIM_SPIN_LIMIT"] = "0"   # every wait on a neighbour gives up at once
+    os.environ["GSIM_BATCH"] = "persistent"  # the schedule whose tiles wait on one another
     try:
         with pytest.raises(pkg.SimError) as e:
             pkg.batch(entries)
         assert e.value.code == pkg.abi.SIM_ERR_TIMEOUT
     finally:
         del os.environ["GSIM_SPIN_LIMIT"]
+        del os.environ["GSIM_BATCH"]
     gb = pkg.batch(entries)   # the GPU and the handles stay usable
     ref = sims[0].forward(slices[0]["wavelet"], slices[0]["src"], slices[0]["rec"])["gather"]
     assert torch.equal(gb[0], ref)
