@@ -35,11 +35,24 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Staged planes in flight: while plane z is computed, planes z+1 .. z+4 are
+// ready or arriving and plane z+5 is being requested. A ring slot holds the
+// plane's p^n with its x/y halo, and p^{n-1} and c of the CTA's own cells;
+// the register queue takes plane z+4's own cells from its slot, so after the
+// prologue every global read of the march is a cp.async issued five planes
+// ahead of its use.
+constexpr int NS3 = 6;
+template <int RY>
+constexpr int slot3d() {
+    return (NW * RY + 8) * SW3 + 2 * NW * RY * TX;
+}
+
 template <int RY>
 __global__ void __launch_bounds__(NTH, 2) k_step3d(const StepArgs<float> A, const int n, const int zchunk) {
     constexpr int TY = NW * RY, NR = TY + 8;  // staged rows per plane
+    constexpr int SLOT = slot3d<RY>();
     extern __shared__ float4 sm3[];
-    float *buf[2] = {reinterpret_cast<float *>(sm3), reinterpret_cast<float *>(sm3) + NR * SW3};
+    float *const ring = reinterpret_cast<float *>(sm3);
 
     const Geom &g = A.g;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -66,9 +79,10 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d(const StepArgs<float> A, cons
 #pragma unroll
         for (int r = 0; r < RY; r++) Ey[r] = __ldg(A.E[1] + y0 + w * RY + r);
     }
-    // offset of (z = 0, y0 + w RY, gx0) and of the staged plane's corner
+    // offsets of (z = 0, y0 + w RY, gx0), of the staged plane's corner and of the tile's corner
     const long long own0 = cell_off(g, 0, y0 + w * RY, gx0);
     const long long halo0 = cell_off(g, 0, y0 - 4, x0 - 4);
+    const long long tile0 = cell_off(g, 0, y0, x0);
 
     cudaGridDependencySynchronize();
 
@@ -87,38 +101,41 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d(const StepArgs<float> A, cons
 #pragma unroll
         for (int r = 0; r < RY; r++) q[k + 1][r] = load_plane(zb - 4 + k, r);
 
-    auto stage = [&](int z, float *dst) {  // plane z with its x/y halo
+    // plane z into its slot: p^n with halo, and (for planes this CTA
+    // updates) p^{n-1} and c of the own cells
+    auto stage = [&](int z) {
+        float *dst = ring + (z % NS3) * SLOT;
         const float *src = pc + halo0 + (long long)z * PP;
         for (int rr = w; rr < NR; rr += NW) {
             cp16(dst + rr * SW3 + 4 * lane, src + rr * g.P + 4 * lane);
             if (lane < 2) cp16(dst + rr * SW3 + 128 + 4 * lane, src + rr * g.P + 128 + 4 * lane);
         }
+        if (z < ze) {
+            float *dpp = dst + NR * SW3, *dch = dpp + TY * TX;
+            const long long o = tile0 + (long long)z * PP;
+            for (int rr = w; rr < TY; rr += NW) {
+                cp16(dpp + rr * TX + 4 * lane, pn + o + rr * g.P + 4 * lane);
+                cp16(dch + rr * TX + 4 * lane, A.ch + o + rr * g.P + 4 * lane);
+            }
+        }
         cp_commit();
     };
-    stage(zb, buf[0]);
+#pragma unroll
+    for (int k = 0; k < NS3 - 1; k++) stage(zb + k);
 
     for (int z = zb; z < ze; z++) {
-        float *cur = buf[(z - zb) & 1];
+        stage(z + NS3 - 1);
+        cp_wait<1>();
+        __syncthreads();
+        const float *cur = ring + (z % NS3) * SLOT;
+        const float *ahead = ring + ((z + 4) % NS3) * SLOT;
 #pragma unroll
         for (int k = 0; k < 8; k++)
 #pragma unroll
             for (int r = 0; r < RY; r++) q[k][r] = q[k + 1][r];
 #pragma unroll
-        for (int r = 0; r < RY; r++) q[8][r] = load_plane(z + 4, r);
-        float4 pp4[RY], ch4[RY];
-#pragma unroll
-        for (int r = 0; r < RY; r++) {
-            const long long o = own0 + (long long)z * PP + r * g.P;
-            pp4[r] = *reinterpret_cast<const float4 *>(pn + o);
-            ch4[r] = __ldg(reinterpret_cast<const float4 *>(A.ch + o));
-        }
-        if (z + 1 < ze) {
-            stage(z + 1, buf[(z + 1 - zb) & 1]);
-            cp_wait<1>();
-        } else {
-            cp_wait<0>();
-        }
-        __syncthreads();
+        for (int r = 0; r < RY; r++)
+            q[8][r] = *reinterpret_cast<const float4 *>(ahead + (w * RY + r + 4) * SW3 + 4 + 4 * lane);
         const float ez = spg ? __ldg(A.E[0] + z) : 0.f;
 #pragma unroll
         for (int r = 0; r < RY; r++) {
@@ -130,6 +147,8 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d(const StepArgs<float> A, cons
             float4 yv[9];
 #pragma unroll
             for (int m = 0; m < 9; m++) yv[m] = *reinterpret_cast<const float4 *>(row + (m - 4) * SW3);
+            const float4 pp4 = *reinterpret_cast<const float4 *>(cur + NR * SW3 + ly * TX + 4 * lane);
+            const float4 ch4 = *reinterpret_cast<const float4 *>(cur + NR * SW3 + TY * TX + ly * TX + 4 * lane);
             float res[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) {
@@ -146,7 +165,7 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d(const StepArgs<float> A, cons
                                   float(kC3) * (lane4(q[7][r], k) + lane4(q[1][r], k)) +
                                   float(kC4) * (lane4(q[8][r], k) + lane4(q[0][r], k));
                 const float rhs = d2x + d2y + d2z;
-                const float chv = lane4(ch4[r], k), pp = lane4(pp4[r], k);
+                const float chv = lane4(ch4, k), pp = lane4(pp4, k);
                 float out;
                 if (spg) {
                     const float a = chv * (ez + Ey[r] + lane4(Ex4, k));
@@ -166,8 +185,9 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d(const StepArgs<float> A, cons
                 *reinterpret_cast<float4 *>(pn + own0 + (long long)z * PP + r * g.P) =
                     make_float4(res[0], res[1], res[2], res[3]);
         }
-        __syncthreads();  // the buffer just used is restaged two planes later
+        __syncthreads();  // this slot is restaged at the next plane
     }
+    cp_wait<0>();  // no copy into shared memory outlives the block
 }
 
 // ---------------------------------------------------------------- CPML (3D)
@@ -180,20 +200,96 @@ struct Box {
     int z0, z1, y0, y1, x0, x1;
 };
 
-__device__ __forceinline__ bool box_cell(const Box &b, long long i, int &z, int &y, int &x) {
-    const int nx = b.x1 - b.x0, ny = b.y1 - b.y0;
-    const long long nzy = i / nx;
-    x = b.x0 + (int)(i - nzy * nx);
-    y = b.y0 + (int)(nzy % ny);
-    z = b.z0 + (int)(nzy / ny);
+// The strip kernels work on float4 columns: a box's x-range is rounded out to
+// multiples of 4 (cells so added lie outside the strips, where both
+// recursion coefficients are zero, or beyond the grid, where c is zero, so
+// they stay zero and add nothing). Item i of a box is float4 column
+// i mod C of row i / C, rows ordered (z, y).
+__device__ __forceinline__ bool box_item(const Box &b, long long i, int &z, int &y, int &x) {
+    const int nc = (b.x1 - b.x0) >> 2, ny = b.y1 - b.y0;
+    if (nc <= 0 || ny <= 0) return false;
+    const long long row = i / nc;
+    x = b.x0 + 4 * (int)(i - row * nc);
+    y = b.y0 + (int)(row % ny);
+    z = b.z0 + (int)(row / ny);
     return z < b.z1;
+}
+__device__ __forceinline__ long long box_items(const Box &b) {
+    return (long long)(b.z1 - b.z0) * (b.y1 - b.y0) * ((b.x1 - b.x0) >> 2);
+}
+__device__ __forceinline__ float4 ld4g(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+
+// D1 of the float4 at o along axis stride s (s > 1), or along x from a
+// 12-float window (s == 1)
+__device__ __forceinline__ float4 d1_4(const float *f, long long o, long long s) {
+    float r[4];
+    if (s == 1) {
+        const float4 L = ld4g(f + o - 4), C = ld4g(f + o), R = ld4g(f + o + 4);
+        const float v[12] = {L.x, L.y, L.z, L.w, C.x, C.y, C.z, C.w, R.x, R.y, R.z, R.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            r[k] = float(kD1) * (v[5 + k] - v[3 + k]) + float(kD2) * (v[6 + k] - v[2 + k]) +
+                   float(kD3) * (v[7 + k] - v[1 + k]) + float(kD4) * (v[8 + k] - v[k]);
+    } else {
+        float4 a = ld4g(f + o + s), b = ld4g(f + o - s);
+        r[0] = float(kD1) * (a.x - b.x); r[1] = float(kD1) * (a.y - b.y);
+        r[2] = float(kD1) * (a.z - b.z); r[3] = float(kD1) * (a.w - b.w);
+        a = ld4g(f + o + 2 * s), b = ld4g(f + o - 2 * s);
+        r[0] += float(kD2) * (a.x - b.x); r[1] += float(kD2) * (a.y - b.y);
+        r[2] += float(kD2) * (a.z - b.z); r[3] += float(kD2) * (a.w - b.w);
+        a = ld4g(f + o + 3 * s), b = ld4g(f + o - 3 * s);
+        r[0] += float(kD3) * (a.x - b.x); r[1] += float(kD3) * (a.y - b.y);
+        r[2] += float(kD3) * (a.z - b.z); r[3] += float(kD3) * (a.w - b.w);
+        a = ld4g(f + o + 4 * s), b = ld4g(f + o - 4 * s);
+        r[0] += float(kD4) * (a.x - b.x); r[1] += float(kD4) * (a.y - b.y);
+        r[2] += float(kD4) * (a.z - b.z); r[3] += float(kD4) * (a.w - b.w);
+    }
+    return make_float4(r[0], r[1], r[2], r[3]);
+}
+// D2 of the float4 at o along axis stride s (same conventions)
+__device__ __forceinline__ float4 d2_4(const float *f, long long o, long long s) {
+    float r[4];
+    if (s == 1) {
+        const float4 L = ld4g(f + o - 4), C = ld4g(f + o), R = ld4g(f + o + 4);
+        const float v[12] = {L.x, L.y, L.z, L.w, C.x, C.y, C.z, C.w, R.x, R.y, R.z, R.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            r[k] = float(kC0) * v[4 + k] + float(kC1) * (v[5 + k] + v[3 + k]) + float(kC2) * (v[6 + k] + v[2 + k]) +
+                   float(kC3) * (v[7 + k] + v[1 + k]) + float(kC4) * (v[8 + k] + v[k]);
+    } else {
+        const float4 c = ld4g(f + o);
+        r[0] = float(kC0) * c.x; r[1] = float(kC0) * c.y; r[2] = float(kC0) * c.z; r[3] = float(kC0) * c.w;
+        float4 a = ld4g(f + o + s), b = ld4g(f + o - s);
+        r[0] += float(kC1) * (a.x + b.x); r[1] += float(kC1) * (a.y + b.y);
+        r[2] += float(kC1) * (a.z + b.z); r[3] += float(kC1) * (a.w + b.w);
+        a = ld4g(f + o + 2 * s), b = ld4g(f + o - 2 * s);
+        r[0] += float(kC2) * (a.x + b.x); r[1] += float(kC2) * (a.y + b.y);
+        r[2] += float(kC2) * (a.z + b.z); r[3] += float(kC2) * (a.w + b.w);
+        a = ld4g(f + o + 3 * s), b = ld4g(f + o - 3 * s);
+        r[0] += float(kC3) * (a.x + b.x); r[1] += float(kC3) * (a.y + b.y);
+        r[2] += float(kC3) * (a.z + b.z); r[3] += float(kC3) * (a.w + b.w);
+        a = ld4g(f + o + 4 * s), b = ld4g(f + o - 4 * s);
+        r[0] += float(kC4) * (a.x + b.x); r[1] += float(kC4) * (a.y + b.y);
+        r[2] += float(kC4) * (a.z + b.z); r[3] += float(kC4) * (a.w + b.w);
+    }
+    return make_float4(r[0], r[1], r[2], r[3]);
+}
+__device__ __forceinline__ void coef4(const StepArgs<float> &A, int ax, int z, int y, int x, float4 &a4, float4 &b4) {
+    if (ax == 2) {
+        a4 = ld4g(A.ca[2] + x);
+        b4 = ld4g(A.cb[2] + x);
+    } else {
+        const int k = ax == 0 ? z : y;
+        const float a = A.ca[ax][k], b = A.cb[ax][k];
+        a4 = make_float4(a, a, a, a);
+        b4 = make_float4(b, b, b, b);
+    }
 }
 
 __global__ void k_psi3d(const StepArgs<float> A, const int n, const int ax, const Box b0, const Box b1) {
     const Geom &g = A.g;
     const long long s = axis_stride(g, ax);
-    const long long n0 = (long long)(b0.z1 - b0.z0) * (b0.y1 - b0.y0) * (b0.x1 - b0.x0);
-    const long long n1 = (long long)(b1.z1 - b1.z0) * (b1.y1 - b1.y0) * (b1.x1 - b1.x0);
+    const long long n0 = box_items(b0), n1 = box_items(b1);
     const int shot = blockIdx.y;
     const long long sh = (long long)shot * g.fstride;
     const float *p = A.pbuf[n & 1] + sh;
@@ -201,11 +297,13 @@ __global__ void k_psi3d(const StepArgs<float> A, const int n, const int ax, cons
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n0 + n1;
          i += (long long)gridDim.x * blockDim.x) {
         int z, y, x;
-        if (i < n0) box_cell(b0, i, z, y, x);
-        else box_cell(b1, i - n0, z, y, x);
+        if (!(i < n0 ? box_item(b0, i, z, y, x) : box_item(b1, i - n0, z, y, x))) continue;
         const long long o = cell_off(g, z, y, x);
-        const int k = ax == 0 ? z : (ax == 1 ? y : x);
-        psi[o] = A.cb[ax][k] * psi[o] + A.ca[ax][k] * d1_row(p + o, (int)s);
+        float4 a4, b4;
+        coef4(A, ax, z, y, x, a4, b4);
+        const float4 d = d1_4(p, o, s), old = ld4g(psi + o);
+        *reinterpret_cast<float4 *>(psi + o) = make_float4(b4.x * old.x + a4.x * d.x, b4.y * old.y + a4.y * d.y,
+                                                           b4.z * old.z + a4.z * d.z, b4.w * old.w + a4.w * d.w);
     }
 }
 
@@ -214,8 +312,7 @@ __global__ void k_psi3d(const StepArgs<float> A, const int n, const int ax, cons
 __global__ void k_cpml_add3d(const StepArgs<float> A, const int n, const int ax, const Box b0, const Box b1) {
     const Geom &g = A.g;
     const long long s = axis_stride(g, ax);
-    const long long n0 = (long long)(b0.z1 - b0.z0) * (b0.y1 - b0.y0) * (b0.x1 - b0.x0);
-    const long long n1 = (long long)(b1.z1 - b1.z0) * (b1.y1 - b1.y0) * (b1.x1 - b1.x0);
+    const long long n0 = box_items(b0), n1 = box_items(b1);
     const int shot = blockIdx.y;
     const long long sh = (long long)shot * g.fstride;
     const float *p = A.pbuf[n & 1] + sh;
@@ -225,28 +322,37 @@ __global__ void k_cpml_add3d(const StepArgs<float> A, const int n, const int ax,
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n0 + n1;
          i += (long long)gridDim.x * blockDim.x) {
         int z, y, x;
-        if (i < n0) box_cell(b0, i, z, y, x);
-        else box_cell(b1, i - n0, z, y, x);
+        if (!(i < n0 ? box_item(b0, i, z, y, x) : box_item(b1, i - n0, z, y, x))) continue;
         if (g.fs && z == 0) continue;
         const long long o = cell_off(g, z, y, x);
-        const int k = ax == 0 ? z : (ax == 1 ? y : x);
-        // D2 along the axis with the free-surface mirror for z-derivatives near the top
-        float d2;
-        if (ax == 0 && g.fs && z < 4) {
-            float c[9];
-            for (int m = -4; m <= 4; m++) {
-                const int zz = z + m;
-                c[m + 4] = zz < 0 ? -p[cell_off(g, -zz, y, x)] : p[cell_off(g, zz, y, x)];
+        float4 d2;
+        if (ax == 0 && g.fs && z < 4) {  // z-derivative across the free surface: odd mirror
+            float r[4];
+            for (int k = 0; k < 4; k++) {
+                float c[9];
+                for (int m = -4; m <= 4; m++) {
+                    const int zz = z + m;
+                    c[m + 4] = zz < 0 ? -p[cell_off(g, -zz, y, x + k)] : p[cell_off(g, zz, y, x + k)];
+                }
+                r[k] = float(kC0) * c[4] + float(kC1) * (c[5] + c[3]) + float(kC2) * (c[6] + c[2]) +
+                       float(kC3) * (c[7] + c[1]) + float(kC4) * (c[8] + c[0]);
             }
-            d2 = float(kC0) * c[4] + float(kC1) * (c[5] + c[3]) + float(kC2) * (c[6] + c[2]) +
-                 float(kC3) * (c[7] + c[1]) + float(kC4) * (c[8] + c[0]);
+            d2 = make_float4(r[0], r[1], r[2], r[3]);
         } else {
-            d2 = d2_col(p + o, (int)s);
+            d2 = d2_4(p, o, s);
         }
-        const float dps = d1_row(psi + o, (int)s);
-        const float zt = A.cb[ax][k] * zeta[o] + A.ca[ax][k] * (d2 + dps);
-        zeta[o] = zt;
-        pn[o] += A.ch[o] * (dps + zt);
+        float4 a4, b4;
+        coef4(A, ax, z, y, x, a4, b4);
+        const float4 dps = d1_4(psi, o, s), zo = ld4g(zeta + o), ch = ld4g(A.ch + o);
+        const float4 zt = make_float4(b4.x * zo.x + a4.x * (d2.x + dps.x), b4.y * zo.y + a4.y * (d2.y + dps.y),
+                                      b4.z * zo.z + a4.z * (d2.z + dps.z), b4.w * zo.w + a4.w * (d2.w + dps.w));
+        *reinterpret_cast<float4 *>(zeta + o) = zt;
+        float4 pv = ld4g(pn + o);
+        pv.x += ch.x * (dps.x + zt.x);
+        pv.y += ch.y * (dps.y + zt.y);
+        pv.z += ch.z * (dps.z + zt.z);
+        pv.w += ch.w * (dps.w + zt.w);
+        *reinterpret_cast<float4 *>(pn + o) = pv;
     }
 }
 
@@ -318,7 +424,7 @@ __global__ void k_snap3d(const StepArgs<float> A, const StepTime t, int pass) {
 
 template <int RY>
 size_t smem3d() {
-    return 2 * (size_t)(NW * RY + 8) * SW3 * sizeof(float);
+    return (size_t)NS3 * slot3d<RY>() * sizeof(float);
 }
 
 }  // namespace
@@ -371,10 +477,25 @@ cudaError_t launch_cpml3d(const StepArgs<float> &a, int n, int ax, int phase, in
     };
     set(B0, a0, a1);
     set(B1, b0, b1);
-    const long long cells = (long long)(B0.z1 - B0.z0) * (B0.y1 - B0.y0) * (B0.x1 - B0.x0) +
-                            (long long)(B1.z1 - B1.z0) * (B1.y1 - B1.y0) * (B1.x1 - B1.x0);
-    if (cells <= 0) return cudaSuccess;
-    const int blocks = (int)std::min<long long>((cells + 255) / 256, 152 * 16);
+    // float4 columns: x-ranges rounded out to multiples of 4; boxes that then
+    // touch or overlap become one box (so no cell is updated twice)
+    auto round4 = [](Box &b) {
+        if (b.x1 <= b.x0) return;
+        b.x0 = b.x0 & ~3;
+        b.x1 = (b.x1 + 3) & ~3;
+    };
+    round4(B0);
+    round4(B1);
+    const bool empty0 = B0.z1 <= B0.z0 || B0.y1 <= B0.y0 || B0.x1 <= B0.x0;
+    const bool empty1 = B1.z1 <= B1.z0 || B1.y1 <= B1.y0 || B1.x1 <= B1.x0;
+    if (ax == 2 && !empty0 && !empty1 && B0.x1 >= B1.x0) {
+        B0.x1 = B1.x1;
+        B1 = Box{0, 0, 0, 0, 0, 0};
+    }
+    const long long items = (long long)(B0.z1 - B0.z0) * (B0.y1 - B0.y0) * ((B0.x1 - B0.x0) >> 2) +
+                            (long long)(B1.z1 - B1.z0) * (B1.y1 - B1.y0) * ((B1.x1 - B1.x0) >> 2);
+    if (items <= 0) return cudaSuccess;
+    const int blocks = (int)std::min<long long>((items + 255) / 256, 152 * 16);
     if (phase == 0) k_psi3d<<<dim3(blocks, nshots), 256, 0, st>>>(a, n, ax, B0, B1);
     else k_cpml_add3d<<<dim3(blocks, nshots), 256, 0, st>>>(a, n, ax, B0, B1);
     return cudaGetLastError();
