@@ -291,7 +291,8 @@ def run_batch(args):
                        "padded_cells_x_shots": cells,
                        "l2": "flushed between timed solves"},
             "roofline": {"bound": "hbm", "achieved": algo / (total / args.steps) / 1e9, "peak": peak,
-                         "unit": "GB/s", "frac": algo / (total / args.steps) / 1e9 / peak, "traffic": None,
+                         "unit": "GB/s", "frac": algo / (total / args.steps) / 1e9 / peak,
+                         "traffic": ncu_traffic("fwd2d_f32.cu", "multi_c3"), "traffic_per": "step launch",
                          "kernel": "k_multi2d", "peak_kind": peak_kind,
                          "algorithmic_bytes_per_solve": algo},
             "clocks": clk.summary(), "gpu_launches": args.steps * nt}
