@@ -206,6 +206,26 @@ sim_status sim_forward_noalloc(const sim_desc *d, const float *vel, const float 
                                void *cuda_stream);
 
 /* Wait for the handle's stream and report any device-side failure. */
+/* Band-passed Ricker source wavelet of the paper's production runs (Sec.
+ * "Source Wavelet", Tab. bands): w(t) = Ricker of peak frequency f0 centred at
+ * t0 = 1/f0, sampled at t = n dt (n = 0 .. nt-1), filtered by a digital
+ * Butterworth band-pass of the given order (2 order poles, edges f_lo < f_hi,
+ * bilinear transform with prewarped edges) forward and then backward in time
+ * (zero phase; odd reflection of 3 (2 order + 1) samples at each end, every
+ * section started in steady state), then divided by its l2 norm and multiplied
+ * by sqrt((f_hi - f_lo) / 24 Hz). The paper's five bands use order 4.
+ *   precision  SIM_FP32 or SIM_FP64: element type of out
+ *   out        [nt], host or device memory, owned by the caller
+ *   stream     CUDA stream (NULL: legacy default stream); the call returns
+ *              when out is written
+ * Runs on the current device; computes in FP64 on the GPU. Errors:
+ * SIM_ERR_ARG (nt <= 3 (2 order + 1), dt <= 0, f0 <= 0, not 0 < f_lo < f_hi <
+ * 1/(2 dt), order outside [1, 16], or a band so wide that the design has real
+ * poles),
+ * SIM_ERR_OOM, SIM_ERR_CUDA (text from sim_last_error(NULL)). */
+sim_status sim_wavelet_bandpass(int nt, double dt, double f0, double f_lo, double f_hi, int order, int precision,
+                                void *out, void *stream);
+
 sim_status sim_sync(sim_t s);
 
 /* Layout and model facts of a live handle. */

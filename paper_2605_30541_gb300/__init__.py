@@ -16,7 +16,7 @@ from .abi import SIM_BC, SIM_FP32, SIM_FP64, SimBatchItem, SimDesc, SimInfo
 
 __all__ = ["SimError", "make_desc", "sim_plan", "sim_create", "sim_set_model", "sim_forward",
            "sim_adjoint", "sim_batch", "sim_sync", "sim_get_info", "sim_last_error", "sim_destroy",
-           "Simulator", "batch", "sim_forward_noalloc"]
+           "Simulator", "batch", "sim_forward_noalloc", "sim_wavelet_bandpass", "bandpass_ricker"]
 
 
 class SimError(RuntimeError):
@@ -159,6 +159,21 @@ def sim_forward_noalloc(desc, vel, wavelet, src_pos, nrec, rec_pos, gather, stre
     """Forward solve that allocates no device memory (see include/sim.h)."""
     _check(abi.load().sim_forward_noalloc(ctypes.byref(desc), _ptr(vel), _ptr(wavelet), _ptr(src_pos), nrec,
                                           _ptr(rec_pos), _ptr(gather), _stream(stream)))
+
+
+def sim_wavelet_bandpass(nt, dt, f0, f_lo, f_hi, order, precision, out, stream=None):
+    """Band-passed Ricker wavelet into ``out`` (see include/sim.h)."""
+    _check(abi.load().sim_wavelet_bandpass(int(nt), float(dt), float(f0), float(f_lo), float(f_hi), int(order),
+                                           int(precision), _ptr(out), _stream(stream)))
+
+
+def bandpass_ricker(nt, dt, f0, f_lo, f_hi, order=4, dtype="float32", device="cuda"):
+    """The paper's band-passed source wavelet as a torch tensor [nt] on ``device``."""
+    import torch
+    tdt = torch.float64 if dtype in ("float64", torch.float64) else torch.float32
+    out = torch.empty(int(nt), dtype=tdt, device=device)
+    sim_wavelet_bandpass(nt, dt, f0, f_lo, f_hi, order, SIM_FP64 if tdt == torch.float64 else SIM_FP32, out)
+    return out
 
 
 def sim_sync(handle):

@@ -67,6 +67,7 @@ _PROTOS = {
     "sim_adjoint": (_I, [_VP, _I, _VP, _VP, _I, _VP, _VP, _VP, _VP, _I, _VP]),
     "sim_batch": (_I, [_I, ctypes.POINTER(SimBatchItem), _VP]),
     "sim_forward_noalloc": (_I, [ctypes.POINTER(SimDesc), _VP, _VP, _VP, _I, _VP, _VP, _VP]),
+    "sim_wavelet_bandpass": (_I, [_I, _D, _D, _D, _D, _I, _I, _VP, _VP]),
     "sim_sync": (_I, [_VP]),
     "sim_get_info": (_I, [_VP, ctypes.POINTER(SimInfo)]),
     "sim_last_error": (ctypes.c_char_p, [_VP]),

@@ -235,3 +235,37 @@ def config_c5(nt=2500, dt=8e-4, n=(619, 1000, 1000), nb=30, seed=5000, nrec_side
     p["src"] = np.array([[(nx // 2) * 10.0, (ny // 2) * 10.0, 10.0]])
     p["rec"] = grid_xy(0.0, (nx - 1) * 10.0, nrec_side, 0.0, (ny - 1) * 10.0, nrec_side, 10.0)
     return p
+
+
+# the paper's five frequency bands: (f_lo, f_hi, f0) in Hz (Tab. bands, Sec. "Source Wavelet")
+BANDS = [(3.0, 6.0, 4.50), (3.0, 8.5, 5.75), (3.0, 12.0, 7.50), (3.0, 17.5, 10.25), (3.0, 25.0, 14.00)]
+
+
+def config_c6(kind="gather", band=0, nt=None, seed=6000, nshots=64):
+    """The paper's production runs on one 619 x 1000 slice at 10 m with a
+    60-cell sponge on the left, right and bottom and a free top, dt = 1 ms,
+    band-passed Ricker source (parameters in ``band``: the wavelet itself is
+    made by the library's band-pass kernel). kind="gather": 8 s (nt = 8001),
+    ``nshots`` sources uniformly spaced over [1.1 km, x_max - 1.1 km] at 10 m
+    depth, 1000 receivers uniformly spaced over the full width at 10 m (saved
+    every 14 steps = the rows 0, 14, ... of the full gather). kind="wavefield":
+    5 s (nt = 5001), one source at a seeded uniform position in the same
+    interval, snapshots every 14 steps (358), no receivers."""
+    nz, nx, h = 619, 1000, 10.0
+    if nt is None:
+        nt = 8001 if kind == "gather" else 5001
+    p = _problem(name="c6" + kind[0], nz=nz, nx=nx, h=h, dt=1e-3, nt=nt, bc="sponge",
+                 nb=[0, 60, 0, 0, 60, 60], free_surface=1, f_ref=10.0)
+    p["vel"] = procedural_2d(nz, nx, h, seed)
+    p["band"] = BANDS[band]
+    xmax = (nx - 1) * h
+    if kind == "gather":
+        p["src"] = np.stack([np.linspace(1100.0, xmax - 1100.0, nshots), np.full(nshots, 10.0)], axis=1)
+        p["rec"] = line(0.0, xmax, 1000, 10.0)
+        p["save_every"] = 14
+    else:
+        rng = np.random.default_rng(seed)
+        p["src"] = np.array([[float(rng.uniform(1100.0, xmax - 1100.0)), 10.0]])
+        p["rec"] = np.zeros((0, 2))
+        p.update(snap_every=14, snap_begin=0, snap_end=nt)
+    return p

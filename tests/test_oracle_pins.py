@@ -401,3 +401,50 @@ def test_dot_product_born_jacobian():
     JTdd = oracle.gradient(cfg, vel, w, src, rec, g0 - dd)["grad"]
     lhs, rhs = np.vdot(Jdv, dd), np.vdot(dv, JTdd)
     assert abs(lhs - rhs) / (np.linalg.norm(Jdv) * np.linalg.norm(dd)) < 1e-10
+
+
+# ---------------------------------------------------------------- source wavelet (Sec. "Source Wavelet")
+
+def test_wavelet_ricker_spectrum_is_the_closed_form():
+    # |FT| of the Ricker pulse is proportional to f^2 exp(-f^2 / f0^2): peak at f0
+    from oracle import wavelet as W
+    dt, nt = 1e-3, 8192
+    for f0 in (4.5, 10.25):
+        r = W.ricker(f0, nt * dt / 2, dt, nt)
+        spec = np.abs(np.fft.rfft(r))
+        f = np.fft.rfftfreq(nt, dt)
+        model = f ** 2 * np.exp(-(f / f0) ** 2)
+        assert np.max(np.abs(spec / spec.max() - model / model.max())) < 1e-6
+        assert abs(f[np.argmax(spec)] - f0) <= f[1]
+
+
+def test_wavelet_norm_and_zero_phase():
+    from oracle import wavelet as W
+    dt, nt = 1e-3, 8001
+    for lo, hi, f0 in W.BANDS:
+        w = W.bandpass_ricker(f0, lo, hi, dt, nt)
+        assert abs(np.linalg.norm(w) - np.sqrt((hi - lo) / 24.0)) < 1e-12
+    # a pulse centred in the record comes out symmetric about its centre
+    y = W.bandpass(W.ricker(7.5, 4.0, dt, nt), 3.0, 12.0, dt)
+    c = 4000
+    assert np.max(np.abs(y[c:c + 3000] - y[c:c - 3000:-1])) <= 1e-9 * np.abs(y).max()
+
+
+def test_wavelet_filter_gain_is_the_squared_analog_butterworth():
+    # forward-backward gain of a pure tone = |H_a(j W)|^2 of the analog band-pass
+    # prototype of order N at the prewarped frequency W = 2 fs tan(pi f / fs)
+    from oracle import wavelet as W
+    dt, nt, N, lo, hi = 1e-3, 40000, 4, 3.0, 12.0
+    fs = 1.0 / dt
+    wl, wh = 2 * fs * np.tan(np.pi * lo / fs), 2 * fs * np.tan(np.pi * hi / fs)
+    w0, bw = np.sqrt(wl * wh), wh - wl
+    t = np.arange(nt) * dt
+    mid = slice(nt // 4, 3 * nt // 4)
+    for f in (1.5, 3.0, 5.0, 12.0, 20.0):
+        y = W.bandpass(np.sin(2 * np.pi * f * t), lo, hi, dt, N)
+        basis = np.stack([np.sin(2 * np.pi * f * t[mid]), np.cos(2 * np.pi * f * t[mid])], 1)
+        ab, *_ = np.linalg.lstsq(basis, y[mid], rcond=None)
+        gain = np.hypot(*ab)
+        wf = 2 * fs * np.tan(np.pi * f / fs)
+        expect = 1.0 / (1.0 + ((wf ** 2 - w0 ** 2) / (wf * bw)) ** (2 * N))
+        assert abs(gain - expect) <= 1e-6 + 1e-6 * expect, (f, gain, expect)
