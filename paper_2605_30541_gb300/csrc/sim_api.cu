@@ -586,24 +586,20 @@ StepArgs<T> step_args(sim_t s) {
 
 // Zero the per-run state of `nshots` shots: both pressure buffers, the CPML
 // memory and the FP16 snapshot maxima.
-sim_status reset_state(sim_t s, int nshots) {
+cudaError_t reset_state_on(const sim_s *s, int nshots, cudaStream_t st) {
     const size_t fb = (size_t)s->g.fstride * s->esz * nshots;
     const size_t half = (size_t)s->g.fstride * s->esz * s->d.max_shots;
-    if (sim_status r = s->cuda(cudaMemsetAsync(s->pbuf, 0, fb, s->st), "reset")) return r;
-    if (sim_status r = s->cuda(cudaMemsetAsync(static_cast<char *>(s->pbuf) + half, 0, fb, s->st), "reset")) return r;
-    for (int ax = 0; ax < 3; ax++) {
-        for (int k = 0; k < 2; k++)
-            if (s->psi[ax][k])
-                if (sim_status r = s->cuda(cudaMemsetAsync(s->psi[ax][k], 0, fb, s->st), "reset")) return r;
-        if (s->zeta[ax])
-            if (sim_status r = s->cuda(cudaMemsetAsync(s->zeta[ax], 0, fb, s->st), "reset")) return r;
+    cudaError_t e = cudaMemsetAsync(s->pbuf, 0, fb, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(static_cast<char *>(s->pbuf) + half, 0, fb, st);
+    for (int ax = 0; ax < 3 && e == cudaSuccess; ax++) {
+        for (int k = 0; k < 2 && e == cudaSuccess; k++)
+            if (s->psi[ax][k]) e = cudaMemsetAsync(s->psi[ax][k], 0, fb, st);
+        if (s->zeta[ax] && e == cudaSuccess) e = cudaMemsetAsync(s->zeta[ax], 0, fb, st);
     }
-    if (s->nsnap > 0)
-        if (sim_status r = s->cuda(cudaMemsetAsync(s->snap_max, 0, sizeof(unsigned) * s->nsnap * nshots, s->st),
-                                   "reset"))
-            return r;
-    return SIM_OK;
+    if (s->nsnap > 0 && e == cudaSuccess) e = cudaMemsetAsync(s->snap_max, 0, sizeof(unsigned) * s->nsnap * nshots, st);
+    return e;
 }
+sim_status reset_state(sim_t s, int nshots) { return s->cuda(reset_state_on(s, nshots, s->st), "reset"); }
 
 // Per-launch facts of step n for the FP32 kernel (see StepTime).
 template <typename T>
@@ -1205,15 +1201,15 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
             return r;
         wav = s->wave;
     }
-    const void *dob = d_obs;
-    if (!is_device_ptr(d_obs)) {
-        if (sim_status r = s->cuda(cudaMemcpyAsync(s->dobs, d_obs, nrows * sizeof(T), cudaMemcpyHostToDevice, s->st),
-                                   "d_obs upload"))
-            return r;
-        dob = s->dobs;
-    }
+    // The time loops run as one captured graph on handle-owned buffers: d_obs
+    // is copied into the handle, the gather is recorded in the handle's buffer
+    // and copied out afterwards.
+    if (sim_status r = s->cuda(cudaMemcpyAsync(s->dobs, d_obs, nrows * sizeof(T), cudaMemcpyDefault, s->st),
+                               "d_obs copy"))
+        return r;
+    const void *dob = s->dobs;
     const bool g_host = gather_out && !is_device_ptr(gather_out);
-    void *gdev = (gather_out && !g_host) ? gather_out : s->gath;
+    void *gdev = s->gath;
     const bool gr_host = !is_device_ptr(grad_v);
     void *grdev = gr_host ? s->gradst : grad_v;
     if (gr_host)
@@ -1252,7 +1248,6 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
     io.nshots = nshots;
     if (sim_status r = s->cuda(cudaMemcpyAsync(s->io, &io, sizeof io, cudaMemcpyHostToDevice, s->st), "io upload"))
         return r;
-    if (sim_status r = reset_state(s, nshots)) return r;
 
     const int L = s->seg;
     const size_t ck_state = (size_t)ms * ncomp;  // elements of one checkpointed state (all shots)
@@ -1269,32 +1264,6 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
     a.inj_per_shot = 1;
     a.inj_kind = 0;
     a.nsnap = 0;
-    for (int n = 0; n < d.nt; n++) {
-        if (n % L == 0) {
-            const int k = n / L;
-            if (sim_status r = s->cuda(launch_store_state<T>(g, a.pbuf[n & 1], ck_ptr(k, 1), ck_scale(k, 1), ckpt_fp16,
-                                                             nshots, ncomp, ckx, ckz, s->st), "checkpoint"))
-                return r;
-            if (sim_status r = s->cuda(launch_store_state<T>(g, a.pbuf[(n + 1) & 1], ck_ptr(k, 0), ck_scale(k, 0),
-                                                             ckpt_fp16, nshots, ncomp, ckx, ckz, s->st),
-                                       "checkpoint"))
-                return r;
-        }
-        if (sim_status r = s->cuda(launch_step<T>(s, a, n, nshots, kModeForward, s->st), "forward step")) return r;
-    }
-    // 2. residual and misfit
-    if (sim_status r = s->cuda(launch_residual<T>(static_cast<const T *>(gdev), static_cast<const T *>(dob),
-                                                  static_cast<T *>(s->res), (long long)nrows, s->mpart, kResidBlocks,
-                                                  s->st), "residual"))
-        return r;
-    // 3. segments in reverse: restore, recompute while recording Q', sweep the adjoint back
-    const size_t ub = (size_t)g.fstride * s->esz * nshots;
-    if (sim_status r = s->cuda(cudaMemsetAsync(s->ubuf, 0, ub, s->st), "adjoint reset")) return r;
-    if (sim_status r = s->cuda(cudaMemsetAsync(static_cast<char *>(s->ubuf) + (size_t)g.fstride * s->esz * ms, 0, ub,
-                                               s->st), "adjoint reset"))
-        return r;
-    if (sim_status r = s->cuda(cudaMemsetAsync(s->Gbuf, 0, (size_t)nshots * g.fstride * s->esz, s->st), "adjoint reset"))
-        return r;
     StepArgs<T> rcp = a;
     rcp.sample = 0;
     rcp.q_fp16 = ckpt_fp16;
@@ -1312,34 +1281,57 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
     adj.q_fp16 = ckpt_fp16;
     adj.G = static_cast<T *>(s->Gbuf);
     const size_t qslot_bytes = (size_t)ms * g.fstride * (ckpt_fp16 ? 2 : sizeof(T));
-    for (int sgi = s->nseg - 1; sgi >= 0; sgi--) {
-        const int n0 = sgi * L, e = std::min(n0 + L, d.nt);
-        if (sim_status r = s->cuda(launch_load_state<T>(g, a.pbuf[n0 & 1], ck_ptr(sgi, 1), ck_scale(sgi, 1), ckpt_fp16,
-                                                        nshots, ncomp, ckx, ckz, s->st), "restore"))
-            return r;
-        if (sim_status r = s->cuda(launch_load_state<T>(g, a.pbuf[(n0 + 1) & 1], ck_ptr(sgi, 0), ck_scale(sgi, 0),
-                                                        ckpt_fp16, nshots, ncomp, ckx, ckz, s->st), "restore"))
-            return r;
-        for (int n = n0; n < e; n++) {
-            void *slot = static_cast<char *>(s->qbuf) + (size_t)(n - n0) * qslot_bytes;
-            float *scl = s->qscale + (size_t)(n - n0) * q_tiles;
-            if (sim_status r = s->cuda(launch_step<T>(s, rcp, n, nshots, kModeRecord, s->st, slot, scl),
-                                       "recompute step"))
-                return r;
-        }
-        for (int k = e; k >= n0 + 1; k--) {
-            void *slot = static_cast<char *>(s->qbuf) + (size_t)(k - 1 - n0) * qslot_bytes;
-            float *scl = s->qscale + (size_t)(k - 1 - n0) * q_tiles;
-            if (sim_status r = s->cuda(launch_step<T>(s, adj, d.nt - k, nshots, kModeAdjoint, s->st, slot, scl),
-                                       "adjoint step"))
-                return r;
-        }
-    }
-    // 4. gradient: FP64 sum over shots and replicated cells, added to grad_v
-    if (sim_status r = s->cuda(cudaMemsetAsync(s->acc, 0, nint * sizeof(double), s->st), "gradient reset")) return r;
-    if (sim_status r = s->cuda(launch_fold_gradient<T>(g, static_cast<const T *>(s->Gbuf), g.fstride, nshots,
-                                                       static_cast<const T *>(s->vpad), 1.0 / (d.h * d.h), s->acc,
-                                                       s->st), "gradient fold"))
+    const size_t ub = (size_t)g.fstride * s->esz * nshots;
+    // graph key: everything the captured launches depend on beyond handle buffers
+    const long long gkey = ((long long)nshots << 40) ^ ((long long)nrec << 12) ^ ((long long)s->tile_z << 4) ^
+                           ((long long)ckpt_fp16 << 3) ^ 5;
+    if (sim_status r = run_graph(s, gkey, [&](cudaStream_t st) {
+            cudaError_t e = reset_state_on(s, nshots, st);
+            for (int n = 0; n < d.nt && e == cudaSuccess; n++) {
+                if (n % L == 0) {
+                    const int k = n / L;
+                    e = launch_store_state<T>(g, a.pbuf[n & 1], ck_ptr(k, 1), ck_scale(k, 1), ckpt_fp16, nshots,
+                                              ncomp, ckx, ckz, st);
+                    if (e == cudaSuccess)
+                        e = launch_store_state<T>(g, a.pbuf[(n + 1) & 1], ck_ptr(k, 0), ck_scale(k, 0), ckpt_fp16,
+                                                  nshots, ncomp, ckx, ckz, st);
+                }
+                if (e == cudaSuccess) e = launch_step<T>(s, a, n, nshots, kModeForward, st);
+            }
+            // 2. residual and misfit
+            if (e == cudaSuccess)
+                e = launch_residual<T>(static_cast<const T *>(gdev), static_cast<const T *>(dob),
+                                       static_cast<T *>(s->res), (long long)nrows, s->mpart, kResidBlocks, st);
+            // 3. segments in reverse: restore, recompute while recording Q', sweep the adjoint back
+            if (e == cudaSuccess) e = cudaMemsetAsync(s->ubuf, 0, ub, st);
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(static_cast<char *>(s->ubuf) + (size_t)g.fstride * s->esz * ms, 0, ub, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(s->Gbuf, 0, (size_t)nshots * g.fstride * s->esz, st);
+            for (int sgi = s->nseg - 1; sgi >= 0 && e == cudaSuccess; sgi--) {
+                const int n0 = sgi * L, n1 = std::min(n0 + L, d.nt);
+                e = launch_load_state<T>(g, a.pbuf[n0 & 1], ck_ptr(sgi, 1), ck_scale(sgi, 1), ckpt_fp16, nshots,
+                                         ncomp, ckx, ckz, st);
+                if (e == cudaSuccess)
+                    e = launch_load_state<T>(g, a.pbuf[(n0 + 1) & 1], ck_ptr(sgi, 0), ck_scale(sgi, 0), ckpt_fp16,
+                                             nshots, ncomp, ckx, ckz, st);
+                for (int n = n0; n < n1 && e == cudaSuccess; n++) {
+                    void *slot = static_cast<char *>(s->qbuf) + (size_t)(n - n0) * qslot_bytes;
+                    float *scl = s->qscale + (size_t)(n - n0) * q_tiles;
+                    e = launch_step<T>(s, rcp, n, nshots, kModeRecord, st, slot, scl);
+                }
+                for (int k = n1; k >= n0 + 1 && e == cudaSuccess; k--) {
+                    void *slot = static_cast<char *>(s->qbuf) + (size_t)(k - 1 - n0) * qslot_bytes;
+                    float *scl = s->qscale + (size_t)(k - 1 - n0) * q_tiles;
+                    e = launch_step<T>(s, adj, d.nt - k, nshots, kModeAdjoint, st, slot, scl);
+                }
+            }
+            // 4. gradient: FP64 sum over shots and replicated cells
+            if (e == cudaSuccess) e = cudaMemsetAsync(s->acc, 0, nint * sizeof(double), st);
+            if (e == cudaSuccess)
+                e = launch_fold_gradient<T>(g, static_cast<const T *>(s->Gbuf), g.fstride, nshots,
+                                            static_cast<const T *>(s->vpad), 1.0 / (d.h * d.h), s->acc, st);
+            return e;
+        }))
         return r;
     if (sim_status r = s->cuda(launch_add_gradient<T>(s->acc, static_cast<T *>(grdev), nint, s->st), "gradient add"))
         return r;
@@ -1352,9 +1344,9 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
         if (sim_status r = s->cuda(cudaMemcpyAsync(grad_v, grdev, nint * sizeof(T), cudaMemcpyDeviceToHost, s->st),
                                    "gradient download"))
             return r;
-    if (g_host)
-        if (sim_status r = s->cuda(cudaMemcpyAsync(gather_out, gdev, nrows * sizeof(T), cudaMemcpyDeviceToHost, s->st),
-                                   "gather download"))
+    if (gather_out)
+        if (sim_status r = s->cuda(cudaMemcpyAsync(gather_out, gdev, nrows * sizeof(T), cudaMemcpyDefault, s->st),
+                                   "gather copy"))
             return r;
     std::vector<double> part(kResidBlocks);
     if (misfit_out) {

@@ -153,3 +153,17 @@ def test_timeout_is_reported(pkg):
     # the context is still usable
     res, info = forward(pkg, c, c["vel"], c["wavelet"], c["src"], c["rec"])
     assert info.last_path == PATH_RESIDENT and np.isfinite(res["gather"]).all()
+
+
+@pytest.mark.parametrize("nt", [1, 2, 3])
+def test_shortest_runs(pkg, nt):
+    # the first steps: p^0 = 0 everywhere, the source enters at n = 0
+    c = synth.config_c1(nt=nt)
+    c["wavelet"] = np.ones(nt, np.float32)
+    res, info = forward(pkg, c, c["vel"], c["wavelet"], c["src"], c["rec"])
+    assert info.last_path == PATH_RESIDENT
+    ref = oracle.forward(c, c["vel"].astype(np.float64), c["wavelet"].astype(np.float64), src=c["src"][0],
+                         rec=c["rec"])["gather"]
+    step, _ = forward(pkg, c, c["vel"], c["wavelet"], c["src"], c["rec"], resident=False)
+    assert np.allclose(res["gather"][0], ref, rtol=1e-5, atol=1e-7 * max(1.0, np.abs(ref).max()))
+    assert np.allclose(res["gather"][0], step["gather"][0], rtol=1e-6, atol=0)
