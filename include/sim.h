@@ -156,11 +156,13 @@ sim_status sim_forward(sim_t s, int nshots, const void *wavelet, const double *s
  *   d_obs      [nshots][nt][nrec]  observed data
  *   gather_out [nshots][nt][nrec]  out: modelled gather (NULL ok)
  *   misfit_out [1] (host)          out: J, accumulated over shots in FP64
- *   ckpt_fp16  1: checkpoints and the stored imaging terms in FP16 with a
- *              power-of-two scale per state; 0: handle precision
+ *   ckpt_fp16  1: checkpoints (2D: and the stored imaging terms) in FP16
+ *              with a power-of-two scale per tile; 0: handle precision. On 3D
+ *              handles the imaging terms of a segment stay FP32.
  *   grad_v     [nz][ny][nx]        out: dJ/dv ACCUMULATED (+=) in handle
  *              precision, after an FP64 sum over the shots
- * Sponge and no-absorption boundaries; SIM_ERR_UNSUPPORTED for CPML. */
+ * 2D and 3D (FP32) handles; sponge and no-absorption boundaries,
+ * SIM_ERR_UNSUPPORTED for CPML. */
 sim_status sim_adjoint(sim_t s, int nshots, const void *wavelet, const double *src_pos,
                        int nrec, const double *rec_pos, const void *d_obs,
                        void *gather_out, double *misfit_out, int ckpt_fp16, void *grad_v);

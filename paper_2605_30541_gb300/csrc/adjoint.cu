@@ -26,12 +26,18 @@ __device__ __forceinline__ float tile_max(float v, float *red) {
     return red[0];
 }
 
-// One CTA per (tile, shot); the compact copy of a state is [shot][NZ * NX].
+// Rows of the computational grid: r = z NY + y (r = z in 2D), NZ NY rows of NX cells.
+__device__ __forceinline__ long long row_off(const Geom &g, int r, int x) {
+    return cell_off(g, r / g.NY, r % g.NY, x);
+}
+
+// One CTA per (tile of rows x columns, shot); the compact copy of a state is
+// [shot][NZ NY NX].
 template <typename T>
 __global__ void __launch_bounds__(NTH) k_store(const Geom g, const T *__restrict__ field, void *dst, float *scale,
                                                int fp16, long long sstride, int ntx) {
     __shared__ float red[NTH / 32];
-    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ, shot = blockIdx.z;
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ, shot = blockIdx.z, nrow = g.NZ * g.NY;
     const int tile = blockIdx.y * ntx + blockIdx.x, ntiles = ntx * gridDim.y;
     const T *f = field + (long long)shot * g.fstride;
     T v[RZ];
@@ -39,7 +45,7 @@ __global__ void __launch_bounds__(NTH) k_store(const Geom g, const T *__restrict
 #pragma unroll
     for (int k = 0; k < RZ; k++) {
         const int gz = z0 + threadIdx.y + k * BY, gx = x0 + threadIdx.x;
-        v[k] = (gz < g.NZ && gx < g.NX) ? f[cell_off(g, gz, 0, gx)] : T(0);
+        v[k] = (gz < nrow && gx < g.NX) ? f[row_off(g, gz, gx)] : T(0);
         m = fmaxf(m, fabsf((float)v[k]));
     }
     float inv = 1.f;
@@ -51,7 +57,7 @@ __global__ void __launch_bounds__(NTH) k_store(const Geom g, const T *__restrict
 #pragma unroll
     for (int k = 0; k < RZ; k++) {
         const int gz = z0 + threadIdx.y + k * BY, gx = x0 + threadIdx.x;
-        if (gz >= g.NZ || gx >= g.NX) continue;
+        if (gz >= nrow || gx >= g.NX) continue;
         const long long ci = shot * sstride + (long long)gz * g.NX + gx;
         if (fp16) static_cast<__half *>(dst)[ci] = __float2half_rn((float)v[k] * inv);
         else static_cast<T *>(dst)[ci] = v[k];
@@ -61,16 +67,16 @@ __global__ void __launch_bounds__(NTH) k_store(const Geom g, const T *__restrict
 template <typename T>
 __global__ void __launch_bounds__(NTH) k_load(const Geom g, T *field, const void *src, const float *scale, int fp16,
                                               long long sstride, int ntx) {
-    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ, shot = blockIdx.z;
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ, shot = blockIdx.z, nrow = g.NZ * g.NY;
     const int tile = blockIdx.y * ntx + blockIdx.x, ntiles = ntx * gridDim.y;
     T *f = field + (long long)shot * g.fstride;
     const float s = fp16 ? scale[(long long)shot * ntiles + tile] : 1.f;
 #pragma unroll
     for (int k = 0; k < RZ; k++) {
         const int gz = z0 + threadIdx.y + k * BY, gx = x0 + threadIdx.x;
-        if (gz >= g.NZ || gx >= g.NX) continue;
+        if (gz >= nrow || gx >= g.NX) continue;
         const long long ci = shot * sstride + (long long)gz * g.NX + gx;
-        f[cell_off(g, gz, 0, gx)] =
+        f[row_off(g, gz, gx)] =
             fp16 ? T(__half2float(static_cast<const __half *>(src)[ci]) * s) : static_cast<const T *>(src)[ci];
     }
 }
@@ -98,18 +104,22 @@ __global__ void k_residual(const T *__restrict__ gath, const T *__restrict__ d, 
 template <typename T>
 __global__ void k_fold(const Geom g, const T *__restrict__ G, long long gshot, int nshots,
                        const T *__restrict__ vpad, double inv_h2, double *acc) {
-    const long long nint = (long long)g.nz * g.nx;
+    const long long nint = (long long)g.nz * g.ny * g.nx;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nint; i += (long long)gridDim.x * blockDim.x) {
-        const int iz = (int)(i / g.nx), ix = (int)(i % g.nx);
+        const int ix = (int)(i % g.nx);
+        const long long zy = i / g.nx;
+        const int iy = (int)(zy % g.ny), iz = (int)(zy / g.ny);
         const int za = iz == 0 ? 0 : iz + g.oz, zb = iz == g.nz - 1 ? g.NZ : iz + g.oz + 1;
+        const int ya = iy == 0 ? 0 : iy + g.oy, yb = iy == g.ny - 1 ? g.NY : iy + g.oy + 1;
         const int xa = ix == 0 ? 0 : ix + g.ox, xb = ix == g.nx - 1 ? g.NX : ix + g.ox + 1;
         double sum = 0.0;
         for (int s = 0; s < nshots; s++)
             for (int z = za; z < zb; z++)
-                for (int x = xa; x < xb; x++) {
-                    const double v = (double)vpad[cell_off(g, z, 0, x)];
-                    sum += -2.0 * inv_h2 / v * (double)G[s * gshot + cell_off(g, z, 0, x)];
-                }
+                for (int y = ya; y < yb; y++)
+                    for (int x = xa; x < xb; x++) {
+                        const double v = (double)vpad[cell_off(g, z, y, x)];
+                        sum += -2.0 * inv_h2 / v * (double)G[s * gshot + cell_off(g, z, y, x)];
+                    }
         acc[i] += sum;
     }
 }

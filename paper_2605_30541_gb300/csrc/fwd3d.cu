@@ -47,8 +47,13 @@ constexpr int slot3d() {
     return (NW * RY + 8) * SW3 + 2 * NW * RY * TX;
 }
 
-template <int RY>
-__global__ void __launch_bounds__(NTH, 2) k_step3d(const StepArgs<float> A, const int n, const int zchunk) {
+// MODE (kModeForward / kModeRecord / kModeAdjoint) as in the 2D kernel: the
+// record sweep also writes the imaging term Q'^n = E (p^{n+1} - p^{n-1}) -
+// h^2 L p^n of each cell to qs (the source's share is added by the injection
+// kernel), the adjoint sweep adds u^{n+1} Q'^n, read from qs, to Gs.
+template <int RY, int MODE>
+__global__ void __launch_bounds__(NTH, 2) k_step3d(const StepArgs<float> A, const int n, const int zchunk,
+                                                   float *qs, float *Gs) {
     constexpr int TY = NW * RY, NR = TY + 8;  // staged rows per plane
     constexpr int SLOT = slot3d<RY>();
     extern __shared__ float4 sm3[];
@@ -149,7 +154,7 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d(const StepArgs<float> A, cons
             for (int m = 0; m < 9; m++) yv[m] = *reinterpret_cast<const float4 *>(row + (m - 4) * SW3);
             const float4 pp4 = *reinterpret_cast<const float4 *>(cur + NR * SW3 + ly * TX + 4 * lane);
             const float4 ch4 = *reinterpret_cast<const float4 *>(cur + NR * SW3 + TY * TX + ly * TX + 4 * lane);
-            float res[4];
+            float res[4], qk[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const float p = v[4 + k];
@@ -166,14 +171,16 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d(const StepArgs<float> A, cons
                                   float(kC4) * (lane4(q[8][r], k) + lane4(q[0][r], k));
                 const float rhs = d2x + d2y + d2z;
                 const float chv = lane4(ch4, k), pp = lane4(pp4, k);
-                float out;
+                float out, es = 0.f;
                 if (spg) {
-                    const float a = chv * (ez + Ey[r] + lane4(Ex4, k));
+                    es = ez + Ey[r] + lane4(Ex4, k);
+                    const float a = chv * es;
                     out = (2.f * p - (1.f - a) * pp + chv * rhs) / (1.f + a);
                 } else {
                     out = 2.f * p - pp + chv * rhs;
                 }
                 res[k] = out;
+                qk[k] = es * (out - pp) - rhs;
             }
             if (xedge) {
 #pragma unroll
@@ -181,9 +188,21 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d(const StepArgs<float> A, cons
                     if (gx0 + k >= g.NX) res[k] = 0.f;
             }
             if (g.fs && z == 0) res[0] = res[1] = res[2] = res[3] = 0.f;
-            if (gy < g.NY)
-                *reinterpret_cast<float4 *>(pn + own0 + (long long)z * PP + r * g.P) =
-                    make_float4(res[0], res[1], res[2], res[3]);
+            if (gy < g.NY) {
+                const long long o = own0 + (long long)z * PP + r * g.P;
+                *reinterpret_cast<float4 *>(pn + o) = make_float4(res[0], res[1], res[2], res[3]);
+                if (MODE == kModeRecord)
+                    *reinterpret_cast<float4 *>(qs + sh + o) = make_float4(qk[0], qk[1], qk[2], qk[3]);
+                if (MODE == kModeAdjoint) {
+                    const float4 q4 = *reinterpret_cast<const float4 *>(qs + sh + o);
+                    float4 g4 = *reinterpret_cast<const float4 *>(Gs + sh + o);
+                    g4.x += res[0] * q4.x;
+                    g4.y += res[1] * q4.y;
+                    g4.z += res[2] * q4.z;
+                    g4.w += res[3] * q4.w;
+                    *reinterpret_cast<float4 *>(Gs + sh + o) = g4;
+                }
+            }
         }
         __syncthreads();  // this slot is restaged at the next plane
     }
@@ -379,6 +398,40 @@ __global__ void k_inject3d(const StepArgs<float> A, const StepTime t, const Pt3 
     pn[o] += A.ch[o] * A.src_scale * P.w[c] * w / (1.f + a);
 }
 
+// Point injection into p^{n+1} by target cell (deterministic order of the
+// entries of a cell): value = wavelet[row] (kind 0) or the residual of
+// receiver pt at row (kind 1). With the record / adjoint modes the cell's
+// imaging term gets the source's share / its G the injected part of u^{n+1}.
+__global__ void k_inj3d(const StepArgs<float> A, const int n, const int row, const Inj3 *grp, const int ngrp,
+                        const InjE3 *ent, const int kind, const int mode, float *qs, float *Gs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ngrp || row < 0 || row >= A.nt) return;
+    const Inj3 G = grp[i];
+    if (G.shot >= 0 && blockIdx.y != 0) return;
+    const int shot = G.shot >= 0 ? G.shot : blockIdx.y;
+    const Geom &g = A.g;
+    const SimIO *io = A.io;
+    float sum = 0.f;
+    for (int e = G.e0; e < G.e1; e++) {
+        const InjE3 E = ent[e];
+        const float val = kind == 0 ? static_cast<const float *>(io->wavelet)[row]
+                                    : static_cast<const float *>(io->resid)[((long long)shot * A.nt + row) * io->nrec + E.pt];
+        sum += E.w * val;
+    }
+    const long long o = G.cell, so = (long long)shot * g.fstride + o;
+    float es = 0.f;
+    if (A.bc == SIM_BC_SPONGE) {
+        const long long r = o - g.org, PP = (long long)g.PY * g.P;
+        const int z = (int)(r / PP), y = (int)((r % PP) / g.P), x = (int)(r % g.P);
+        es = A.E[0][z] + A.E[1][y] + A.E[2][x];
+    }
+    const float chv = A.ch[o];
+    const float d = chv * A.src_scale * sum / (1.f + chv * es);
+    A.pbuf[(n + 1) & 1][so] += d;
+    if (mode == kModeRecord) qs[so] += es * d - A.src_scale * sum;
+    if (mode == kModeAdjoint) Gs[so] += d * qs[so];
+}
+
 __global__ void k_sample3d(const StepArgs<float> A, const StepTime t, const Pt3 *rec, int nrec, int nshots) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)nrec * nshots) return;
@@ -430,14 +483,26 @@ size_t smem3d() {
 }  // namespace
 
 cudaError_t configure_step3d() {
-    cudaError_t e = cudaFuncSetAttribute(k_step3d<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3d<1>());
+    cudaError_t e = cudaFuncSetAttribute(k_step3d<1, kModeForward>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem3d<1>());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_step3d<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3d<2>());
+        e = cudaFuncSetAttribute(k_step3d<1, kModeRecord>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem3d<1>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step3d<1, kModeAdjoint>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem3d<1>());
     return e;
 }
 
+template <int RY, int MODE>
+cudaError_t launch_step3d_mode(cudaLaunchConfig_t &cfg, const StepArgs<float> &a, int n, int zchunk, float *qs,
+                               float *Gs) {
+    cfg.dynamicSmemBytes = smem3d<RY>();
+    return cudaLaunchKernelEx(&cfg, k_step3d<RY, MODE>, a, n, zchunk, qs, Gs);
+}
+
 cudaError_t launch_step3d(const StepArgs<float> &a, int n, int ry, int zchunk, int nshots, cudaStream_t st,
-                          bool pdl) {
+                          bool pdl, int mode, float *qs, float *Gs) {
     const int nchunk = (a.g.NZ + zchunk - 1) / zchunk;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(a.ntx, (a.g.NY + NW * ry - 1) / (NW * ry), nchunk * nshots);
@@ -448,12 +513,17 @@ cudaError_t launch_step3d(const StepArgs<float> &a, int n, int ry, int zchunk, i
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    if (ry == 1) {
-        cfg.dynamicSmemBytes = smem3d<1>();
-        return cudaLaunchKernelEx(&cfg, k_step3d<1>, a, n, zchunk);
-    }
-    cfg.dynamicSmemBytes = smem3d<2>();
-    return cudaLaunchKernelEx(&cfg, k_step3d<2>, a, n, zchunk);
+    if (ry != 1) return cudaErrorInvalidValue;
+    if (mode == kModeRecord) return launch_step3d_mode<1, kModeRecord>(cfg, a, n, zchunk, qs, Gs);
+    if (mode == kModeAdjoint) return launch_step3d_mode<1, kModeAdjoint>(cfg, a, n, zchunk, qs, Gs);
+    return launch_step3d_mode<1, kModeForward>(cfg, a, n, zchunk, qs, Gs);
+}
+
+cudaError_t launch_inj3d(const StepArgs<float> &a, int n, int row, const Inj3 *grp, int ngrp, const InjE3 *ent,
+                         int kind, int nshots, int mode, float *qs, float *Gs, cudaStream_t st) {
+    if (ngrp <= 0) return cudaSuccess;
+    k_inj3d<<<dim3((ngrp + 127) / 128, nshots), 128, 0, st>>>(a, n, row, grp, ngrp, ent, kind, mode, qs, Gs);
+    return cudaGetLastError();
 }
 
 // CPML side kernels for one axis: boxes = the two strips (psi) or the two

@@ -254,6 +254,8 @@ struct sim_s {
     int tuned_nshots = 0;  // shot count the tile shape was tuned for (0: not yet)
     Pt3 *src3 = nullptr, *rec3 = nullptr;  // 3D point tables
     int *rdone = nullptr;                  // resident path: step counter per (shot, subdomain)
+    Inj3 *src3g = nullptr, *res3g = nullptr;  // 3D adjoint: injection groups (sources, residuals)
+    InjE3 *src3e = nullptr, *res3e = nullptr;
     RTile *rtiles = nullptr;               // resident path: subdomain descriptors
     const TileMap *tmap = nullptr;         // set while lists are built for a non-uniform tiling
     std::list<std::pair<int, ResidentPlan>> rplans;  // per shot count
@@ -764,6 +766,16 @@ sim_status autotune(sim_t s, int nshots) {
     return SIM_OK;
 }
 
+// z-chunks of the 3D z-march: enough CTAs for two per SM, at least 64 planes per chunk
+int zchunk_for(const sim_s *s, int nshots) {
+    const Geom &g = s->g;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->dev);
+    const long long cols = (long long)s->ntx * ((g.NY + 7) / 8) * nshots;
+    const int chunks = (int)std::max<long long>(1, std::min<long long>((2LL * sms + cols - 1) / cols, g.NZ / 64));
+    return (g.NZ + chunks - 1) / chunks;
+}
+
 // 3D points: the 8 trilinear corners of each point as field offsets.
 sim_status points3d(sim_t s, int npts, const double *pos, std::vector<Pt3> &out, bool drop_surface,
                     const char *what) {
@@ -826,12 +838,7 @@ sim_status forward3d(sim_t s, int nshots, const void *wav, const double *src_pos
     a.inj_per_shot = 1;
     a.inj_kind = 0;
     a.sample = nrec > 0 && gdev != nullptr;
-    // z-chunks: enough CTAs for two per SM, at least 64 planes per chunk
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->dev);
-    const long long cols = (long long)s->ntx * ((g.NY + 7) / 8) * nshots;
-    int chunks = (int)std::max<long long>(1, std::min<long long>((2LL * sms + cols - 1) / cols, g.NZ / 64));
-    s->zchunk = (g.NZ + chunks - 1) / chunks;
+    s->zchunk = zchunk_for(s, nshots);
     const bool cpml = d.bc == SIM_BC_CPML;
     const int on[3] = {s->psi[0][0] != nullptr, s->psi[1][0] != nullptr, s->psi[2][0] != nullptr};
     const bool has_src = !src.empty(), has_snap = io.snaps != nullptr;
@@ -1159,7 +1166,7 @@ sim_status ensure_adjoint(sim_t s) {
     s->qbuf = A((size_t)s->seg * ms * g.fstride * s->esz);
     s->qscale = static_cast<float *>(A((size_t)s->seg * ms * ntiles * sizeof(float)));
     s->ckpt = A((size_t)s->nseg * 2 * ms * ncomp * s->esz);
-    const size_t ck_tiles = (size_t)((g.NX + kTileX2 - 1) / kTileX2) * ((g.NZ + kTileZ2 - 1) / kTileZ2);
+    const size_t ck_tiles = (size_t)((g.NX + kTileX2 - 1) / kTileX2) * ((g.NZ * g.NY + kTileZ2 - 1) / kTileZ2);
     s->ckscale = static_cast<float *>(A((size_t)s->nseg * 2 * ms * ck_tiles * sizeof(float)));
     s->res = A(nrows * s->esz);
     s->dobs = A(nrows * s->esz);
@@ -1169,8 +1176,214 @@ sim_status ensure_adjoint(sim_t s) {
     s->inj2_start = static_cast<int *>(A(s->cap_start * sizeof(int)));
     s->inj2_grp = static_cast<InjGroup *>(A(s->cap_grp * sizeof(InjGroup)));
     s->inj2_ent = A(s->cap_grp * sizeof(InjEntryT<double>));
+    if (g.ndim == 3) {
+        s->src3g = static_cast<Inj3 *>(A(8 * (size_t)ms * sizeof(Inj3)));
+        s->src3e = static_cast<InjE3 *>(A(8 * (size_t)ms * sizeof(InjE3)));
+        s->res3g = static_cast<Inj3 *>(A(8 * (size_t)std::max(1, d.max_rec) * sizeof(Inj3)));
+        s->res3e = static_cast<InjE3 *>(A(8 * (size_t)std::max(1, d.max_rec) * sizeof(InjE3)));
+    }
     if (rc == SIM_OK) s->adj_ready = true;
     return rc;
+}
+
+// Injection groups of 3D points (adjoint path): every corner with a non-zero
+// weight off the free surface, grouped by target cell in a fixed order;
+// shot >= 0 gives each point's groups to that shot, -1 shares them.
+void group3d(const std::vector<Pt3> &pts, bool per_shot, std::vector<Inj3> &grp, std::vector<InjE3> &ent) {
+    struct C {
+        long long cell;
+        int shot, pt;
+        float w;
+    };
+    std::vector<C> cs;
+    for (size_t q = 0; q < pts.size(); q++)
+        for (int k = 0; k < 8; k++)
+            if (pts[q].cell[k] >= 0) cs.push_back({pts[q].cell[k], per_shot ? (int)q : -1, (int)q, pts[q].w[k]});
+    std::stable_sort(cs.begin(), cs.end(), [](const C &a, const C &b) {
+        return a.shot != b.shot ? a.shot < b.shot : a.cell < b.cell;
+    });
+    grp.clear();
+    ent.clear();
+    for (size_t i = 0; i < cs.size();) {
+        Inj3 G{};
+        G.cell = cs[i].cell;
+        G.shot = cs[i].shot;
+        G.e0 = (int)ent.size();
+        size_t j = i;
+        while (j < cs.size() && cs[j].cell == cs[i].cell && cs[j].shot == cs[i].shot) {
+            ent.push_back(InjE3{cs[j].pt, cs[j].w});
+            j++;
+        }
+        G.e1 = (int)ent.size();
+        grp.push_back(G);
+        i = j;
+    }
+}
+
+// The adjoint-state gradient on the 3D path: the 2D path's sweeps (forward
+// with checkpoints, residual, per segment a recompute recording Q' and the
+// adjoint sweep accumulating u^{n+1} Q'), with the z-march in its record /
+// adjoint modes and point injection grouped by cell. Q' slots are FP32
+// (checkpoints may be FP16); sponge or no absorption.
+sim_status adjoint3d(sim_t s, int nshots, const void *wavelet, const double *src_pos, int nrec,
+                     const double *rec_pos, const void *d_obs, void *gather_out, double *misfit_out, int ckpt_fp16,
+                     void *grad_v) {
+    const sim_desc &d = s->d;
+    const Geom &g = s->g;
+    if (sim_status r = ensure_adjoint(s)) return r;
+    const size_t nt = d.nt;
+    const int ms = d.max_shots;
+    const long long ncomp = (long long)g.NZ * g.NY * g.NX;
+    const long long nint = (long long)g.nz * g.ny * g.nx;
+    const size_t nrows = (size_t)nshots * nt * nrec;
+    const void *wav = wavelet;
+    if (!is_device_ptr(wavelet)) {
+        if (sim_status r = s->cuda(cudaMemcpyAsync(s->wave, wavelet, nt * sizeof(float), cudaMemcpyHostToDevice,
+                                                   s->st), "wavelet upload"))
+            return r;
+        wav = s->wave;
+    }
+    if (sim_status r = s->cuda(cudaMemcpyAsync(s->dobs, d_obs, nrows * sizeof(float), cudaMemcpyDefault, s->st),
+                               "d_obs copy"))
+        return r;
+    const bool g_host = gather_out && !is_device_ptr(gather_out);
+    const bool gr_host = !is_device_ptr(grad_v);
+    void *grdev = gr_host ? s->gradst : grad_v;
+    if (gr_host)
+        if (sim_status r = s->cuda(cudaMemcpyAsync(grdev, grad_v, nint * sizeof(float), cudaMemcpyHostToDevice, s->st),
+                                   "gradient upload"))
+            return r;
+    // points: receivers for sampling (all corners), sources and residuals for injection
+    std::vector<Pt3> src, rsam, rinj;
+    if (sim_status r = points3d(s, nshots, src_pos, src, true, "source")) return r;
+    if (sim_status r = points3d(s, nrec, rec_pos, rsam, false, "receiver")) return r;
+    if (sim_status r = points3d(s, nrec, rec_pos, rinj, true, "receiver")) return r;
+    std::vector<Inj3> sg, rg;
+    std::vector<InjE3> se, re;
+    group3d(src, true, sg, se);
+    group3d(rinj, false, rg, re);
+    if (sim_status r = s->cuda(cudaMemcpyAsync(s->rec3, rsam.data(), rsam.size() * sizeof(Pt3),
+                                               cudaMemcpyHostToDevice, s->st), "receiver upload"))
+        return r;
+    if (sim_status r = upload(s, s->src3g, sg, 8 * (size_t)ms, "source group")) return r;
+    if (sim_status r = upload(s, s->src3e, se, 8 * (size_t)ms, "source entry")) return r;
+    if (sim_status r = upload(s, s->res3g, rg, 8 * (size_t)std::max(1, d.max_rec), "residual group")) return r;
+    if (sim_status r = upload(s, s->res3e, re, 8 * (size_t)std::max(1, d.max_rec), "residual entry")) return r;
+    SimIO io{};
+    io.wavelet = wav;
+    io.gather = s->gath;
+    io.resid = s->res;
+    io.nrec = nrec;
+    io.nshots = nshots;
+    if (sim_status r = s->cuda(cudaMemcpyAsync(s->io, &io, sizeof io, cudaMemcpyHostToDevice, s->st), "io upload"))
+        return r;
+
+    const int L = s->seg, zc = zchunk_for(s, nshots);
+    const size_t ck_state = (size_t)ms * ncomp;
+    const int ckx = (g.NX + kTileX2 - 1) / kTileX2, ckz = (g.NZ * g.NY + kTileZ2 - 1) / kTileZ2;
+    const size_t ck_tiles = (size_t)ms * ckx * ckz;
+    auto ck_ptr = [&](int k, int which) {
+        return static_cast<char *>(s->ckpt) + ((size_t)k * 2 + which) * ck_state * (ckpt_fp16 ? 2 : sizeof(float));
+    };
+    auto ck_scale = [&](int k, int which) { return s->ckscale + ((size_t)k * 2 + which) * ck_tiles; };
+    StepArgs<float> a = step_args<float>(s);
+    a.sample = 1;
+    a.nsnap = 0;
+    StepArgs<float> adj = a;
+    adj.pbuf[0] = static_cast<float *>(s->ubuf);
+    adj.pbuf[1] = static_cast<float *>(s->ubuf) + (long long)ms * g.fstride;
+    adj.src_scale = (float)(d.h * d.h);
+    float *Gs = static_cast<float *>(s->Gbuf);
+    const size_t qslot = (size_t)ms * g.fstride;  // floats per slot
+    const size_t ub = (size_t)g.fstride * sizeof(float) * nshots;
+    const int nsg = (int)sg.size(), nrg = (int)rg.size();
+    const Pt3 *r3 = s->rec3;
+    const long long gkey = ((long long)nshots << 40) ^ ((long long)nrec << 16) ^ ((long long)ckpt_fp16 << 3) ^ 6;
+    if (sim_status r = run_graph(s, gkey, [&](cudaStream_t st) {
+            cudaError_t e = reset_state_on(s, nshots, st);
+            for (int n = 0; n < d.nt && e == cudaSuccess; n++) {
+                if (n % L == 0) {
+                    const int k = n / L;
+                    e = launch_store_state<float>(g, a.pbuf[n & 1], ck_ptr(k, 1), ck_scale(k, 1), ckpt_fp16,
+                                                  nshots, ncomp, ckx, ckz, st);
+                    if (e == cudaSuccess)
+                        e = launch_store_state<float>(g, a.pbuf[(n + 1) & 1], ck_ptr(k, 0), ck_scale(k, 0),
+                                                      ckpt_fp16, nshots, ncomp, ckx, ckz, st);
+                }
+                if (e == cudaSuccess)
+                    e = launch_sample3d(a, step_time(s, a, n, kModeForward, nullptr, nullptr), r3, nrec, nshots, st);
+                if (e == cudaSuccess) e = launch_step3d(a, n, 1, zc, nshots, st, true, kModeForward);
+                if (e == cudaSuccess)
+                    e = launch_inj3d(a, n, n, s->src3g, nsg, s->src3e, 0, nshots, kModeForward, nullptr, nullptr, st);
+            }
+            if (e == cudaSuccess)
+                e = launch_residual<float>(static_cast<const float *>(s->gath), static_cast<const float *>(s->dobs),
+                                           static_cast<float *>(s->res), (long long)nrows, s->mpart, kResidBlocks,
+                                           st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(s->ubuf, 0, ub, st);
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(static_cast<char *>(s->ubuf) + (size_t)g.fstride * sizeof(float) * ms, 0, ub,
+                                    st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(s->Gbuf, 0, ub, st);
+            for (int sgi = s->nseg - 1; sgi >= 0 && e == cudaSuccess; sgi--) {
+                const int n0 = sgi * L, n1 = std::min(n0 + L, d.nt);
+                e = launch_load_state<float>(g, a.pbuf[n0 & 1], ck_ptr(sgi, 1), ck_scale(sgi, 1), ckpt_fp16, nshots,
+                                             ncomp, ckx, ckz, st);
+                if (e == cudaSuccess)
+                    e = launch_load_state<float>(g, a.pbuf[(n0 + 1) & 1], ck_ptr(sgi, 0), ck_scale(sgi, 0),
+                                                 ckpt_fp16, nshots, ncomp, ckx, ckz, st);
+                for (int n = n0; n < n1 && e == cudaSuccess; n++) {
+                    float *slot = static_cast<float *>(s->qbuf) + (size_t)(n - n0) * qslot;
+                    e = launch_step3d(a, n, 1, zc, nshots, st, true, kModeRecord, slot, nullptr);
+                    if (e == cudaSuccess)
+                        e = launch_inj3d(a, n, n, s->src3g, nsg, s->src3e, 0, nshots, kModeRecord, slot, nullptr, st);
+                }
+                for (int k = n1; k >= n0 + 1 && e == cudaSuccess; k--) {
+                    float *slot = static_cast<float *>(s->qbuf) + (size_t)(k - 1 - n0) * qslot;
+                    const int n = d.nt - k;
+                    e = launch_step3d(adj, n, 1, zc, nshots, st, true, kModeAdjoint, slot, Gs);
+                    if (e == cudaSuccess)
+                        e = launch_inj3d(adj, n, k, s->res3g, nrg, s->res3e, 1, nshots, kModeAdjoint, slot, Gs, st);
+                }
+            }
+            if (e == cudaSuccess) e = cudaMemsetAsync(s->acc, 0, nint * sizeof(double), st);
+            if (e == cudaSuccess)
+                e = launch_fold_gradient<float>(g, Gs, g.fstride, nshots, static_cast<const float *>(s->vpad),
+                                                1.0 / (d.h * d.h), s->acc, st);
+            return e;
+        }))
+        return r;
+    if (sim_status r = s->cuda(launch_add_gradient<float>(s->acc, static_cast<float *>(grdev), nint, s->st),
+                               "gradient add"))
+        return r;
+    if (sim_status r = s->cuda(launch_check_finite<float>(g, a.pbuf[d.nt & 1], nshots, s->flags, s->st),
+                               "finite check"))
+        return r;
+    if (sim_status r = s->cuda(cudaMemcpyAsync(s->flags_host, s->flags, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                               s->st), "flag readback"))
+        return r;
+    if (gr_host)
+        if (sim_status r = s->cuda(cudaMemcpyAsync(grad_v, grdev, nint * sizeof(float), cudaMemcpyDeviceToHost, s->st),
+                                   "gradient download"))
+            return r;
+    if (gather_out)
+        if (sim_status r = s->cuda(cudaMemcpyAsync(gather_out, s->gath, nrows * sizeof(float), cudaMemcpyDefault,
+                                                   s->st), "gather copy"))
+            return r;
+    std::vector<double> part(kResidBlocks);
+    if (misfit_out)
+        if (sim_status r = s->cuda(cudaMemcpyAsync(part.data(), s->mpart, part.size() * sizeof(double),
+                                                   cudaMemcpyDeviceToHost, s->st), "misfit readback"))
+            return r;
+    if (misfit_out || gr_host || g_host) {
+        if (sim_status r = poll_flags(s, true)) return r;
+        if (misfit_out) {
+            double J = 0;
+            for (double v : part) J += v;
+            *misfit_out = J;
+        }
+    }
+    return SIM_OK;
 }
 
 template <typename T>
@@ -1179,11 +1392,14 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
                      void *grad_v) {
     const sim_desc &d = s->d;
     const Geom &g = s->g;
-    if (g.ndim != 2) return s->fail(SIM_ERR_UNSUPPORTED, "the 3D adjoint is not built");
+    if (g.ndim == 3 && d.precision != SIM_FP32) return s->fail(SIM_ERR_UNSUPPORTED, "the 3D path runs in FP32");
     if (d.bc == SIM_BC_CPML) return s->fail(SIM_ERR_UNSUPPORTED, "the adjoint supports sponge or no absorption");
     if (ckpt_fp16 && d.precision != SIM_FP32) return s->fail(SIM_ERR_ARG, "FP16 checkpoints need an FP32 handle");
     if (nrec < 1) return s->fail(SIM_ERR_ARG, "the misfit needs receivers");
     if (!d_obs || !wavelet || !grad_v) return s->fail(SIM_ERR_ARG, "d_obs, wavelet and grad_v are required");
+    if (g.ndim == 3)
+        return adjoint3d(s, nshots, wavelet, src_pos, nrec, rec_pos, d_obs, gather_out, misfit_out, ckpt_fp16,
+                         grad_v);
     if (sim_status r = ensure_adjoint(s)) return r;
     if (sim_status r = autotune(s, nshots)) return r;
     const size_t nt = d.nt;
@@ -1251,7 +1467,7 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
 
     const int L = s->seg;
     const size_t ck_state = (size_t)ms * ncomp;  // elements of one checkpointed state (all shots)
-    const int ckx = (g.NX + kTileX2 - 1) / kTileX2, ckz = (g.NZ + kTileZ2 - 1) / kTileZ2;  // store-kernel tiles
+    const int ckx = (g.NX + kTileX2 - 1) / kTileX2, ckz = (g.NZ * g.NY + kTileZ2 - 1) / kTileZ2;  // store tiles
     const size_t ck_tiles = (size_t)ms * ckx * ckz;
     const size_t q_tiles = (size_t)ms * ntiles;
     auto ck_ptr = [&](int k, int which) {

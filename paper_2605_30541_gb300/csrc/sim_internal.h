@@ -182,7 +182,21 @@ int batch_blocks_per_sm(int tz, bool cpml);
 // update, CPML zeta + addend, source injection.
 cudaError_t configure_step3d();
 cudaError_t launch_step3d(const StepArgs<float> &a, int n, int ry, int zchunk, int nshots, cudaStream_t st,
-                          bool pdl);
+                          bool pdl, int mode = kModeForward, float *qs = nullptr, float *Gs = nullptr);
+// 3D point injection grouped by target cell (the adjoint path): group =
+// cell offset within a field, entry range, shot (-1: the same for every
+// shot, the launch's y index).
+struct Inj3 {
+    long long cell;
+    int e0, e1;
+    int shot, pad;
+};
+struct InjE3 {
+    int pt;
+    float w;
+};
+cudaError_t launch_inj3d(const StepArgs<float> &a, int n, int row, const Inj3 *grp, int ngrp, const InjE3 *ent,
+                         int kind, int nshots, int mode, float *qs, float *Gs, cudaStream_t st);
 cudaError_t launch_cpml3d(const StepArgs<float> &a, int n, int ax, int phase, int nshots, cudaStream_t st);
 cudaError_t launch_sample3d(const StepArgs<float> &a, const StepTime &t, const void *rec, int nrec, int nshots,
                             cudaStream_t st);
