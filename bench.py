@@ -68,7 +68,7 @@ def workload(args):
     return cfg, nshots
 
 
-PATH_STEP, PATH_RESIDENT = 1, 2  # sim_info.last_path
+PATH_STEP, PATH_RESIDENT, PATH_MARCH = 1, 2, 4  # sim_info.last_path
 
 
 def padded_cells(cfg):
@@ -294,6 +294,10 @@ def run_batch(args):
     value = args.steps * nt * cells / total / 1e9
     peak, peak_kind = read_peaks()
     algo = sum(algorithmic_bytes_per_launch(c, len(c["src"])) for c in slices) * nt
+    sched = os.environ.get("GSIM_BATCH", "march")
+    kfile, kname, kkey = (("fwd2d_f32.cu", "k_multi2d", "multi_") if sched == "stepped" else
+                          ("fwd2d_f32.cu", "k_batch2d", "batch_") if sched == "persistent" else
+                          ("march2d.cu", "k_march2d", "march_"))
     line = {"metric": METRIC, "value": value, "unit": "Gcell/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -301,14 +305,14 @@ def run_batch(args):
                                     "free top), band 3-6 Hz, nt=%d, 1000 receivers, saved every 14 steps" % nt)
                                    if args.workload == "c6g" else
                                    ("c3: 64 shots on a 619x1000 slice + 16 uneven slices x 8 shots, nt=%d, "
-                                    "one launch per step over all slices and shots (stepped batch)" % nt),
+                                    "one launch per step over all slices and shots (%s batch)" % (nt, sched)),
                        "seconds_per_slice_band": total / args.steps if args.workload == "c6g" else None,
                        "padded_cells_x_shots": cells,
                        "l2": "flushed between timed solves"},
             "roofline": {"bound": "hbm", "achieved": algo / (total / args.steps) / 1e9, "peak": peak,
                          "unit": "GB/s", "frac": algo / (total / args.steps) / 1e9 / peak,
-                         "traffic": ncu_traffic("fwd2d_f32.cu", "multi_" + args.workload), "traffic_per": "step launch",
-                         "kernel": "k_multi2d", "peak_kind": peak_kind,
+                         "traffic": ncu_traffic(kfile, kkey + args.workload), "traffic_per": "step launch",
+                         "kernel": kname, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_solve": algo},
             "clocks": clk.summary(), "gpu_launches": args.steps * nt}
     print(json.dumps(line), flush=True)
@@ -433,14 +437,16 @@ def run_ours(args):
     algo = algorithmic_bytes_per_launch(cfg, nshots) * (nt if path == PATH_RESIDENT else 1)
     peak, peak_kind = read_peaks()
     achieved = algo / per_launch_s / 1e9
-    key = "%s_%s" % ("resident" if path == PATH_RESIDENT else "step", args.workload)
+    pname = {PATH_RESIDENT: "resident", PATH_MARCH: "march"}.get(path, "step")
+    key = "%s_%s" % (pname, args.workload)
     kfile, kname = (("fwd3d.cu", "k_step3d") if cfg["ndim"] == 3 else
-                    ("resident2d.cu", "k_resident2d") if path == PATH_RESIDENT else ("fwd2d_f32.cu", "k_step2d_f32"))
+                    ("resident2d.cu", "k_resident2d") if path == PATH_RESIDENT else
+                    ("march2d.cu", "k_march2d") if path == PATH_MARCH else ("fwd2d_f32.cu", "k_step2d_f32"))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": ncu_traffic(kfile, key), "kernel": kname,
             "peak_kind": peak_kind + " (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind,
             "algorithmic_bytes_per_launch": algo, "avg_launch_us": per_launch_s * 1e6,
-            "path": "resident" if path == PATH_RESIDENT else "per-step"}
+            "path": {PATH_RESIDENT: "resident", PATH_MARCH: "row march, one launch per step"}.get(path, "per-step")}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None

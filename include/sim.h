@@ -106,7 +106,9 @@ typedef struct {
     int last_path;            /* how the last sim_forward ran: 0 none yet, 1 one kernel launch per
                                  step (captured as a CUDA graph), 2 resident: the whole time loop in
                                  one cooperative launch that keeps the wavefield on chip (2D FP32
-                                 runs whose subdomains all fit on the GPU at once), 3 the 3D path */
+                                 runs whose subdomains all fit on the GPU at once), 3 the 3D path,
+                                 4 row march: one launch per step in which every warp streams
+                                 down a 128-column strip of rows (2D FP32, when not resident) */
     int last_rows;            /* path 2: rows of the tallest resident subdomain (x 128 columns) */
 } sim_info;
 

@@ -252,6 +252,7 @@ struct sim_s {
     std::vector<std::pair<long long, cudaGraphExec_t>> graphs;
     bool use_graphs = true;
     int tuned_nshots = 0;  // shot count the tile shape was tuned for (0: not yet)
+    bool use_march = false; // the autotuner's choice: row march rather than the tiled step kernel
     Pt3 *src3 = nullptr, *rec3 = nullptr;  // 3D point tables
     int *rdone = nullptr;                  // resident path: step counter per (shot, subdomain)
     Inj3 *src3g = nullptr, *res3g = nullptr;  // 3D adjoint: injection groups (sources, residuals)
@@ -259,6 +260,13 @@ struct sim_s {
     RTile *rtiles = nullptr;               // resident path: subdomain descriptors
     const TileMap *tmap = nullptr;         // set while lists are built for a non-uniform tiling
     std::list<std::pair<int, ResidentPlan>> rplans;  // per shot count
+    MarchSeg *mseg = nullptr;              // row march: segments, warp ranges, slice arguments
+    int *mwseg = nullptr;
+    StepArgs<float> *mslice = nullptr;
+    size_t cap_mseg = 0, cap_mwseg = 0;
+    long long march_key = -1;              // (shot count, item rows, tile height) of the plan on the device
+    int march_nwarps = 0, march_nitems = 0;
+    unsigned *mctr = nullptr;              // dynamic schedule: per-step item counters
     int last_path = 0, last_rows = 0;      // see sim_info
     int zchunk = 0;                        // z-march chunk of the 3D kernel
     // adjoint-state buffers, allocated by the first sim_adjoint call
@@ -461,7 +469,10 @@ sim_status build_receivers(sim_t s, int nrec, const double *rec_pos, std::vector
                 for (int dx = 0; dx < 2; dx++) e.w[k++] = T(corner_weight(t, dz, dy, dx));
         tmp.push_back({tl, e});
     }
-    std::stable_sort(tmp.begin(), tmp.end(), [](const auto &a, const auto &b) { return a.first < b.first; });
+    // by tile, then by row within the tile (the row march walks them in order)
+    std::stable_sort(tmp.begin(), tmp.end(), [](const auto &a, const auto &b) {
+        return a.first != b.first ? a.first < b.first : a.second.lz < b.second.lz;
+    });
     start.assign(ntiles + 1, 0);
     ent.clear();
     for (auto &p : tmp) {
@@ -697,9 +708,22 @@ void set_tile_z(sim_t s, int tz) {
     s->ntz = (s->g.NZ + tz - 1) / tz;
 }
 
+bool march_enabled(const sim_s *s);
+sim_status march_prepare(sim_t s, const StepArgs<float> &a, int nshots, MarchArgs &m);
+
+// 2D FP32 forward: the row march (march2d.cu) is one more candidate, timed
+// the same way; GSIM_MARCH=1 takes it without timing, GSIM_MARCH=0 never.
+int march_forced() {
+    const char *f = getenv("GSIM_MARCH");
+    return f ? (f[0] == '0' ? 0 : 1) : -1;
+}
+
 sim_status autotune(sim_t s, int nshots) {
     if (s->d.precision != SIM_FP32 || s->tuned_nshots == nshots) return SIM_OK;
     s->tuned_nshots = nshots;
+    const bool can_march = march_enabled(s);
+    const int forced = march_forced();
+    s->use_march = can_march && forced != 0;  // untimed default
     if (const char *f = getenv("GSIM_TILE_Z")) {
         const int tz = atoi(f);
         if (tz == 8 || tz == 16 || tz == 32) set_tile_z(s, tz);
@@ -714,7 +738,8 @@ sim_status autotune(sim_t s, int nshots) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            set_tile_z(s, it->second);
+            set_tile_z(s, it->second & 0xff);
+            if (forced < 0) s->use_march = can_march && (it->second >> 8) != 0;
             return SIM_OK;
         }
     }
@@ -757,12 +782,45 @@ sim_status autotune(sim_t s, int nshots) {
             best_tz = tz;
         }
     }
+    bool march_best = false;
+    if (!rc && can_march && forced < 0) {  // the row march, with empty lists of the finest tiling
+        set_tile_z(s, 8);
+        std::vector<int> zeros((size_t)nshots * s->ntx * s->ntz + 1, 0);
+        rc = upload(s, s->rec_start, zeros, s->cap_start, "tune lists");
+        if (!rc) rc = upload(s, s->inj_start, zeros, s->cap_start, "tune lists");
+        if (!rc) rc = reset_state(s, nshots);
+        StepArgs<float> a = step_args<float>(s);
+        a.sample = 0;
+        a.nsnap = 0;
+        MarchArgs m{};
+        if (!rc) rc = march_prepare(s, a, nshots, m);
+        if (!rc) {
+            const int warm = 3, timed = 12;
+            cudaError_t e = m.ctr ? cudaMemsetAsync(m.ctr, 0, 2 * sizeof(unsigned), s->st) : cudaSuccess;
+            for (int n = 0; n < warm + timed && e == cudaSuccess; n++) {
+                if (n == warm) e = cudaEventRecord(e0, s->st);
+                if (e == cudaSuccess)
+                    e = launch_march2d(m, s->d.bc == SIM_BC_CPML, step_time(s, a, n, kModeForward, nullptr, nullptr),
+                                       s->st, false);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s->st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            rc = s->cuda(e, "autotune");
+            if (!rc && getenv("GSIM_TUNE_LOG"))
+                fprintf(stderr, "[gsim autotune] grid %dx%d shots %d row march: %.2f us/step\n", s->g.NZ, s->g.NX,
+                        nshots, 1e3 * ms / timed);
+            if (!rc && ms < best) march_best = true;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     set_tile_z(s, best_tz);
+    if (forced < 0) s->use_march = march_best;
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[key] = best_tz;
+    g_tune_cache[key] = best_tz | (march_best ? 256 : 0);
     return SIM_OK;
 }
 
@@ -1018,6 +1076,213 @@ sim_status run_resident<float>(sim_t s, const StepArgs<float> &a, const Resident
     return s->cuda(launch_resident2d(a, r, plan.rz, nshots, s->st), "resident launch");
 }
 
+// ---------------------------------------------------------------- row march plan
+//
+// The step's work as (member, strip, row) items in member-major order, cut
+// into pieces of equal estimated cost, one per warp that fits on the GPU at
+// once; fewer warps when rows are few, so each marches at least
+// kMarchMinRows rows (a warp re-reads 8 halo rows at the start of each
+// segment). Segments start on multiples of 4 rows (the list tiles are 8, 16
+// or 32 rows high). Cost of one row of a strip: its active lanes plus a fixed share
+// for the row's waits and halo, more where CPML memory terms are updated.
+constexpr int kMarchMinRows = 16;
+struct MarchMember {
+    int slice, shot;
+    const sim_s *s;
+};
+
+void plan_march(const std::vector<MarchMember> &mem, long long max_warps, std::vector<MarchSeg> &segs,
+                std::vector<int> &wseg) {
+    struct Strip {
+        double base;
+        bool cpml;
+    };
+    // cost weights: per active lane, per row, and extra per row of a strip
+    // with x-sponge / x-CPML cells and per row of z-sponge / z-CPML
+    // (GSIM_MARCH_COST="lane,row,spx,cpx,spz,cpz" overrides them)
+    double wl = 0.0, wr = 40.0, wspx = 40.0, wcpx = 40.0, wspz = 40.0, wcpz = 12.0;
+    if (const char *f = getenv("GSIM_MARCH_COST"))
+        sscanf(f, "%lf,%lf,%lf,%lf,%lf,%lf", &wl, &wr, &wspx, &wcpx, &wspz, &wcpz);
+    auto strips = [&](const sim_s *s) {
+        const Geom &g = s->g;
+        std::vector<Strip> v;
+        const bool cp = s->d.bc == SIM_BC_CPML, sp = s->d.bc == SIM_BC_SPONGE;
+        for (int x0 = 0; x0 < g.NX; x0 += kMarchW) {
+            const int lanes = std::min(32, (g.NX - x0 + 3) / 4);
+            const bool ax = (g.nbx0 > 0 && x0 - 4 < g.nbx0) || (g.nbx1 > 0 && x0 + kMarchW + 4 > g.NX - g.nbx1);
+            v.push_back({wl * lanes + wr + (cp && ax ? wcpx : 0.0) + (sp && ax ? wspx : 0.0), cp});
+        }
+        return v;
+    };
+    auto zextra = [&](const sim_s *s, int z) {
+        const Geom &g = s->g;
+        const bool az = (g.nbz0 > 0 && z < g.nbz0 + 4) || (g.nbz1 > 0 && z >= g.NZ - g.nbz1 - 4);
+        if (!az) return 0.0;
+        return s->d.bc == SIM_BC_CPML ? wcpz : s->d.bc == SIM_BC_SPONGE ? wspz : 0.0;
+    };
+    double total = 0;
+    long long rows = 0;
+    for (const MarchMember &m : mem) {
+        const int NZ = m.s->g.NZ;
+        double zx = 0;
+        for (int z = 0; z < NZ; z++) zx += zextra(m.s, z);
+        for (const Strip &st : strips(m.s)) total += st.base * NZ + zx;
+        rows += (long long)NZ * ((m.s->g.NX + kMarchW - 1) / kMarchW);
+    }
+    int min_rows = kMarchMinRows;
+    if (const char *f = getenv("GSIM_MARCH_MINROWS")) min_rows = std::max(1, atoi(f));
+    if (const char *f = getenv("GSIM_MARCH_WAVES")) max_warps *= std::max(1, atoi(f));
+    const int nw = (int)std::max<long long>(1, std::min<long long>(max_warps, rows / min_rows));
+    const double target = total / nw;
+    segs.clear();
+    wseg.assign(1, 0);
+    // Order of the items: by member, then by bands of H rows, then by strip,
+    // then by row. With H about the rows one warp gets, the warps of a CTA
+    // (consecutive pieces) march the neighbouring strips of the same rows
+    // side by side, so HBM sees whole rows rather than 512-byte pieces of
+    // rows far apart. H = 0 (GSIM_MARCH_BAND=0): strip after strip.
+    int H = (int)std::min<long long>(1 << 20, std::max<long long>(16, rows / nw));
+    H = (H + 3) & ~3;
+    if (const char *f = getenv("GSIM_MARCH_BAND")) {
+        const int v = atoi(f);
+        if (v == 0) H = 1 << 30;
+        else if (v > 0) H = (v + 3) & ~3;
+    }
+    double acc = 0, next = target;
+    int w = 0;
+    for (const MarchMember &m : mem) {
+        const std::vector<Strip> sv = strips(m.s);
+        const int NZ = m.s->g.NZ;
+        for (int zc = 0; zc < NZ; zc += H) {
+            const int ze = (int)std::min<long long>(NZ, (long long)zc + H);
+            for (int bx = 0; bx < (int)sv.size(); bx++) {
+                int z0 = zc;
+                for (int z = zc; z < ze; z++) {
+                    acc += sv[bx].base + zextra(m.s, z);
+                    // cuts after rows 4k + 3: segments start on multiples of 4 rows,
+                    // so a 4-row block never straddles two list tiles
+                    if (acc >= next && w < nw - 1 && (z & 3) == 3 && z + 1 < ze) {
+                        segs.push_back(MarchSeg{m.slice, m.shot, bx, z0, z + 1, {0, 0, 0}});
+                        z0 = z + 1;
+                        wseg.push_back((int)segs.size());
+                        w++;
+                        next = target * (w + 1);
+                    }
+                }
+                if (z0 < ze) segs.push_back(MarchSeg{m.slice, m.shot, bx, z0, ze, {0, 0, 0}});
+            }
+        }
+    }
+    wseg.push_back((int)segs.size());
+    if (getenv("GSIM_MARCH_LOG"))
+        fprintf(stderr, "[gsim march] %zu members, %lld strip rows, %d warps (at most %d), %zu segments\n", mem.size(),
+                rows, (int)wseg.size() - 1, max_warps, segs.size());
+}
+
+// Dynamic schedule: the step's work as items of `item` rows of one strip of
+// one member. Items that update CPML memory (their strip within 4 cells of
+// an x strip, or a row within 4 rows of a z strip) take the slower CPML
+// loop, so they come first; then by member, band of rows and strip, so the
+// items taken at about the same time cover neighbouring strips of the same
+// rows. Returns the number of warps to launch (one per item at most).
+int march_item_rows() {
+    int k = 16;
+    if (const char *f = getenv("GSIM_MARCH_ITEM")) k = atoi(f);
+    return k <= 0 ? 0 : (k + 3) & ~3;
+}
+int plan_march_items(const std::vector<MarchMember> &mem, long long max_warps, int item, std::vector<MarchSeg> &segs) {
+    segs.clear();
+    for (int pass = 0; pass < 2; pass++)
+        for (const MarchMember &m : mem) {
+            const Geom &g = m.s->g;
+            const bool cp = m.s->d.bc == SIM_BC_CPML;
+            const int NZ = g.NZ, ntx = (g.NX + kMarchW - 1) / kMarchW;
+            for (int zc = 0; zc < NZ; zc += item)
+                for (int bx = 0; bx < ntx; bx++) {
+                    const int x0 = bx * kMarchW, ze = std::min(NZ, zc + item);
+                    const bool c = cp && ((g.nbx0 > 0 && x0 - 4 < g.nbx0) ||
+                                          (g.nbx1 > 0 && x0 + kMarchW + 4 > g.NX - g.nbx1) ||
+                                          (g.nbz0 > 0 && zc < g.nbz0 + 4) || (g.nbz1 > 0 && ze > NZ - g.nbz1 - 4));
+                    if (c == (pass == 0)) segs.push_back(MarchSeg{m.slice, m.shot, bx, zc, ze, {0, 0, 0}});
+                }
+        }
+    return (int)std::min<long long>(max_warps, (long long)segs.size());
+}
+
+bool march_enabled(const sim_s *s) {
+    if (!s->mseg || s->g.ndim != 2 || s->d.precision != SIM_FP32) return false;
+    const char *f = getenv("GSIM_MARCH");
+    return !(f && f[0] == '0');
+}
+
+int device_sms(int dev) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+// Plan (when the shot count or list tiling changed) and slice arguments of a
+// single-handle row march, uploaded to the handle's buffers.
+sim_status march_prepare(sim_t s, const StepArgs<float> &a, int nshots, MarchArgs &m) {
+    const int item = march_item_rows();
+    const long long key = ((long long)nshots << 16) | ((long long)item << 6) | s->tile_z;
+    if (key != s->march_key) {
+        std::vector<MarchMember> mem;
+        for (int k = 0; k < nshots; k++) mem.push_back({0, k, s});
+        std::vector<MarchSeg> segs;
+        std::vector<int> wseg;
+        const int maxw = device_sms(s->dev) * std::max(1, march2d_warps_per_sm(s->d.bc == SIM_BC_CPML));
+        if (item) {
+            s->march_nwarps = plan_march_items(mem, maxw, item, segs);
+            s->march_nitems = (int)segs.size();
+        } else {
+            plan_march(mem, maxw, segs, wseg);
+            if (sim_status r = upload(s, s->mwseg, wseg, s->cap_mwseg, "march warps")) return r;
+            s->march_nwarps = (int)wseg.size() - 1;
+            s->march_nitems = 0;
+        }
+        if (sim_status r = upload(s, s->mseg, segs, s->cap_mseg, "march segments")) return r;
+        s->march_key = key;
+    }
+    if (sim_status r = s->cuda(cudaMemcpyAsync(s->mslice, &a, sizeof a, cudaMemcpyHostToDevice, s->st), "march args"))
+        return r;
+    m.slices = s->mslice;
+    m.segs = s->mseg;
+    m.wseg = s->mwseg;
+    m.ctr = s->march_nitems ? s->mctr : nullptr;
+    m.nwarps = s->march_nwarps;
+    m.nitems = s->march_nitems;
+    m.tz = s->tile_z;
+    return SIM_OK;
+}
+
+// The forward time loop as one row-march launch per step, captured as a graph.
+template <typename T>
+sim_status run_march(sim_t s, const StepArgs<T> &a, int nshots);
+template <>
+sim_status run_march<double>(sim_t s, const StepArgs<double> &, int) {
+    return s->fail(SIM_ERR_UNSUPPORTED, "the row march is FP32 only");
+}
+template <>
+sim_status run_march<float>(sim_t s, const StepArgs<float> &a, int nshots) {
+    MarchArgs m{};
+    if (sim_status r = march_prepare(s, a, nshots, m)) return r;
+    const bool cpml = s->d.bc == SIM_BC_CPML;
+    return run_graph(s, ((long long)nshots << 16) | ((long long)march_item_rows() << 8) | ((long long)s->tile_z << 2) | 3,
+                     [&](cudaStream_t st) {
+        if (m.ctr) {
+            cudaError_t e = cudaMemsetAsync(m.ctr, 0, 2 * sizeof(unsigned), st);
+            if (e != cudaSuccess) return e;
+        }
+        for (int n = 0; n < s->d.nt; n++) {
+            cudaError_t e = launch_march2d(m, cpml, step_time(s, a, n, kModeForward, nullptr, nullptr), st,
+                                           s->use_graphs);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    });
+}
+
 template <typename T>
 sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src_pos, int nrec,
                      const double *rec_pos, void *gather, void *snaps, float *snap_scale) {
@@ -1027,6 +1292,7 @@ sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src
     const int rz = plan ? plan->rz : 0;
     if (g.ndim == 2 && !rz)
         if (sim_status r = autotune(s, nshots)) return r;
+    const bool march = std::is_same<T, float>::value && g.ndim == 2 && !rz && s->use_march;
     const size_t nt = d.nt;
     // inputs
     const void *wav = wavelet;
@@ -1101,12 +1367,14 @@ sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src
     StepArgs<T> a = step_args<T>(s);
     a.inj_per_shot = 1;
     a.inj_kind = 0;
-    s->last_path = rz ? 2 : 1;
+    s->last_path = rz ? 2 : (march ? 4 : 1);
     s->last_rows = 0;
     if (rz)
         for (const RTile &t : plan->tiles) s->last_rows = std::max(s->last_rows, t.rows);
     if (rz) {
         if (sim_status r = run_resident(s, a, *plan, nshots)) return r;
+    } else if (march) {
+        if (sim_status r = run_march(s, a, nshots)) return r;
     } else if (sim_status r = run_graph(s, ((long long)nshots << 8) | ((long long)s->tile_z << 2) | 1,
                                         [&](cudaStream_t st) {
                                             for (int n = 0; n < d.nt; n++) {
@@ -1595,6 +1863,9 @@ struct BatchCtx {
     unsigned long long *head = nullptr;
     unsigned *flags = nullptr, *flags_host = nullptr;
     size_t cap_slices = 0, cap_groups = 0, cap_members = 0, cap_done = 0;
+    void *msegs = nullptr, *mwseg = nullptr;  // row march plan
+    size_t cap_msegs = 0, cap_mwseg = 0;
+    unsigned *mctr = nullptr;                  // row march: per-step item counters
     cudaGraphExec_t exec = nullptr;
     std::vector<char> key;
     cudaEvent_t ev = nullptr;
@@ -1634,13 +1905,16 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
     }
     cudaSetDevice(s0->dev);
     const int nt = s0->d.nt;
-    // Two schedules: "stepped" (default) launches step n of every member at
-    // once, nt launches replayed as a graph (streams the batch through HBM at
-    // the per-step kernel's rate); "persistent" (GSIM_BATCH=persistent) runs
-    // the dataflow kernel k_batch2d, one launch for all steps.
+    // Three schedules: "march" (default) launches step n of every member as
+    // one row-march launch, nt launches replayed as a graph (streams the batch
+    // through HBM); "stepped" (GSIM_BATCH=stepped) does the same with the
+    // tiled step kernel; "persistent" (GSIM_BATCH=persistent) runs the
+    // dataflow kernel k_batch2d, one launch for all steps.
     const char *bm = getenv("GSIM_BATCH");
-    const bool stepped = !(bm && strcmp(bm, "persistent") == 0);
-    int tz = stepped ? 32 : 16;
+    const bool persistent = bm && strcmp(bm, "persistent") == 0;
+    const bool march = !persistent && !(bm && strcmp(bm, "stepped") == 0);
+    const bool stepped = !persistent;
+    int tz = persistent || march ? 16 : 32;
     if (const char *f = getenv("GSIM_TILE_Z")) {
         const int v = atoi(f);
         if (v == 8 || v == 16 || v == 32) tz = v;
@@ -1775,6 +2049,41 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
         (e = cudaMemcpyAsync(ctx->members, members.data(), members.size() * sizeof(BatchMember),
                              cudaMemcpyHostToDevice, bst)))
         return fail(e, "upload");
+    MarchArgs mb{};
+    if (march) {  // the row-march plan over all members
+        std::vector<MarchMember> mm;
+        for (const BatchMember &m : members) mm.push_back({m.slice, m.shot, items[m.slice].sim});
+        std::vector<MarchSeg> segs;
+        std::vector<int> wseg;
+        const long long maxw = (long long)sms * std::max(1, march2d_warps_per_sm(any_cpml));
+        const int item = march_item_rows();
+        int nw = 0;
+        if (item) {
+            nw = plan_march_items(mm, maxw, item, segs);
+            wseg.assign(1, 0);
+        } else {
+            plan_march(mm, maxw, segs, wseg);
+            nw = (int)wseg.size() - 1;
+        }
+        if (!ctx->mctr && (e = cudaMalloc(&ctx->mctr, 2 * sizeof(unsigned)))) return fail(e, "allocation");
+        if ((e = grow(&ctx->msegs, &ctx->cap_msegs, segs.size() * sizeof(MarchSeg))) ||
+            (e = grow(&ctx->mwseg, &ctx->cap_mwseg, wseg.size() * sizeof(int)))) {
+            if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+            ctx->exec = nullptr;
+            return fail(e, "allocation");
+        }
+        if ((e = cudaMemcpyAsync(ctx->msegs, segs.data(), segs.size() * sizeof(MarchSeg), cudaMemcpyHostToDevice,
+                                 bst)) ||
+            (e = cudaMemcpyAsync(ctx->mwseg, wseg.data(), wseg.size() * sizeof(int), cudaMemcpyHostToDevice, bst)))
+            return fail(e, "upload");
+        mb.slices = static_cast<const StepArgs<float> *>(ctx->slices);
+        mb.segs = static_cast<const MarchSeg *>(ctx->msegs);
+        mb.wseg = static_cast<const int *>(ctx->mwseg);
+        mb.ctr = item ? ctx->mctr : nullptr;
+        mb.nwarps = nw;
+        mb.nitems = item ? (int)segs.size() : 0;
+        mb.tz = tz;
+    }
     if (stepped) {  // members with global tile offsets
         long long t0 = 0;
         for (BatchMember &m : members) {
@@ -1798,16 +2107,29 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
     b.flags = ctx->flags;
     const int grid = sms * std::max(1, batch_blocks_per_sm(tz, any_cpml));
     // counters reset + the persistent kernel, replayed as one graph
-    std::vector<char> key(sizeof b + 3 * sizeof(int) + sizeof(long long));
+    std::vector<char> key(sizeof b + sizeof mb + 3 * sizeof(int) + sizeof(long long));
     memcpy(key.data(), &b, sizeof b);
-    const int kk[3] = {tz, (int)any_cpml | (stepped ? 2 : 0), grid};
-    memcpy(key.data() + sizeof b, kk, sizeof kk);
-    memcpy(key.data() + sizeof b + sizeof kk, &done_total, sizeof done_total);
+    memcpy(key.data() + sizeof b, &mb, sizeof mb);
+    const int kk[3] = {tz, (int)any_cpml | (stepped ? 2 : 0) | (march ? 4 : 0), grid};
+    memcpy(key.data() + sizeof b + sizeof mb, kk, sizeof kk);
+    memcpy(key.data() + sizeof b + sizeof mb + sizeof kk, &done_total, sizeof done_total);
     if (!ctx->exec || key != ctx->key || bst == nullptr) {
         if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
         ctx->exec = nullptr;
     }
     auto body = [&](cudaStream_t st) {
+        if (march) {
+            cudaError_t r = cudaMemsetAsync(ctx->flags, 0, sizeof(unsigned), st);
+            if (r == cudaSuccess && mb.ctr) r = cudaMemsetAsync(mb.ctr, 0, 2 * sizeof(unsigned), st);
+            for (int n = 0; n < nt && r == cudaSuccess; n++) {
+                StepTime t{};
+                t.n = n;
+                t.snap_k = t.max_k = -1;
+                t.inj_row = n;
+                r = launch_march2d(mb, any_cpml, t, st, st != nullptr);
+            }
+            return r;
+        }
         if (stepped) {
             cudaError_t r = cudaMemsetAsync(ctx->flags, 0, sizeof(unsigned), st);
             for (int n = 0; n < nt && r == cudaSuccess; n++)
@@ -1960,8 +2282,17 @@ sim_status sim_create(const sim_desc *din, const void *vel, void *cuda_stream, s
     if (rc == SIM_OK && d.precision == SIM_FP32) rc = s->cuda(configure_step2d_f32(), "kernel configuration");
     if (rc == SIM_OK && d.precision == SIM_FP32 && d.ndim == 2) {
         rc = s->cuda(configure_resident2d(), "kernel configuration");
+        if (rc == SIM_OK) rc = s->cuda(configure_march2d(), "kernel configuration");
         s->rdone = static_cast<int *>(A(sizeof(int) * ms * max_tiles(s)));
         s->rtiles = static_cast<RTile *>(A(sizeof(RTile) * max_tiles(s)));
+        // row march: at most one segment start per warp plus one per (shot, strip)
+        const size_t maxw = (size_t)device_sms(s->dev) * 128;
+        s->cap_mwseg = maxw + 2;
+        s->cap_mseg = maxw + (size_t)ms * ((g.NX + kMarchW - 1) / kMarchW) * ((g.NZ + 3) / 4) + 2;
+        s->mseg = static_cast<MarchSeg *>(A(sizeof(MarchSeg) * s->cap_mseg));
+        s->mwseg = static_cast<int *>(A(sizeof(int) * s->cap_mwseg));
+        s->mslice = static_cast<StepArgs<float> *>(A(sizeof(StepArgs<float>)));
+        s->mctr = static_cast<unsigned *>(A(2 * sizeof(unsigned)));
     }
     if (rc == SIM_OK && d.ndim == 3) {
         rc = s->cuda(configure_step3d(), "kernel configuration");

@@ -178,6 +178,32 @@ cudaError_t launch_batch2d(const BatchArgs &b, int tz, bool cpml, int grid, cuda
 cudaError_t launch_multi2d(const BatchArgs &b, int tz, bool cpml, int nblocks, int n, cudaStream_t st, bool pdl);
 int batch_blocks_per_sm(int tz, bool cpml);
 
+// Row march (march2d.cu): the 2D FP32 forward step as warps that each walk
+// down the rows [z0, z1) of one 128-column strip (bx) of one member (slice,
+// shot). Two schedules: static (ctr == NULL), where wseg[w] .. wseg[w + 1]
+// are warp w's segments, and dynamic, where the warps take the nitems
+// segments in order from the step's counter ctr[n & 1] (ctr[0] zeroed before
+// the first step; each step zeroes the next step's). tz is the tile height of
+// the slices' receiver and injection lists.
+constexpr int kMarchW = 128;
+struct MarchSeg {
+    int slice, shot, bx, z0, z1;
+    int pad[3];
+};
+struct MarchArgs {
+    const StepArgs<float> *slices;
+    const MarchSeg *segs;
+    const int *wseg;
+    unsigned *ctr;
+    int nwarps;
+    int nitems;
+    int tz;
+    int pad;
+};
+cudaError_t configure_march2d();
+int march2d_warps_per_sm(bool cpml);
+cudaError_t launch_march2d(const MarchArgs &m, bool cpml, const StepTime &t, cudaStream_t st, bool pdl);
+
 // 3D launchers (fwd3d.cu). Per step: snapshot, sample, CPML psi, z-march
 // update, CPML zeta + addend, source injection.
 cudaError_t configure_step3d();

@@ -1,8 +1,11 @@
-"""sim_batch: many shots on uneven grids, stepped (one launch per step over all
-members, the default) or persistent (one dataflow launch). Results must equal
-per-handle sim_forward bit for bit in both schedules (each cell's arithmetic
-does not depend on the schedule) and match the FP64 oracle; a bounded wait of
-the persistent schedule that runs out reports SIM_ERR_TIMEOUT, not a hang."""
+"""sim_batch: many shots on uneven grids, as one row-march launch per step over
+all members (the default), one tiled-kernel launch per step ("stepped") or one
+dataflow launch ("persistent"). Results must equal per-handle sim_forward bit
+for bit (the row march on both sides; each cell's arithmetic does not depend on
+how the work is split), the two tiled schedules must equal each other bit for
+bit, the march must agree with them to FP32 rounding, and everything must
+match the FP64 oracle; a bounded wait of the persistent schedule that runs out
+reports SIM_ERR_TIMEOUT, not a hang."""
 import os
 
 import numpy as np
@@ -16,16 +19,19 @@ torch = pytest.importorskip("torch")
 
 
 @pytest.fixture(autouse=True)
-def per_step_forward():
-    # the bit-for-bit comparisons below are against the per-step kernel path,
-    # whose per-tile function the batch kernel shares
-    old = os.environ.get("GSIM_RESIDENT")
+def march_forward():
+    # the bit-for-bit comparisons below are against per-handle forwards on the
+    # row march, the kernel of the default batch schedule
+    keys = ("GSIM_RESIDENT", "GSIM_MARCH")
+    old = {k: os.environ.get(k) for k in keys}
     os.environ["GSIM_RESIDENT"] = "0"
+    os.environ["GSIM_MARCH"] = "1"
     yield
-    if old is None:
-        os.environ.pop("GSIM_RESIDENT", None)
-    else:
-        os.environ["GSIM_RESIDENT"] = old
+    for k, v in old.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
 
 
 @pytest.fixture(scope="module")
@@ -75,18 +81,26 @@ def test_batch_equals_forward_and_oracle(pkg):
         s.close()
 
 
-def test_stepped_and_persistent_schedules_agree(pkg):
+def batch_with(pkg, entries, schedule):
+    if schedule is None:
+        return [g.clone() for g in pkg.batch(entries)]
+    os.environ["GSIM_BATCH"] = schedule
+    try:
+        return [g.clone() for g in pkg.batch(entries)]
+    finally:
+        del os.environ["GSIM_BATCH"]
+
+
+def test_schedules_agree(pkg):
     slices = uneven_slices(nt=200)
     sims = sims_for(pkg, slices)
     entries = [dict(sim=s, wavelet=c["wavelet"], src=c["src"], rec=c["rec"]) for s, c in zip(sims, slices)]
-    stepped = [g.clone() for g in pkg.batch(entries)]
-    os.environ["GSIM_BATCH"] = "persistent"
-    try:
-        persistent = pkg.batch(entries)
-    finally:
-        del os.environ["GSIM_BATCH"]
-    for a, b in zip(stepped, persistent):
-        assert torch.equal(a, b)
+    march = batch_with(pkg, entries, None)
+    stepped = batch_with(pkg, entries, "stepped")
+    persistent = batch_with(pkg, entries, "persistent")
+    for a, b, c in zip(march, stepped, persistent):
+        assert torch.equal(b, c)
+        assert rel(a.cpu().numpy(), b.cpu().numpy().astype(np.float64)) <= 1e-5
     for s in sims:
         s.close()
 
