@@ -101,16 +101,28 @@ struct Lists {
         const int btz = z / tz;
         tz0 = btz * tz;
         const int tile = btz * A.ntx + S.bx, lz = z - tz0;
+        // skip the entries of the tile's earlier rows (a segment may start
+        // mid tile), 32 at a time: they form a prefix of the sorted list
         if (rec) {
             rp = A.rec_start[tile];
             re = A.rec_start[tile + 1];
-            while (rp < re && A.rec[rp].lz < lz) rp++;
+            while (rp < re) {
+                const int e = rp + (threadIdx.x & 31);
+                const unsigned b = __ballot_sync(0xffffffffu, e < re && A.rec[e].lz < lz);
+                rp += __popc(b);
+                if (b != 0xffffffffu) break;
+            }
         }
         if (inj) {
             const int it = A.inj_per_shot ? S.shot * (A.ntx * A.ntz) + tile : tile;
             gp = A.inj_start[it];
             ge = A.inj_start[it + 1];
-            while (gp < ge && (A.inj_grp[gp].cell >> 7) < lz) gp++;
+            while (gp < ge) {
+                const int e = gp + (threadIdx.x & 31);
+                const unsigned b = __ballot_sync(0xffffffffu, e < ge && (A.inj_grp[e].cell >> 7) < lz);
+                gp += __popc(b);
+                if (b != 0xffffffffu) break;
+            }
         }
     }
 };

@@ -736,10 +736,11 @@ sim_status autotune(sim_t s, int nshots) {
     const TuneKey key{s->g.NZ, s->g.NX, s->d.bc, s->d.free_surface, nshots, dev_sms};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
+        // value: tile height | 256 if the march was faster | 512 if it was timed
         auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end()) {
+        if (it != g_tune_cache.end() && (forced >= 0 || !can_march || (it->second & 512))) {
             set_tile_z(s, it->second & 0xff);
-            if (forced < 0) s->use_march = can_march && (it->second >> 8) != 0;
+            if (forced < 0) s->use_march = can_march && (it->second & 256) != 0;
             return SIM_OK;
         }
     }
@@ -783,7 +784,8 @@ sim_status autotune(sim_t s, int nshots) {
         }
     }
     bool march_best = false;
-    if (!rc && can_march && forced < 0) {  // the row march, with empty lists of the finest tiling
+    const bool march_timed = !rc && can_march && forced < 0;
+    if (march_timed) {  // the row march, with empty lists of the finest tiling
         set_tile_z(s, 8);
         std::vector<int> zeros((size_t)nshots * s->ntx * s->ntz + 1, 0);
         rc = upload(s, s->rec_start, zeros, s->cap_start, "tune lists");
@@ -820,7 +822,7 @@ sim_status autotune(sim_t s, int nshots) {
     if (forced < 0) s->use_march = march_best;
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[key] = best_tz | (march_best ? 256 : 0);
+    g_tune_cache[key] = best_tz | (march_best ? 256 : 0) | (march_timed ? 512 : 0);
     return SIM_OK;
 }
 
