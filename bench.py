@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c2x32", "c3", "c5", "c5s", "c6g", "c6w"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c2x32", "c3", "c5", "c5s", "c6g", "c6w", "model"])
     ap.add_argument("--nt", type=int, default=0, help="override nt (profiling runs only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -509,10 +509,148 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def model_recipe(nz, nx, seed):
+    """Seeded inputs of one paper-shaped 2D slice build: four deposits of six
+    beds (noisy boundaries, texture, tapers), a squish and two faults."""
+    import synth
+    rng = np.random.default_rng(seed)
+    ops = []
+    for k in range(4):
+        t, nb = nz // 5, 6
+        base = np.sort(rng.uniform(2, t - 2, nb - 1))
+        b = base[:, None, None] + 2.0 * synth.smooth(rng.standard_normal((nb - 1, 1, nx)).astype(np.float32), 3.0)
+        ops.append(("deposit", dict(t=t, bounds=np.clip(b, 0, t - 1).astype(np.float32),
+                                    vbed=rng.normal(1800.0 + 500.0 * (3 - k), 150.0, nb).astype(np.float32),
+                                    beta=1.0, a_eta=30.0, f_top=0.1, f_base=0.1,
+                                    eta=rng.standard_normal((t + 40, 1, nx)).astype(np.float32),
+                                    offsets=rng.integers(0, 40, nb), label0=10 * (k + 1))))
+    dz = synth.smooth(rng.uniform(-1, 1, (1, nx)).astype(np.float32), 40.0)
+    ops.append(("squish", dict(dz=(dz / np.abs(dz).max() * 20.0).astype(np.float32), fill=1500.0, fill_label=0)))
+    for k in range(2):
+        ops.append(("fault", dict(cz=nz * rng.uniform(0.3, 0.6), cx=nx * rng.uniform(0.2, 0.8),
+                                  dip=np.deg2rad(rng.uniform(50, 70)), radius=rng.uniform(300, 3000),
+                                  slip=rng.uniform(3, 15), direction=int(rng.choice([-1, 1])),
+                                  d_die=rng.uniform(20, 60), theta_die=np.deg2rad(40.0), fill=1500.0,
+                                  fill_label=0)))
+    return ops
+
+
+def run_model(args):
+    """Model-builder warps (App. model builder modules): one 619 x 1000 slice
+    built from a 4500 m/s half-space by four deposits, a squish and two
+    faults, all on the GPU; value = voxel updates per second of the chain."""
+    import torch
+    import paper_2605_30541_gb300 as pkg
+    from paper_2605_30541_gb300 import model
+    torch.cuda.set_device(0)
+    nz, nx = 619, 1000
+    ops = model_recipe(nz, nx, 7000)
+    # the drawn fields live on the device before the timed builds
+    dev_ops = [(kind, {k: (torch.as_tensor(a, device="cuda") if k in ("bounds", "eta", "dz") else a)
+                       for k, a in p.items()}) for kind, p in ops]
+    base = torch.full((nz, nx), 4500.0, device="cuda")
+    lab0 = torch.zeros((nz, nx), dtype=torch.int32, device="cuda")
+
+    def build():
+        v, lab = base, lab0
+        for kind, p in dev_ops:
+            if kind == "deposit":
+                v, lab = model.deposit(v, lab, p["t"], p["bounds"], p["vbed"], beta=p["beta"], a_eta=p["a_eta"],
+                                       f_top=p["f_top"], f_base=p["f_base"], eta=p["eta"], offsets=p["offsets"],
+                                       label0=p["label0"])
+            elif kind == "squish":
+                v, lab = model.squish(v, lab, p["dz"], p["fill"], p["fill_label"])
+            else:
+                v, lab = model.fault(v, lab, **p)
+        return v, lab
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        build()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(0) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            v, lab = build()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    per = sum(a.elapsed_time(b) for a, b in ev) / args.steps / 1e3
+    updates = len(ops) * nz * nx
+    # the warps alone on a 619 x 64 x 1000 volume (41 M voxels, far above L2),
+    # outputs preallocated, through the C ABI: squish for its HBM roofline
+    # (16 B per voxel: velocity and label, in and out), the 3D fault (8^3 taps)
+    ny3 = 64
+    v3 = torch.empty((nz, ny3, nx), device="cuda").uniform_(1500.0, 4500.0)
+    l3 = torch.randint(0, 9, (nz, ny3, nx), dtype=torch.int32, device="cuda")
+    vo3, lo3 = torch.empty_like(v3), torch.empty_like(l3)
+    dz3 = torch.empty((ny3, nx), device="cuda").uniform_(-12.0, 12.0)
+    f3 = pkg.abi.SimFault(cz=300.0, cy=32.0, cx=500.0, azimuth=0.6, dip=np.deg2rad(60.0), radius=800.0, slip=9.0,
+                          direction=1, pad=0, d_die=40.0, d_perp=400.0, theta_die=np.deg2rad(40.0))
+
+    def timed(fn, reps):
+        fn()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps / 1e3
+
+    t_sq = timed(lambda: pkg.sim_model_squish(nz, ny3, nx, v3, l3, dz3, 1500.0, 0, vo3, lo3), 10)
+    t_f3 = timed(lambda: pkg.sim_model_fault(nz, ny3, nx, v3, l3, f3, 1500.0, 0, vo3, lo3), 3)
+    vox3 = nz * ny3 * nx
+    peak, peak_kind = read_peaks()
+    ach = 16.0 * vox3 / t_sq / 1e9
+    cpu = None
+    if not args.no_cpu:
+        from oracle import model as om
+        import time as _t
+        cols = 100  # bounded sample: the same chain on the first 100 columns
+        v = np.full((nz, 1, cols), 4500.0)
+        lab = np.zeros((nz, 1, cols), np.int32)
+        t0 = _t.perf_counter()
+        for kind, p in ops:
+            if kind == "deposit":
+                v, lab = om.deposit(v, lab, p["t"], p["bounds"][..., :cols].astype(np.float64), p["vbed"], p["beta"],
+                                    p["a_eta"], p["f_top"], p["f_base"], p["eta"][..., :cols].astype(np.float64),
+                                    p["offsets"], p["label0"])
+            elif kind == "squish":
+                v, lab = om.squish(v, lab, p["dz"][..., :cols].astype(np.float64), p["fill"], p["fill_label"])
+            else:
+                q = {k2: v2 for k2, v2 in p.items() if k2 not in ("fill", "fill_label")}
+                q.update(cy=0.0, azimuth=np.pi / 2, d_perp=1e9)
+                v, lab = om.fault(v, lab, q, p["fill"], p["fill_label"])
+        dt = _t.perf_counter() - t0
+        cpu = {"value": len(ops) * nz * cols / dt / 1e6, "unit": "Mvoxel/s", "cores": 1, "kind": "oracle",
+               "sample": "the same chain on the first %d of %d columns (numpy FP64), %.1f s" % (cols, nx, dt)}
+    line = {"metric": "Mvoxel-updates/s (model-builder warps)", "value": updates / per / 1e6, "unit": "Mvoxel/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 coordinates)",
+            "data": "synthetic",
+            "config": {"workload": "model: one 619x1000 slice = 4 deposits (6 beds, texture, tapers) + squish + "
+                                   "2 faults, from a 4500 m/s half-space", "warps_per_slice": len(ops),
+                       "volume_619x64x1000": {"squish_us": t_sq * 1e6, "fault_us": t_f3 * 1e6,
+                                              "fault_mvoxel_s": vox3 / t_f3 / 1e6},
+                       "l2": "flushed between timed builds"},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "traffic": None, "kernel": "k_squish", "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": 16.0 * vox3, "avg_launch_us": t_sq * 1e6,
+                         "case": "619 x 64 x 1000 volume"},
+            "cpu_baseline": cpu, "clocks": clk.summary(), "gpu_launches": args.steps * len(ops)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "model":
+        run_model(args)
     elif args.workload in ("c3", "c6g"):
         run_batch(args)
     else:

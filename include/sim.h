@@ -230,6 +230,88 @@ sim_status sim_forward_noalloc(const sim_desc *d, const float *vel, const float 
 sim_status sim_wavelet_bandpass(int nt, double dt, double f0, double f_lo, double f_hi, int order, int precision,
                                 void *out, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Velocity-model builder warps: the pull-sample steps of the paper's model
+ * generator modules Squish (Alg. squish), Fault (Alg. fault) and a
+ * simplified Deposit (Alg. deposit), App. "Model builder modules". They run
+ * on the GPU so generated models feed sim_create / sim_set_model / sim_batch
+ * without leaving the device.
+ *
+ * Grids are (nz, ny, nx) row-major DEVICE arrays owned by the caller (ny = 1
+ * for a 2D slice, z the depth index): velocities FP32 (m/s), labels int32
+ * (the geologic layer of each voxel). Labels are optional, but on both sides
+ * or neither. Outputs must not overlap the inputs. The drawn random fields
+ * of the modules (fractal-noise displacements, bed thicknesses and
+ * velocities, perturbed bed boundaries, texture) are inputs.
+ *
+ * Interpolation (the paper says "sinc"; this library's reading): an 8-tap
+ * Lanczos-windowed sinc per axis (sinc(x) sinc(x/4), |x| < 4), weights
+ * normalised to sum 1, taps beyond the grid taking the edge value; labels by
+ * nearest neighbour (round half to even, clamped). A voxel whose pulled depth
+ * lies outside [0, nz) takes fill_v / fill_label (Alg. fault; Squish alike);
+ * depths down to -1e-6 count as 0. Source positions are computed in FP64,
+ * weights and sums in FP32.
+ *
+ * Calls are stream-ordered on `stream` (NULL: legacy default stream) and
+ * return after enqueue. Errors: SIM_ERR_ARG (sizes, NULL or overlapping
+ * arrays, parameters out of range), SIM_ERR_CUDA (launch failure); text from
+ * sim_last_error(NULL). */
+
+/* Alg. squish: out(z, y, x) = in(z + dz(y, x), y, x).
+ *   dz  [ny][nx] device, displacement in cells (a 2D fractal-noise field) */
+sim_status sim_model_squish(int nz, int ny, int nx, const float *v_in, const int *lab_in, const float *dz,
+                            float fill_v, int fill_label, float *v_out, int *lab_out, void *stream);
+
+/* Alg. fault: a listric normal fault as a rotation about a cylinder whose
+ * axis runs along strike. Frame (z down): dip-azimuth direction
+ * e_d = (0, cos a, sin a) in (z, y, x), strike e_s = (0, -sin a, cos a);
+ * the cylinder centre is c - (R sin dip) e_z - (R cos dip) e_d, so the fault
+ * surface (radius R) passes through c with the given dip. Each voxel is
+ * rotated about the axis by -chi d w slip/R (chi = +1 outside the cylinder,
+ * the footwall, -1 inside; w the product of cosine tapers of
+ * |r - R| / d_die, |angle - angle of c| / theta_die and |along-strike
+ * offset| / d_perp, zero where any ratio reaches 1) and pulled from
+ * 2 p - p_rotated. A 2D slice is the case a = +-pi/2 on ny = 1. */
+typedef struct {
+    double cz, cy, cx;   /* point on the fault surface, cells */
+    double azimuth;      /* a, radians */
+    double dip;          /* radians */
+    double radius;       /* R, cells (> 0; large: planar fault) */
+    double slip;         /* cells of arc along the fault */
+    int direction;       /* +1 or -1 */
+    int pad;
+    double d_die;        /* cells (> 0) */
+    double d_perp;       /* cells (> 0) */
+    double theta_die;    /* radians (> 0) */
+} sim_fault;
+sim_status sim_model_fault(int nz, int ny, int nx, const float *v_in, const int *lab_in, const sim_fault *f,
+                           float fill_v, int fill_label, float *v_out, int *lab_out, void *stream);
+
+/* Alg. deposit, simplified: a slab of t rows with nbeds beds is laid on top
+ * of the model (rows z < t; the model below is pushed down by t rows). In the
+ * slab, l = number of bed boundaries above z, S_l = the deepest of them (0 in
+ * the first bed), tau(z) = min(z / (f_top t), 1) min((t - z) / (f_base t), 1)
+ * (a zero fraction: no taper on that side), vbar = mean bed velocity, and
+ *   v = (vbar + beta z) + tau(z) [(vbed_l - vbar) + a_eta eta(z - floor(S_l) + off_l, y, x)]
+ * with the texture depth clamped to [0, nzt); label = label0 + l. The final
+ * conformance of the slab to an underlying topography is not applied. */
+typedef struct {
+    int t;               /* slab rows, 1 <= t <= nz */
+    int nbeds;           /* 1 .. 128 */
+    int nzt;             /* rows of the texture field eta */
+    int label0;
+    float beta;          /* m/s per row */
+    float a_eta;         /* m/s per unit of texture */
+    float f_top, f_base; /* taper fractions >= 0 */
+} sim_deposit;
+/*   bounds   [nbeds - 1][ny][nx] device: bed boundary depths in rows (noise
+ *            already applied); may be NULL when nbeds == 1
+ *   vbed     [nbeds] HOST bed velocities; offsets [nbeds] HOST texture offsets
+ *   eta      [nzt][ny][nx] device texture, or NULL (no texture) */
+sim_status sim_model_deposit(int nz, int ny, int nx, const float *v_in, const int *lab_in, const sim_deposit *p,
+                             const float *bounds, const float *vbed, const int *offsets, const float *eta,
+                             float *v_out, int *lab_out, void *stream);
+
 sim_status sim_sync(sim_t s);
 
 /* Layout and model facts of a live handle. */

@@ -29,8 +29,8 @@ notes):
      model (rows z < t; the model below is pushed down by t rows, labels
      likewise); bed index = number of bed boundaries H_i(y, x) below z (the
      searchsorted count); the texture is read at depth z - floor(S_l) + o_l
-     (S_l the bed's start depth, o_l its drawn offset), clamped to the
-     field; a zero taper fraction means no taper on that side; the final
+     (S_l the bed's start depth: the deepest boundary above z, 0 in the
+     first bed; o_l its drawn offset), clamped to the field; a zero taper fraction means no taper on that side; the final
      conformance to an underlying topography is not applied.
 """
 import numpy as np
@@ -167,7 +167,7 @@ def deposit(v, lab, t, bounds, vbed, beta, a_eta, f_top, f_base, eta, offsets, l
             out_l[z] = lab[z - t]
             continue
         ell = np.sum(bounds < z, axis=0)  # bed of each column
-        start = np.where(ell > 0, np.take_along_axis(bounds, np.maximum(ell - 1, 0)[None], 0)[0], 0.0)
+        start = np.max(np.where(bounds < z, bounds, 0.0), axis=0) if len(bounds) else np.zeros((ny, nx))
         top = min(z / (f_top * t), 1.0) if f_top > 0 else 1.0
         base = min((t - z) / (f_base * t), 1.0) if f_base > 0 else 1.0
         tau = top * base

@@ -16,7 +16,8 @@ from .abi import SIM_BC, SIM_FP32, SIM_FP64, SimBatchItem, SimDesc, SimInfo
 
 __all__ = ["SimError", "make_desc", "sim_plan", "sim_create", "sim_set_model", "sim_forward",
            "sim_adjoint", "sim_batch", "sim_sync", "sim_get_info", "sim_last_error", "sim_destroy",
-           "Simulator", "batch", "sim_forward_noalloc", "sim_wavelet_bandpass", "bandpass_ricker"]
+           "Simulator", "batch", "sim_forward_noalloc", "sim_wavelet_bandpass", "bandpass_ricker",
+           "sim_model_squish", "sim_model_fault", "sim_model_deposit"]
 
 
 class SimError(RuntimeError):
@@ -174,6 +175,28 @@ def bandpass_ricker(nt, dt, f0, f_lo, f_hi, order=4, dtype="float32", device="cu
     out = torch.empty(int(nt), dtype=tdt, device=device)
     sim_wavelet_bandpass(nt, dt, f0, f_lo, f_hi, order, SIM_FP64 if tdt == torch.float64 else SIM_FP32, out)
     return out
+
+
+def sim_model_squish(nz, ny, nx, v_in, lab_in, dz, fill_v, fill_label, v_out, lab_out, stream=None):
+    """Squish warp on device grids (see include/sim.h)."""
+    _check(abi.load().sim_model_squish(int(nz), int(ny), int(nx), _ptr(v_in), _ptr(lab_in), _ptr(dz),
+                                       float(fill_v), int(fill_label), _ptr(v_out), _ptr(lab_out), _stream(stream)))
+
+
+def sim_model_fault(nz, ny, nx, v_in, lab_in, fault, fill_v, fill_label, v_out, lab_out, stream=None):
+    """Fault warp on device grids; fault: abi.SimFault (see include/sim.h)."""
+    _check(abi.load().sim_model_fault(int(nz), int(ny), int(nx), _ptr(v_in), _ptr(lab_in), ctypes.byref(fault),
+                                      float(fill_v), int(fill_label), _ptr(v_out), _ptr(lab_out), _stream(stream)))
+
+
+def sim_model_deposit(nz, ny, nx, v_in, lab_in, params, bounds, vbed, offsets, eta, v_out, lab_out, stream=None):
+    """Deposit slab on device grids; params: abi.SimDeposit, vbed / offsets
+    host arrays (see include/sim.h)."""
+    vb = np.ascontiguousarray(vbed, np.float32)
+    of = np.ascontiguousarray(offsets, np.int32)
+    _check(abi.load().sim_model_deposit(int(nz), int(ny), int(nx), _ptr(v_in), _ptr(lab_in), ctypes.byref(params),
+                                        _ptr(bounds), _ptr(vb), _ptr(of), _ptr(eta), _ptr(v_out), _ptr(lab_out),
+                                        _stream(stream)))
 
 
 def sim_sync(handle):

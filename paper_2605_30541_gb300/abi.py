@@ -55,9 +55,26 @@ class SimBatchItem(ctypes.Structure):
     ]
 
 
+class SimFault(ctypes.Structure):
+    _fields_ = [
+        ("cz", ctypes.c_double), ("cy", ctypes.c_double), ("cx", ctypes.c_double),
+        ("azimuth", ctypes.c_double), ("dip", ctypes.c_double), ("radius", ctypes.c_double),
+        ("slip", ctypes.c_double), ("direction", ctypes.c_int), ("pad", ctypes.c_int),
+        ("d_die", ctypes.c_double), ("d_perp", ctypes.c_double), ("theta_die", ctypes.c_double),
+    ]
+
+
+class SimDeposit(ctypes.Structure):
+    _fields_ = [
+        ("t", ctypes.c_int), ("nbeds", ctypes.c_int), ("nzt", ctypes.c_int), ("label0", ctypes.c_int),
+        ("beta", ctypes.c_float), ("a_eta", ctypes.c_float), ("f_top", ctypes.c_float), ("f_base", ctypes.c_float),
+    ]
+
+
 _VP = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
+_F = ctypes.c_float
 _PROTOS = {
     "sim_desc_init": (None, [ctypes.POINTER(SimDesc)]),
     "sim_plan": (_I, [ctypes.POINTER(SimDesc), _D, _D, ctypes.POINTER(SimInfo)]),
@@ -68,6 +85,10 @@ _PROTOS = {
     "sim_batch": (_I, [_I, ctypes.POINTER(SimBatchItem), _VP]),
     "sim_forward_noalloc": (_I, [ctypes.POINTER(SimDesc), _VP, _VP, _VP, _I, _VP, _VP, _VP]),
     "sim_wavelet_bandpass": (_I, [_I, _D, _D, _D, _D, _I, _I, _VP, _VP]),
+    "sim_model_squish": (_I, [_I, _I, _I, _VP, _VP, _VP, _F, _I, _VP, _VP, _VP]),
+    "sim_model_fault": (_I, [_I, _I, _I, _VP, _VP, ctypes.POINTER(SimFault), _F, _I, _VP, _VP, _VP]),
+    "sim_model_deposit": (_I, [_I, _I, _I, _VP, _VP, ctypes.POINTER(SimDeposit), _VP, _VP, _VP, _VP, _VP, _VP,
+                               _VP]),
     "sim_sync": (_I, [_VP]),
     "sim_get_info": (_I, [_VP, ctypes.POINTER(SimInfo)]),
     "sim_last_error": (ctypes.c_char_p, [_VP]),
