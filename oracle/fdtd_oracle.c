@@ -420,7 +420,7 @@ static int coord_of(int ax, int z, int y, int x) { return ax == 0 ? z : (ax == 1
  * free surface R4). s is the per-cell source density at step n (or NULL). */
 static void step(const or_params *P, const grid_t *G, const real_t *c,
                  const real_t *a, cpml_t *C, const real_t *s, const real_t *pprev,
-                 const real_t *pcur, real_t *pnext) {
+                 const real_t *pcur, real_t *pnext, real_t *cadd) {
     /* CPML pass 1: psi^n = b psi^{n-1} + a D1 p^n on every cell */
     for (int ax = 0; ax < 3; ax++) {
         if (!C->on[ax]) continue;
@@ -440,7 +440,7 @@ static void step(const or_params *P, const grid_t *G, const real_t *c,
         for (int y = 0; y < G->NY; y++)
             for (int x = 0; x < G->NX; x++) {
                 long i = IDX(G, z, y, x);
-                real_t rhs = 0;
+                real_t rhs = 0, add = 0;
                 for (int ax = 0; ax < 3; ax++) {
                     if (!axis_active(P, ax)) continue;
                     real_t d2 = d2_axis(P, G, pcur, ax, z, y, x);
@@ -450,8 +450,10 @@ static void step(const or_params *P, const grid_t *G, const real_t *c,
                         real_t dpsi = d1_axis(P, G, C->psi[ax], ax, z, y, x);
                         C->zeta[ax][i] = C->cb[ax][k] * C->zeta[ax][i] + C->ca[ax][k] * (d2 + dpsi);
                         rhs += dpsi + C->zeta[ax][i];
+                        add += dpsi + C->zeta[ax][i];
                     }
                 }
+                if (cadd) cadd[i] = add;
                 if (s) rhs += s[i];
                 pnext[i] = (2.0 * pcur[i] - (1.0 - a[i]) * pprev[i] + c[i] * rhs) / (1.0 + a[i]);
             }
@@ -496,7 +498,7 @@ int oracle_forward(const or_params *P, const real_t *vel, const double *wavelet,
         }
         if (s)
             for (int j = 0; j < geo.ncell_src; j++) s[geo.src_cell[j]] = wavelet[n] * geo.src_w[j] / hd;
-        step(P, &G, c, a, &C, s, pprev, pcur, pnext);
+        step(P, &G, c, a, &C, s, pprev, pcur, pnext, NULL);
         if (s)
             for (int j = 0; j < geo.ncell_src; j++) s[geo.src_cell[j]] = 0;
         real_t *t = pprev;
@@ -554,6 +556,38 @@ static void lap_transpose(const or_params *P, const grid_t *G, const real_t *f,
             }
 }
 
+/* out += D1^T f and out += D2^T f along one axis: the scatters that transpose
+ * d1_axis and d2_axis term by term (ghost rules through put()). */
+static void d1_transpose_add(const or_params *P, const grid_t *G, const real_t *f, int ax,
+                             real_t *out) {
+    for (int z = 0; z < G->NZ; z++)
+        for (int y = 0; y < G->NY; y++)
+            for (int x = 0; x < G->NX; x++) {
+                real_t v = f[IDX(G, z, y, x)] / P->h;
+                for (int m = 1; m <= 4; m++) {
+                    int dz, dy, dx;
+                    axis_step(ax, m, &dz, &dy, &dx);
+                    put(P, G, out, z + dz, y + dy, x + dx, D1W[m] * v);
+                    put(P, G, out, z - dz, y - dy, x - dx, -D1W[m] * v);
+                }
+            }
+}
+static void d2_transpose_add(const or_params *P, const grid_t *G, const real_t *f, int ax,
+                             real_t *out) {
+    for (int z = 0; z < G->NZ; z++)
+        for (int y = 0; y < G->NY; y++)
+            for (int x = 0; x < G->NX; x++) {
+                real_t v = f[IDX(G, z, y, x)] / (P->h * P->h);
+                put(P, G, out, z, y, x, D2W[0] * v);
+                for (int m = 1; m <= 4; m++) {
+                    int dz, dy, dx;
+                    axis_step(ax, m, &dz, &dy, &dx);
+                    put(P, G, out, z + dz, y + dy, x + dx, D2W[m] * v);
+                    put(P, G, out, z - dz, y - dy, x - dx, D2W[m] * v);
+                }
+            }
+}
+
 int oracle_apply_laplacian(const or_params *P, const real_t *f, real_t *out) {
     grid_t G;
     if (make_grid(P, &G)) return -1;
@@ -601,7 +635,17 @@ int oracle_coefficients(const or_params *P, const real_t *vel, real_t *c,
  * A free-surface row carries no unknown (p = 0 there), so its multiplier is 0.
  * dJ/dw^n = sum_i lambda_i^{n+1} c_i weight_i / h^d gives the wavelet gradient.
  * All forward states are stored (no checkpointing: this is the plain version).
- * CPML is not differentiated here (returns -4).
+ *
+ * CPML (reading R3) adds, per absorbing axis, the constraints
+ *   Psi^n  = psi^n  - b psi^{n-1}  - a D1 p^n
+ *   Zeta^n = zeta^n - b zeta^{n-1} - a (D2 p^n + D1 psi^n)
+ * and the term D1 psi^n + zeta^n to (L p^n) in F^n. With multipliers mu^k, nu^k
+ * (zero for k >= nt), stationarity in zeta^k, psi^k and p^k gives
+ *   nu^k = b nu^{k+1} + c lambda^{k+1}
+ *   mu^k = b mu^{k+1} + D1^T (c lambda^{k+1} + a nu^k)
+ *   and D1^T (a mu^k) + D2^T (a nu^k) added to the right side of lambda^k,
+ * and dF/dv gains -2 v dt^2 (D1 psi^n + zeta^n). The CPML coefficients are
+ * constants of the map (taken at cpml_vmax, else at the model's maximum).
  */
 int oracle_gradient(const or_params *P, const real_t *vel, const double *wavelet,
                     const double *src, int nrec, const double *rec,
@@ -609,7 +653,6 @@ int oracle_gradient(const or_params *P, const real_t *vel, const double *wavelet
                     real_t *grad_wavelet, real_t *gather) {
     grid_t G;
     if (make_grid(P, &G) || !vel || !wavelet || !src || nrec < 1 || !rec || !d_obs) return -1;
-    if (P->bc == 1) return -4;
     long nc = G.ncell;
     int nt = P->nt;
     int rc = 0;
@@ -624,13 +667,33 @@ int oracle_gradient(const or_params *P, const real_t *vel, const double *wavelet
     real_t *lp = calloc(nc, sizeof(real_t)), *rt = calloc(nc, sizeof(real_t));
     real_t *gpad = calloc(nc, sizeof(real_t));
     real_t *pm1 = calloc(nc, sizeof(real_t));
+    real_t *tadd = NULL, *nu[3] = {NULL, NULL, NULL}, *mu[3] = {NULL, NULL, NULL}, *tmp = NULL;
     cpml_t C;
     memset(&C, 0, sizeof(C));
     geometry_t geo;
+    memset(&geo, 0, sizeof(geo));
     if (!c || !a || !eta || !states || !s || !g || !lam[0] || !lam[1] || !lam[2] ||
         !work || !lt || !lp || !rt || !gpad || !pm1) {
         rc = -3;
         goto out_nogeo;
+    }
+    if ((rc = cpml_init(P, &G, vel, &C))) goto out_nogeo;
+    if (P->bc == 1) {
+        tadd = calloc((size_t)nt * nc, sizeof(real_t));
+        tmp = calloc(nc, sizeof(real_t));
+        if (!tadd || !tmp) {
+            rc = -3;
+            goto out_nogeo;
+        }
+        for (int ax = 0; ax < 3; ax++) {
+            if (!C.on[ax]) continue;
+            nu[ax] = calloc(nc, sizeof(real_t));
+            mu[ax] = calloc(nc, sizeof(real_t));
+            if (!nu[ax] || !mu[ax]) {
+                rc = -3;
+                goto out_nogeo;
+            }
+        }
     }
     if ((rc = build_geometry(P, &G, src, nrec, rec, &geo))) goto out;
     build_coefficients(P, &G, vel, c, a, eta);
@@ -642,7 +705,7 @@ int oracle_gradient(const or_params *P, const real_t *vel, const double *wavelet
         const real_t *pprev = n > 0 ? states + (size_t)(n - 1) * nc : pm1;
         for (int r = 0; r < nrec; r++) g[(size_t)n * nrec + r] = sample(&geo, r, pcur);
         for (int j = 0; j < geo.ncell_src; j++) s[geo.src_cell[j]] = wavelet[n] * geo.src_w[j] / hd;
-        step(P, &G, c, a, &C, s, pprev, pcur, states + (size_t)(n + 1) * nc);
+        step(P, &G, c, a, &C, s, pprev, pcur, states + (size_t)(n + 1) * nc, tadd ? tadd + (size_t)n * nc : NULL);
         for (int j = 0; j < geo.ncell_src; j++) s[geo.src_cell[j]] = 0;
     }
     if (gather) memcpy(gather, g, (size_t)nt * nrec * sizeof(real_t));
@@ -660,6 +723,44 @@ int oracle_gradient(const or_params *P, const real_t *vel, const double *wavelet
     for (int k = nt; k >= 1; k--) {
         for (long i = 0; i < nc; i++) work[i] = c[i] * l1[i];
         lap_transpose(P, &G, work, lt);
+        /* CPML multipliers of step k (zero for k = nt) and their terms in lambda^k */
+        if (tadd && k <= nt - 1)
+            for (int ax = 0; ax < 3; ax++) {
+                if (!C.on[ax]) continue;
+                for (int z = 0; z < G.NZ; z++)
+                    for (int y = 0; y < G.NY; y++)
+                        for (int x = 0; x < G.NX; x++) {
+                            long i = IDX(&G, z, y, x);
+                            int q = coord_of(ax, z, y, x);
+                            nu[ax][i] = C.cb[ax][q] * nu[ax][i] + work[i];
+                            tmp[i] = work[i] + C.ca[ax][q] * nu[ax][i];
+                        }
+                memset(rt, 0, nc * sizeof(real_t));
+                d1_transpose_add(P, &G, tmp, ax, rt);
+                for (int z = 0; z < G.NZ; z++)
+                    for (int y = 0; y < G.NY; y++)
+                        for (int x = 0; x < G.NX; x++) {
+                            long i = IDX(&G, z, y, x);
+                            int q = coord_of(ax, z, y, x);
+                            mu[ax][i] = C.cb[ax][q] * mu[ax][i] + rt[i];
+                        }
+                for (int z = 0; z < G.NZ; z++)
+                    for (int y = 0; y < G.NY; y++)
+                        for (int x = 0; x < G.NX; x++) {
+                            long i = IDX(&G, z, y, x);
+                            int q = coord_of(ax, z, y, x);
+                            tmp[i] = C.ca[ax][q] * mu[ax][i];
+                        }
+                d1_transpose_add(P, &G, tmp, ax, lt);
+                for (int z = 0; z < G.NZ; z++)
+                    for (int y = 0; y < G.NY; y++)
+                        for (int x = 0; x < G.NX; x++) {
+                            long i = IDX(&G, z, y, x);
+                            int q = coord_of(ax, z, y, x);
+                            tmp[i] = C.ca[ax][q] * nu[ax][i];
+                        }
+                d2_transpose_add(P, &G, tmp, ax, lt);
+            }
         memset(rt, 0, nc * sizeof(real_t));
         if (k <= nt - 1)
             for (int r = 0; r < nrec; r++)
@@ -678,6 +779,8 @@ int oracle_gradient(const or_params *P, const real_t *vel, const double *wavelet
         const real_t *pnm1 = n > 0 ? states + (size_t)(n - 1) * nc : pm1;
         oracle_apply_laplacian(P, pn, lp);
         for (int j = 0; j < geo.ncell_src; j++) lp[geo.src_cell[j]] += wavelet[n] * geo.src_w[j] / hd;
+        if (tadd)
+            for (long i = 0; i < nc; i++) lp[i] += tadd[(size_t)n * nc + i];
         for (int z = 0; z < G.NZ; z++) {
             if (P->free_surface && z == 0) continue;
             for (int y = 0; y < G.NY; y++)
@@ -732,5 +835,12 @@ out_nogeo:
     free(rt);
     free(gpad);
     free(pm1);
+    free(tadd);
+    free(tmp);
+    for (int ax = 0; ax < 3; ax++) {
+        free(nu[ax]);
+        free(mu[ax]);
+    }
+    cpml_free(&C);
     return rc;
 }

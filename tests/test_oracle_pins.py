@@ -359,6 +359,37 @@ def test_gradient_matches_complex_step(fs):
         assert abs(cs - out["grad"][iz, ix]) <= 1e-9 * abs(out["grad"]).max(), (iz, ix, cs, out["grad"][iz, ix])
 
 
+@pytest.mark.parametrize("fs", [0, 1])
+def test_cpml_gradient_matches_complex_step(fs):
+    # the exact adjoint of the CPML recursions (psi, zeta multipliers); the
+    # CPML coefficients are constants of the map (cpml_vmax fixed)
+    cfg, vel, w, src, rec, d = _c4_small(bc="cpml", fs=fs, nt=250)
+    cfg["cpml_vmax"] = float(vel.max())
+    out = oracle.gradient(cfg, vel, w, src, rec, d)
+    rng = np.random.default_rng(11)
+    cells = [(0, 0), (cfg["nz"] - 1, cfg["nx"] - 1), (cfg["nz"] - 1, 3), (2, cfg["nx"] - 2)] + \
+        [tuple(rng.integers(0, s) for s in vel.shape) for _ in range(3)]
+    eps = 1e-30
+    for (iz, ix) in cells:
+        vc = vel.astype(np.complex128)
+        vc[iz, ix] += 1j * eps * vel[iz, ix]
+        J = oracle.gradient(cfg, vc, w, src, rec, d, complex_=True)["misfit"]
+        cs = J.imag / (eps * vel[iz, ix])
+        assert abs(cs - out["grad"][iz, ix]) <= 1e-9 * abs(out["grad"]).max(), (iz, ix, cs, out["grad"][iz, ix])
+
+
+@pytest.mark.parametrize("fs", [0, 1])
+def test_cpml_dot_product_source_to_gather(fs):
+    cfg, vel, _, src, rec, _ = _c4_small(bc="cpml", fs=fs, nt=200)
+    rng = np.random.default_rng(13)
+    x = rng.standard_normal(cfg["nt"])
+    y = rng.standard_normal((cfg["nt"], len(rec)))
+    Ax = oracle.forward(cfg, vel, x, src=src, rec=rec)["gather"]
+    ATy = oracle.gradient(cfg, vel, np.zeros(cfg["nt"]), src, rec, -y)["grad_wavelet"]
+    lhs, rhs = np.vdot(Ax, y), np.vdot(x, ATy)
+    assert abs(lhs - rhs) / (np.linalg.norm(Ax) * np.linalg.norm(y)) < 1e-12
+
+
 def test_gradient_matches_central_differences():
     cfg, vel, w, src, rec, d = _c4_small(nt=300)
     g = oracle.gradient(cfg, vel, w, src, rec, d)["grad"]
