@@ -363,7 +363,7 @@ def gradient_timing(reps=2):
         out[name] = (e0.elapsed_time(e1) / 1e3 / reps / ns, g)
     sim.close()
     g16, g32 = out["batched_fp16"][1], out["one_shot_fp32"][1]
-    return {"workload": "c4: 201x201 + 20-cell sponge, 16 shots, nt=4000, sqrt(nt) checkpoints",
+    return {"workload": "c4: 201x201 + 20-cell CPML on every side, 16 shots, nt=4000, sqrt(nt) checkpoints",
             "s_per_shot_batched_fp16": out["batched_fp16"][0], "s_per_shot_one_shot_fp32": out["one_shot_fp32"][0],
             "speedup": out["one_shot_fp32"][0] / out["batched_fp16"][0],
             "rel_l2_fp16_vs_fp32": float(torch.linalg.norm(g16 - g32) / torch.linalg.norm(g32)),

@@ -356,8 +356,9 @@ __device__ __forceinline__ void tile_step(const StepArgs<float> &A, const StepTi
         float v[12];
         unpack3(ld4(S + (rb + j) * SW + c0 - 4), zw[j + 4], ld4(S + (rb + j) * SW + c0 + 4), v);
         float res[4], qk[4];
-        float4 inj4 = make_float4(0, 0, 0, 0);
+        float4 inj4 = make_float4(0, 0, 0, 0), ext4 = make_float4(0, 0, 0, 0);
         if (has_inj) inj4 = ld4(INJ + lz * TX + 4 * lane);
+        if (MODE == kModeAdjoint && A.cext) ext4 = ld4(A.cext + sh + org + o);
         const float ez = spg ? A.E[0][gz] : 0.f;
 #pragma unroll
         for (int k = 0; k < 4; k++) {
@@ -369,6 +370,7 @@ __device__ __forceinline__ void tile_step(const StepArgs<float> &A, const StepTi
                               float(kC4) * (lane_of(zw[j + 8], k) + lane_of(zw[j], k));
             float rhs = d2z + d2x;
             if (cpx || cpz) rhs += lane_of(cadd[j], k);
+            if (MODE == kModeAdjoint && A.cext) rhs += lane_of(ext4, k);
             if (has_inj) rhs += A.src_scale * lane_of(inj4, k);
             const float chv = lane_of(ch4[j], k), pp = lane_of(pp4[j], k);
             float out, es = 0.f;

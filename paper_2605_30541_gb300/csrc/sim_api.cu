@@ -273,6 +273,11 @@ struct sim_s {
     bool adj_ready = false;
     int seg = 0, nseg = 0;
     void *ubuf = nullptr, *Gbuf = nullptr, *qbuf = nullptr, *ckpt = nullptr, *res = nullptr, *dobs = nullptr;
+    // 2D FP32 CPML gradient: multipliers nu [z, x][parity], mu [z, x], the
+    // adjoint Laplacian term, and checkpoints of (psi_z, zeta_z, psi_x, zeta_x)
+    float *cnu[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}}, *cmu[2] = {nullptr, nullptr}, *cext = nullptr;
+    void *ckcpml = nullptr;
+    float *ckcpml_scale = nullptr;
     float *qscale = nullptr, *ckscale = nullptr;
     double *acc = nullptr, *mpart = nullptr;
     void *gradst = nullptr;
@@ -1433,6 +1438,18 @@ sim_status ensure_adjoint(sim_t s) {
     auto A = [&](size_t n) { return rc == SIM_OK ? s->alloc(n, &rc) : nullptr; };
     s->ubuf = A(2 * (size_t)ms * g.fstride * s->esz);
     s->Gbuf = A((size_t)ms * g.fstride * s->esz);
+    if (d.bc == SIM_BC_CPML && g.ndim == 2 && d.precision == SIM_FP32) {
+        const size_t fb = (size_t)ms * g.fstride * sizeof(float);
+        for (int k = 0; k < 2; k++) {
+            s->cnu[k][0] = static_cast<float *>(A(fb));
+            s->cnu[k][1] = static_cast<float *>(A(fb));
+            s->cmu[k] = static_cast<float *>(A(fb));
+        }
+        s->cext = static_cast<float *>(A(fb));
+        const size_t ck_t = (size_t)((g.NX + kTileX2 - 1) / kTileX2) * ((g.NZ * g.NY + kTileZ2 - 1) / kTileZ2);
+        s->ckcpml = A((size_t)s->nseg * 4 * ms * ncomp * sizeof(float));
+        s->ckcpml_scale = static_cast<float *>(A((size_t)s->nseg * 4 * ms * ck_t * sizeof(float)));
+    }
     s->qbuf = A((size_t)s->seg * ms * g.fstride * s->esz);
     s->qscale = static_cast<float *>(A((size_t)s->seg * ms * ntiles * sizeof(float)));
     s->ckpt = A((size_t)s->nseg * 2 * ms * ncomp * s->esz);
@@ -1663,7 +1680,8 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
     const sim_desc &d = s->d;
     const Geom &g = s->g;
     if (g.ndim == 3 && d.precision != SIM_FP32) return s->fail(SIM_ERR_UNSUPPORTED, "the 3D path runs in FP32");
-    if (d.bc == SIM_BC_CPML) return s->fail(SIM_ERR_UNSUPPORTED, "the adjoint supports sponge or no absorption");
+    if (d.bc == SIM_BC_CPML && (g.ndim == 3 || d.precision != SIM_FP32))
+        return s->fail(SIM_ERR_UNSUPPORTED, "the CPML adjoint runs on 2D FP32 handles");
     if (ckpt_fp16 && d.precision != SIM_FP32) return s->fail(SIM_ERR_ARG, "FP16 checkpoints need an FP32 handle");
     if (nrec < 1) return s->fail(SIM_ERR_ARG, "the misfit needs receivers");
     if (!d_obs || !wavelet || !grad_v) return s->fail(SIM_ERR_ARG, "d_obs, wavelet and grad_v are required");
@@ -1766,6 +1784,36 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
     adj.src_scale = T(d.h * d.h);
     adj.q_fp16 = ckpt_fp16;
     adj.G = static_cast<T *>(s->Gbuf);
+    // CPML: the sweep runs the plain update of u plus the transposed CPML
+    // terms (cpml_adj.cu) it receives through cext; the forward CPML state
+    // of every segment start joins the checkpoints
+    const bool cpml = d.bc == SIM_BC_CPML;
+    if (cpml) {
+        adj.bc = SIM_BC_NONE;
+        adj.cext = reinterpret_cast<const T *>(s->cext);
+    }
+    const int ckcx = ckx, ckcz = ckz;
+    auto ckc_ptr = [&](int k, int j) {
+        return static_cast<char *>(s->ckcpml) + ((size_t)k * 4 + j) * ck_state * (ckpt_fp16 ? 2 : sizeof(T));
+    };
+    auto ckc_scale = [&](int k, int j) { return s->ckcpml_scale + ((size_t)k * 4 + j) * ck_tiles; };
+    // the forward CPML state entering step n: psi^{n-1} in the buffer of parity
+    // (n + 1) & 1, zeta^{n-1}; j = 0..3: psi_z, zeta_z, psi_x, zeta_x
+    auto cpml_field = [&](int n, int j) -> T * {
+        const int ax = j < 2 ? 0 : 2;
+        return static_cast<T *>(j % 2 == 0 ? s->psi[ax][(n + 1) & 1] : s->zeta[ax]);
+    };
+    auto cpml_ckpt = [&](int n, int k, bool store, cudaStream_t st) {
+        cudaError_t e = cudaSuccess;
+        for (int j = 0; j < 4 && e == cudaSuccess; j++) {
+            if (!s->psi[j < 2 ? 0 : 2][0]) continue;
+            e = store ? launch_store_state<T>(g, cpml_field(n, j), ckc_ptr(k, j), ckc_scale(k, j), ckpt_fp16, nshots,
+                                              ncomp, ckcx, ckcz, st)
+                      : launch_load_state<T>(g, cpml_field(n, j), ckc_ptr(k, j), ckc_scale(k, j), ckpt_fp16, nshots,
+                                             ncomp, ckcx, ckcz, st);
+        }
+        return e;
+    };
     const size_t qslot_bytes = (size_t)ms * g.fstride * (ckpt_fp16 ? 2 : sizeof(T));
     const size_t ub = (size_t)g.fstride * s->esz * nshots;
     // graph key: everything the captured launches depend on beyond handle buffers
@@ -1781,6 +1829,7 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
                     if (e == cudaSuccess)
                         e = launch_store_state<T>(g, a.pbuf[(n + 1) & 1], ck_ptr(k, 0), ck_scale(k, 0), ckpt_fp16,
                                                   nshots, ncomp, ckx, ckz, st);
+                    if (e == cudaSuccess && cpml) e = cpml_ckpt(n, k, true, st);
                 }
                 if (e == cudaSuccess) e = launch_step<T>(s, a, n, nshots, kModeForward, st);
             }
@@ -1793,6 +1842,15 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
             if (e == cudaSuccess)
                 e = cudaMemsetAsync(static_cast<char *>(s->ubuf) + (size_t)g.fstride * s->esz * ms, 0, ub, st);
             if (e == cudaSuccess) e = cudaMemsetAsync(s->Gbuf, 0, (size_t)nshots * g.fstride * s->esz, st);
+            if (cpml) {
+                const size_t fb = (size_t)nshots * g.fstride * sizeof(float);
+                for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+                    e = cudaMemsetAsync(s->cnu[k][0], 0, fb, st);
+                    if (e == cudaSuccess) e = cudaMemsetAsync(s->cnu[k][1], 0, fb, st);
+                    if (e == cudaSuccess) e = cudaMemsetAsync(s->cmu[k], 0, fb, st);
+                }
+                if (e == cudaSuccess) e = cudaMemsetAsync(s->cext, 0, fb, st);
+            }
             for (int sgi = s->nseg - 1; sgi >= 0 && e == cudaSuccess; sgi--) {
                 const int n0 = sgi * L, n1 = std::min(n0 + L, d.nt);
                 e = launch_load_state<T>(g, a.pbuf[n0 & 1], ck_ptr(sgi, 1), ck_scale(sgi, 1), ckpt_fp16, nshots,
@@ -1800,6 +1858,7 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
                 if (e == cudaSuccess)
                     e = launch_load_state<T>(g, a.pbuf[(n0 + 1) & 1], ck_ptr(sgi, 0), ck_scale(sgi, 0), ckpt_fp16,
                                              nshots, ncomp, ckx, ckz, st);
+                if (e == cudaSuccess && cpml) e = cpml_ckpt(n0, sgi, false, st);
                 for (int n = n0; n < n1 && e == cudaSuccess; n++) {
                     void *slot = static_cast<char *>(s->qbuf) + (size_t)(n - n0) * qslot_bytes;
                     float *scl = s->qscale + (size_t)(n - n0) * q_tiles;
@@ -1808,7 +1867,18 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
                 for (int k = n1; k >= n0 + 1 && e == cudaSuccess; k--) {
                     void *slot = static_cast<char *>(s->qbuf) + (size_t)(k - 1 - n0) * qslot_bytes;
                     float *scl = s->qscale + (size_t)(k - 1 - n0) * q_tiles;
-                    e = launch_step<T>(s, adj, d.nt - k, nshots, kModeAdjoint, st, slot, scl);
+                    if (cpml && k <= d.nt - 1) {  // nu^k, mu^k from u^{k+1}, then their term in u^k
+                        CpmlAdjArgs ca{};
+                        ca.u = reinterpret_cast<const float *>(adj.pbuf[(d.nt - k) & 1]);
+                        for (int q = 0; q < 2; q++) {
+                            ca.nu[q][0] = s->cnu[q][0];
+                            ca.nu[q][1] = s->cnu[q][1];
+                            ca.mu[q] = s->cmu[q];
+                        }
+                        ca.ext = s->cext;
+                        e = launch_cpml_adjoint(reinterpret_cast<const StepArgs<float> &>(a), ca, k & 1, nshots, st);
+                    }
+                    if (e == cudaSuccess) e = launch_step<T>(s, adj, d.nt - k, nshots, kModeAdjoint, st, slot, scl);
                 }
             }
             // 4. gradient: FP64 sum over shots and replicated cells

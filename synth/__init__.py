@@ -207,10 +207,12 @@ def config_c3(nt=4000, nslices=16):
     return slices
 
 
-def config_c4(nt=4000, nshots=16, bc="sponge", nb=20):
-    """FWI gradient: 201 x 201 procedural model (seed 4000), starting model =
-    true model smoothed with a 250 m (25-cell) Gaussian; 16 shots equally
-    spaced at 20 m depth; 201 receivers at 20 m depth; Ricker 10 Hz."""
+def config_c4(nt=4000, nshots=16, bc="cpml", nb=20):
+    """FWI gradient on the config-1 slice geometry (201 x 201, 20-cell CPML on
+    every side, no free surface) filled by the procedural model (seed 4000);
+    starting model = true model smoothed with a 250 m (25-cell) Gaussian; 16
+    shots equally spaced at 20 m depth; 201 receivers at 20 m depth; Ricker
+    10 Hz."""
     p = _problem(name="c4", nz=201, nx=201, h=10.0, dt=1e-3, nt=nt, bc=bc,
                  nb=[nb, nb, 0, 0, nb, nb], free_surface=0, f_ref=10.0)
     p["vel_true"] = procedural_2d(201, 201, 10.0, 4000)

@@ -176,13 +176,33 @@ def test_gradient_accumulates(pkg):
     sim.close()
 
 
-def test_cpml_adjoint_is_reported_unsupported(pkg):
+@pytest.mark.parametrize("fs", [0, 1])
+def test_cpml_gradient_fp32_matches_oracle(pkg, fs):
+    # the exact transpose of the CPML recursions, FP32 storage
+    cfg, vt, v0, w, src, rec = small_case(fs=fs, bc="cpml")
+    d = observed(cfg, vt, w, src, rec)
+    ref, Jref = oracle_grad(cfg, v0, w, src, rec, d)
+    g, J = gpu_grad(pkg, cfg, v0, w, src, rec, d)
+    assert abs(J - Jref) <= 1e-4 * Jref
+    assert rel(g, ref) <= 1e-4
+
+
+def test_cpml_gradient_fp16_checkpoints_within_1e2(pkg):
+    cfg, vt, v0, w, src, rec = small_case(nt=700, bc="cpml")
+    d = observed(cfg, vt, w, src, rec)
+    ref, _ = oracle_grad(cfg, v0, w, src, rec, d)
+    g16, _ = gpu_grad(pkg, cfg, v0, w, src, rec, d, fp16=1)
+    assert rel(g16, ref) <= 1e-2
+
+
+def test_cpml_adjoint_fp64_is_reported_unsupported(pkg):
     c = synth.config_c1(nt=50)
-    sim = pkg.Simulator(c, c["vel"], max_rec=3)
-    grad = torch.zeros(c["vel"].shape, device="cuda")
+    sim = pkg.Simulator(c, c["vel"].astype(np.float64), max_rec=3, precision=1)
+    grad = torch.zeros(c["vel"].shape, dtype=torch.float64, device="cuda")
     with pytest.raises(pkg.SimError) as e:
-        pkg.sim_adjoint(sim.handle, 1, torch.as_tensor(c["wavelet"], device="cuda"), c["src"], 3, c["rec"][:3],
-                        torch.zeros((1, 50, 3), device="cuda"), None, None, 0, grad)
+        pkg.sim_adjoint(sim.handle, 1, torch.as_tensor(c["wavelet"], dtype=torch.float64, device="cuda"), c["src"],
+                        3, c["rec"][:3], torch.zeros((1, 50, 3), dtype=torch.float64, device="cuda"), None, None, 0,
+                        grad)
     assert e.value.code == pkg.abi.SIM_ERR_UNSUPPORTED
     sim.close()
 
