@@ -15,6 +15,8 @@
 // the step kernel adds to the Laplacian of u^{k+1}. a = b = 0 outside the
 // strips, so nu and mu matter only there and the bracket vanishes beyond 4
 // cells from them.
+#include <algorithm>
+
 #include "sim_internal.h"
 #include "stencil.cuh"
 
@@ -50,11 +52,33 @@ __device__ __forceinline__ bool in_strip(const AxisView &v, int q, int margin) {
     return (v.lo > 0 && q < v.lo + margin) || (v.hi > 0 && q >= v.N - v.hi - margin);
 }
 
+// The launch covers the union of the strips (widened by a margin) as up to 4
+// disjoint boxes: the top and bottom row bands over the full width, then the
+// left and right column bands of the rows between; thread i -> (box, z, x),
+// x fastest.
+struct Boxes {
+    int n;
+    int z0[4], z1[4], x0[4], x1[4];
+    long long start[5];
+};
+
+__device__ __forceinline__ bool box_cell(const Boxes &B, long long i, int &z, int &x) {
+    if (i >= B.start[B.n]) return false;
+    int b = 0;
+    while (b + 1 < B.n && B.start[b + 1] <= i) b++;
+    const long long r = i - B.start[b];
+    const int w = B.x1[b] - B.x0[b];
+    z = B.z0[b] + (int)(r / w);
+    x = B.x0[b] + (int)(r % w);
+    return true;
+}
+
 // pass A: nu_new, mu (in place) on the strip cells of axes z (0) and x (2)
-__global__ void k_cpml_adj_a(const StepArgs<float> A, CpmlAdjArgs C, int parity) {
+__global__ void k_cpml_adj_a(const StepArgs<float> A, CpmlAdjArgs C, int parity, const Boxes B) {
     const Geom &g = A.g;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, z = blockIdx.y, shot = blockIdx.z;
-    if (x >= g.NX) return;
+    const int shot = blockIdx.y;
+    int z, x;
+    if (!box_cell(B, blockIdx.x * (long long)blockDim.x + threadIdx.x, z, x)) return;
     const long long o = (long long)shot * g.fstride + cell_off(g, z, 0, x);
     const float *u = C.u;
 #pragma unroll
@@ -84,10 +108,11 @@ __global__ void k_cpml_adj_a(const StepArgs<float> A, CpmlAdjArgs C, int parity)
 
 // pass B: ext = sum over the axes of -D1 (a mu) + D2 (a nu) on the cells
 // within 4 of a strip
-__global__ void k_cpml_adj_b(const StepArgs<float> A, CpmlAdjArgs C, int parity) {
+__global__ void k_cpml_adj_b(const StepArgs<float> A, CpmlAdjArgs C, int parity, const Boxes B) {
     const Geom &g = A.g;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, z = blockIdx.y, shot = blockIdx.z;
-    if (x >= g.NX) return;
+    const int shot = blockIdx.y;
+    int z, x;
+    if (!box_cell(B, blockIdx.x * (long long)blockDim.x + threadIdx.x, z, x)) return;
     const long long o = (long long)shot * g.fstride + cell_off(g, z, 0, x);
     float ext = 0.f;
     bool near = false;
@@ -116,13 +141,42 @@ __global__ void k_cpml_adj_b(const StepArgs<float> A, CpmlAdjArgs C, int parity)
 
 }  // namespace
 
+namespace {
+// the strips of the active axes widened by `margin`, as disjoint boxes
+Boxes strip_boxes(const StepArgs<float> &a, int margin) {
+    const Geom &g = a.g;
+    const bool zon = a.ca[0] != nullptr, xon = a.ca[2] != nullptr;
+    const int zt = zon && g.nbz0 > 0 ? std::min(g.NZ, g.nbz0 + margin) : 0;
+    const int zb = zon && g.nbz1 > 0 ? std::max(zt, g.NZ - g.nbz1 - margin) : g.NZ;
+    const int xl = xon && g.nbx0 > 0 ? std::min(g.NX, g.nbx0 + margin) : 0;
+    const int xr = xon && g.nbx1 > 0 ? std::max(xl, g.NX - g.nbx1 - margin) : g.NX;
+    Boxes B{};
+    auto add = [&](int z0, int z1, int x0, int x1) {
+        if (z1 <= z0 || x1 <= x0) return;
+        B.z0[B.n] = z0;
+        B.z1[B.n] = z1;
+        B.x0[B.n] = x0;
+        B.x1[B.n] = x1;
+        B.start[B.n + 1] = B.start[B.n] + (long long)(z1 - z0) * (x1 - x0);
+        B.n++;
+    };
+    add(0, zt, 0, g.NX);
+    add(zb, g.NZ, 0, g.NX);
+    add(zt, zb, 0, xl);
+    add(zt, zb, xr, g.NX);
+    return B;
+}
+}  // namespace
+
 cudaError_t launch_cpml_adjoint(const StepArgs<float> &a, const CpmlAdjArgs &c, int parity, int nshots,
                                 cudaStream_t st) {
-    const dim3 grid((a.g.NX + 127) / 128, a.g.NZ, nshots);
-    k_cpml_adj_a<<<grid, 128, 0, st>>>(a, c, parity);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_cpml_adj_b<<<grid, 128, 0, st>>>(a, c, parity);
+    const Boxes ba = strip_boxes(a, 0), bb = strip_boxes(a, 4);
+    if (ba.n > 0) {
+        k_cpml_adj_a<<<dim3((unsigned)((ba.start[ba.n] + 127) / 128), nshots), 128, 0, st>>>(a, c, parity, ba);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (bb.n > 0) k_cpml_adj_b<<<dim3((unsigned)((bb.start[bb.n] + 127) / 128), nshots), 128, 0, st>>>(a, c, parity, bb);
     return cudaGetLastError();
 }
 
