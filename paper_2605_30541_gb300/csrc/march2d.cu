@@ -24,10 +24,12 @@
 //    4 rows ahead of the output row (p^n staged 8 rows ahead) in a second
 //    register window.
 //
-// Segments (member, strip, rows) come from a host plan that splits the whole
-// step into equal-cost pieces, one per resident warp; segment starts are
-// multiples of 4 rows.
+// Segments (member, strip, rows) are claimed by the warps from a per-step
+// counter (16-row items, CPML items first), or come from a static host plan
+// of equal-cost pieces, one per resident warp; segment starts are multiples
+// of 4 rows.
 #include <cfloat>
+#include <climits>
 
 #include "f32_tile.cuh"
 #include "sim_internal.h"
@@ -50,6 +52,7 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 __device__ __forceinline__ void cp16(unsigned a, const void *gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void cp16_if(unsigned a, const void *gmem, bool p) {
     asm volatile(
         "{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q cp.async.cg.shared.global [%0], [%1], 16;\n}\n" ::"r"(a),
@@ -453,6 +456,11 @@ struct CpmlCfg {
     static constexpr int WF = ARGS + NSP * RW + D * OW + SCR;
 };
 
+// Runs only on CPML slices (see cpml_segment). Every per-item constant the
+// row loop needs (field pointers, strip bounds, the lane's x profile) is
+// taken into registers first: the slice arguments live in shared memory and
+// the cp.async statements clobber memory, so fields read in the loop would be
+// reloaded after every copy.
 __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepTime &t, const MarchSeg &S, int tz,
                                            float *W, int lane) {
     using C = CpmlCfg;
@@ -462,22 +470,66 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
     float *SC = OR + D * OW;   // psi_x^n of the row, cells -4 .. 131
     const Geom &g = A.g;
     const int P = g.P, NX = g.NX, NZ = g.NZ;
+    const bool fs = g.fs;
     const int za = S.z0, zb = S.z1, x0 = S.bx * kMarchW, gx0 = x0 + 4 * lane;
     const long long base = (long long)S.shot * g.fstride + g.org;
-    const float *pc = A.pbuf[t.n & 1] + base;
-    float *pn = A.pbuf[(t.n + 1) & 1] + base;
+    const int par = t.n & 1;
+    const float *pc = A.pbuf[par] + base;
+    float *pn = A.pbuf[par ^ 1] + base;
     const float *chp = A.ch + g.org;
-    const bool cpx = A.ca[2] != nullptr &&
-                     ((g.nbx0 > 0 && x0 - 4 < g.nbx0) || (g.nbx1 > 0 && x0 + kMarchW + 4 > NX - g.nbx1));
-    const bool cpz = A.ca[0] != nullptr;
-    const bool sponge = A.bc == SIM_BC_SPONGE;  // a batch may mix sponge and CPML slices
-    const bool spx = sponge && ((g.nbx0 > 0 && x0 < g.nbx0) || (g.nbx1 > 0 && x0 + kMarchW > NX - g.nbx1));
-    auto zstrip = [&](int r) {
-        return cpz && r >= 0 && r < NZ && ((g.nbz0 > 0 && r < g.nbz0) || (g.nbz1 > 0 && r >= NZ - g.nbz1));
-    };
-    auto znear = [&](int r) {
-        return cpz && ((g.nbz0 > 0 && r < g.nbz0 + 4) || (g.nbz1 > 0 && r >= NZ - g.nbz1 - 4));
-    };
+    const float src_scale = A.src_scale;
+
+    // x strips: cells [0, nbx0) and [NX - nbx1, NX)
+    const int nbx0 = g.nbx0, nbx1 = g.nbx1;
+    const float *cax = A.ca[2], *cbx = A.cb[2];
+    const bool cpx = cax != nullptr && ((nbx0 > 0 && x0 - 4 < nbx0) || (nbx1 > 0 && x0 + kMarchW + 4 > NX - nbx1));
+    // psi_x^n is needed on cells x0 - 4 .. x0 + 131 (34 chunks of 4) and is
+    // zero off the strips (a = b = 0 there): only chunks [cx0, cx1) meeting a
+    // strip are recomputed and streamed, and of the row's own cells only the
+    // float4s meeting a strip carry zeta_x
+    int cx0 = 34, cx1 = 0;
+    if (cpx) {
+        if (nbx0 > 0 && x0 - 4 < nbx0) {
+            cx0 = 0;
+            cx1 = min(34, (nbx0 - 1 - (x0 - 4)) / 4 + 1);
+        }
+        const int xs = NX - nbx1;
+        if (nbx1 > 0 && x0 + kMarchW + 4 > xs) {
+            cx0 = min(cx0, max(0, xs - (x0 - 4)) / 4);
+            cx1 = max(cx1, min(34, (NX - 1 - (x0 - 4)) / 4 + 1));
+        }
+    }
+    const bool zxl = cpx && ((nbx0 > 0 && gx0 < nbx0) || (nbx1 > 0 && gx0 + 3 >= NX - nbx1));
+    const bool cin0 = cx0 <= lane && lane < cx1, cin1 = lane < 2 && cx0 <= lane + 32 && lane + 32 < cx1;
+    float *psx_n = nullptr, *zex = nullptr;
+    const float *psx_o = nullptr;
+    float4 ax4 = make_float4(0.f, 0.f, 0.f, 0.f), bx4 = ax4, ac4 = ax4, bc4 = ax4;
+    if (cpx) {
+        psx_n = A.psi[2][par] + base;
+        psx_o = A.psi[2][par ^ 1] + base;
+        zex = A.zeta[2] + base;
+        ax4 = __ldg(reinterpret_cast<const float4 *>(cax + gx0));
+        bx4 = __ldg(reinterpret_cast<const float4 *>(cbx + gx0));
+        if (cx0 + lane < cx1) {  // the lane's chunk of the first recompute pass
+            ac4 = __ldg(reinterpret_cast<const float4 *>(cax + x0 - 4 + 4 * (cx0 + lane)));
+            bc4 = __ldg(reinterpret_cast<const float4 *>(cbx + x0 - 4 + 4 * (cx0 + lane)));
+        }
+    }
+    // z strips: rows [0, zs0) and [zs1, NZ); zeta_z and the z addend matter
+    // on rows < zn0 and >= zn1 (within 4 rows of a strip)
+    const float *caz = A.ca[0], *cbz = A.cb[0];
+    const bool cpz = caz != nullptr;
+    const int zs0 = g.nbz0 > 0 ? g.nbz0 : 0, zs1 = g.nbz1 > 0 ? NZ - g.nbz1 : NZ;
+    const int zn0 = zs0 > 0 ? zs0 + 4 : 0, zn1 = zs1 < NZ ? zs1 - 4 : INT_MAX;
+    float *psz_n = nullptr, *zez = nullptr;
+    const float *psz_o = nullptr;
+    if (cpz) {
+        psz_n = A.psi[0][par] + base;
+        psz_o = A.psi[0][par ^ 1] + base;
+        zez = A.zeta[0] + base;
+    }
+    auto zstrip = [&](int r) { return cpz && r >= 0 && r < NZ && (r < zs0 || r >= zs1); };
+    auto znear = [&](int r) { return cpz && (r < zn0 || r >= zn1); };
     const int zlast = zb - 1 + LA;  // last p^n row the segment reads
 
     auto issue_p = [&](int r) {
@@ -492,15 +544,19 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
         cp_async16(o + C::O_PP + 4 * lane, pn + ro);
         cp_async16(o + C::O_C + 4 * lane, chp + ro);
         if (cpx) {
-            const float *ps = A.psi[2][(t.n + 1) & 1] + base + (long long)z * P + x0 - 4;
-            cp_async16(o + C::O_PSX + 4 * lane, ps + 4 * lane);
-            if (lane < 2) cp_async16(o + C::O_PSX + 128 + 4 * lane, ps + 128 + 4 * lane);
-            cp_async16(o + C::O_ZX + 4 * lane, A.zeta[2] + base + ro);
+            const float *ps = psx_o + (long long)z * P + x0 - 4;
+            cp16_if(smem_u32(o + C::O_PSX + 4 * lane), ps + 4 * lane, cin0);
+            cp16_if(smem_u32(o + C::O_PSX + 128 + 4 * lane), ps + 128 + 4 * lane, cin1);
+            cp16_if(smem_u32(o + C::O_ZX + 4 * lane), zex + ro, zxl);
         }
-        if (zstrip(z)) cp_async16(o + C::O_ZZ + 4 * lane, A.zeta[0] + base + ro);
-        if (zstrip(z + 4)) cp_async16(o + C::O_PSZ + 4 * lane, A.psi[0][(t.n + 1) & 1] + base + ro + 4LL * P);
+        if (zstrip(z)) cp_async16(o + C::O_ZZ + 4 * lane, zez + ro);
+        if (zstrip(z + 4)) cp_async16(o + C::O_PSZ + 4 * lane, psz_o + ro + 4LL * P);
     };
 
+    if (cpx) {  // chunks outside [cx0, cx1) read as zero in the psi_x^n row
+        st4(SC + 4 * lane, make_float4(0.f, 0.f, 0.f, 0.f));
+        if (lane < 2) st4(SC + 128 + 4 * lane, make_float4(0.f, 0.f, 0.f, 0.f));
+    }
 #pragma unroll
     for (int j = 0; j < D; j++) {
         if (j == 0) {
@@ -523,8 +579,6 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
 #pragma unroll
     for (int k = 0; k < 9; k++) qz[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (cpz) {
-        float *psn = A.psi[0][t.n & 1] + base;
-        const float *pso = A.psi[0][(t.n + 1) & 1] + base;
 #pragma unroll
         for (int k = 0; k < 8; k++) {
             const int r = za - 4 + k;
@@ -536,22 +590,38 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
                     pm[m] = rr >= za ? ld4(PR + ((rr - za) % NSP) * RW + H + 4 * lane)
                                      : ld4(pc + (long long)rr * P + gx0);
                 }
-                const float az = __ldg(A.ca[0] + r), bz = __ldg(A.cb[0] + r);
-                const float4 old = ld4(pso + (long long)r * P + gx0);
+                const float az = __ldg(caz + r), bz = __ldg(cbz + r);
+                const float4 old = ld4(psz_o + (long long)r * P + gx0);
                 qz[k] = psi_z_row(pm[0], pm[1], pm[2], pm[3], pm[5], pm[6], pm[7], pm[8], old, az, bz, gx0, NX);
-                if (r >= za && r < zb) st4(psn + (long long)r * P + gx0, qz[k]);
+                if (r >= za && r < zb) st4(psz_n + (long long)r * P + gx0, qz[k]);
             }
         }
     }
 
-    float4 E4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (spx) E4 = __ldg(reinterpret_cast<const float4 *>(A.E[2] + gx0));
     float *gout = A.sample ? static_cast<float *>(A.io->gather) : nullptr;
     const bool has_inj = t.inj_row >= 0;
     Snap snap;
     snap.init(A, t, S, lane);
     float tmax = 0.f;
     Lists L;
+
+    // psi_x^n of chunk c (cells x0 - 4 + 4c ..) from row z's p^n, into SC and,
+    // for the row's own cells, into the field
+    auto psi_chunk = [&](const float *rz, const float *pso, float *pw, int c, const float4 &a4, const float4 &b4) {
+        const int gx = x0 - 4 + 4 * c;
+        float w12[12];
+        unpack3(ld4(rz + 4 * c - 8), ld4(rz + 4 * c - 4), ld4(rz + 4 * c), w12);
+        const float4 old = ld4(pso + 4 * c);
+        float o[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const bool in = gx + k >= 0 && gx + k < NX;
+            o[k] = in ? lane_of(b4, k) * lane_of(old, k) + lane_of(a4, k) * d1w(w12, k) : 0.f;
+        }
+        const float4 o4 = make_float4(o[0], o[1], o[2], o[3]);
+        st4(SC + 4 * c, o4);
+        if (c >= 1 && c <= 32) st4(pw + gx, o4);
+    };
 
     for (int z = za; z < zb; z++) {
         const int i = z - za;
@@ -577,42 +647,23 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
         float cadd[4] = {0.f, 0.f, 0.f, 0.f};
         if (cpx) {
             const float *pso = os + C::O_PSX;
-            float *pw = A.psi[2][t.n & 1] + base + (long long)z * P;
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int c = lane + 32 * h;
-                if (c < 34) {
-                    const int gx = x0 - 4 + 4 * c;
-                    float w12[12];
-                    unpack3(ld4(rz + 4 * c - 8), ld4(rz + 4 * c - 4), ld4(rz + 4 * c), w12);
-                    const float4 a4 = __ldg(reinterpret_cast<const float4 *>(A.ca[2] + gx));
-                    const float4 b4 = __ldg(reinterpret_cast<const float4 *>(A.cb[2] + gx));
-                    const float4 old = ld4(pso + 4 * c);
-                    float o[4];
-#pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        const bool in = gx + k >= 0 && gx + k < NX;
-                        o[k] = in ? lane_of(b4, k) * lane_of(old, k) + lane_of(a4, k) * d1w(w12, k) : 0.f;
-                    }
-                    const float4 o4 = make_float4(o[0], o[1], o[2], o[3]);
-                    st4(SC + 4 * c, o4);
-                    if (c >= 1 && c <= 32) st4(pw + gx, o4);
-                }
-            }
+            float *pw = psx_n + (long long)z * P;
+            if (cx0 + lane < cx1) psi_chunk(rz, pso, pw, cx0 + lane, ac4, bc4);
+            for (int c = cx0 + lane + 32; c < cx1; c += 32)
+                psi_chunk(rz, pso, pw, c, __ldg(reinterpret_cast<const float4 *>(cax + x0 - 4 + 4 * c)),
+                          __ldg(reinterpret_cast<const float4 *>(cbx + x0 - 4 + 4 * c)));
             __syncwarp();
             float px[12];
             unpack3(ld4(SC + 4 * lane), ld4(SC + 4 * lane + 4), ld4(SC + 4 * lane + 8), px);
-            const float4 a4 = __ldg(reinterpret_cast<const float4 *>(A.ca[2] + gx0));
-            const float4 b4 = __ldg(reinterpret_cast<const float4 *>(A.cb[2] + gx0));
-            const float4 z4 = ld4(os + C::O_ZX + 4 * lane);
+            const float4 z4 = zxl ? ld4(os + C::O_ZX + 4 * lane) : make_float4(0.f, 0.f, 0.f, 0.f);
             float zo[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const float dps = d1w(px, k);
-                zo[k] = lane_of(b4, k) * lane_of(z4, k) + lane_of(a4, k) * (d2x[k] + dps);
+                zo[k] = lane_of(bx4, k) * lane_of(z4, k) + lane_of(ax4, k) * (d2x[k] + dps);
                 cadd[k] += dps + zo[k];
             }
-            st4(A.zeta[2] + base + ro, make_float4(zo[0], zo[1], zo[2], zo[3]));
+            if (zxl) st4(zex + ro, make_float4(zo[0], zo[1], zo[2], zo[3]));
         }
         if (cpz) {
             // psi_z^n of row z + 4 enters the window first: D1 over rows z .. z+8
@@ -623,10 +674,10 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
                 const float4 f6 = ld4(PR + ((i + 6) % NSP) * RW + H + 4 * lane);
                 const float4 f7 = ld4(PR + ((i + 7) % NSP) * RW + H + 4 * lane);
                 const float4 f8 = ld4(PR + ((i + 8) % NSP) * RW + H + 4 * lane);
-                const float az = __ldg(A.ca[0] + r), bz = __ldg(A.cb[0] + r);
+                const float az = __ldg(caz + r), bz = __ldg(cbz + r);
                 const float4 old = ld4(os + C::O_PSZ + 4 * lane);
                 nz4 = psi_z_row(q[4], q[5], q[6], q[7], f5, f6, f7, f8, old, az, bz, gx0, NX);
-                if (r < zb) st4(A.psi[0][t.n & 1] + base + ro + 4LL * P, nz4);
+                if (r < zb) st4(psz_n + ro + 4LL * P, nz4);
             }
             qz[8] = nz4;
             if (znear(z)) {
@@ -634,8 +685,8 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
                 float az = 0.f, bz = 0.f;
                 float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (in) {
-                    az = __ldg(A.ca[0] + z);
-                    bz = __ldg(A.cb[0] + z);
+                    az = __ldg(caz + z);
+                    bz = __ldg(cbz + z);
                     z4 = ld4(os + C::O_ZZ + 4 * lane);
                 }
                 float zo[4];
@@ -648,7 +699,7 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
                     zo[k] = bz * lane_of(z4, k) + az * (d2z[k] + dps);
                     cadd[k] += dps + zo[k];
                 }
-                if (in) st4(A.zeta[0] + base + ro, make_float4(zo[0], zo[1], zo[2], zo[3]));
+                if (in) st4(zez + ro, make_float4(zo[0], zo[1], zo[2], zo[3]));
             }
         }
 
@@ -657,25 +708,16 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
         const bool any_inj = has_inj && inject_row(A, t, S, L, lzc, inj, lane);
 
         const float4 pp4 = ld4(os + C::O_PP + 4 * lane), c4 = ld4(os + C::O_C + 4 * lane);
-        const bool spg = sponge && (spx || (g.nbz0 > 0 && z < g.nbz0) || (g.nbz1 > 0 && z >= NZ - g.nbz1));
-        const float ez = spg ? __ldg(A.E[0] + z) : 0.f;
         float res[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             float rhs = d2z[k] + d2x[k];
             rhs += cadd[k];
-            if (any_inj) rhs += A.src_scale * lane_of(inj, k);
-            const float p = v[4 + k], pp = lane_of(pp4, k), chv = lane_of(c4, k);
-            float out;
-            if (spg) {
-                const float a = chv * (ez + lane_of(E4, k));
-                out = __fdividef(2.f * p - (1.f - a) * pp + chv * rhs, 1.f + a);
-            } else {
-                out = 2.f * p - pp + chv * rhs;
-            }
+            if (any_inj) rhs += src_scale * lane_of(inj, k);
+            const float out = 2.f * v[4 + k] - lane_of(pp4, k) + lane_of(c4, k) * rhs;
             res[k] = gx0 + k < NX ? out : 0.f;
         }
-        if (g.fs && z == 0) res[0] = res[1] = res[2] = res[3] = 0.f;
+        if (fs && z == 0) res[0] = res[1] = res[2] = res[3] = 0.f;
         st4(pn + ro, make_float4(res[0], res[1], res[2], res[3]));
         snap.row(g, t, z, gx0, v + 4, res, tmax);
 
@@ -706,7 +748,7 @@ struct KCfg<false> {
 };
 template <>
 struct KCfg<true> {  // both loops: CPML segments and the plain ones of CPML problems
-    static constexpr int WPB = 4, MINB = 3, WF = CpmlCfg::WF > LeanCfg::WF ? CpmlCfg::WF : LeanCfg::WF,
+    static constexpr int WPB = 4, MINB = 2, WF = CpmlCfg::WF > LeanCfg::WF ? CpmlCfg::WF : LeanCfg::WF,
                          ARGS = CpmlCfg::ARGS;
     static_assert(CpmlCfg::ARGS == LeanCfg::ARGS, "one argument block layout");
 };
