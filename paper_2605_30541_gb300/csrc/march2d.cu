@@ -443,10 +443,11 @@ __device__ __forceinline__ void march_lean(const StepArgs<float> &A, const StepT
 // ---------------------------------------------------------------- CPML: one row per iteration
 struct CpmlCfg {
     static constexpr int LA = 8;   // p^n rows staged ahead of the output row
-    static constexpr int D = 2;    // rows of copies in flight
+    static constexpr int D = 2;    // rows of copies in flight (a power of two)
     static constexpr int H = 8;    // x halo of a staged p^n row
     static constexpr int RW = kMarchW + 2 * H;
-    static constexpr int NSP = LA + D;
+    static constexpr int NSP = 16;  // p^n ring slots: a power of two >= LA + D
+    static_assert((NSP & (NSP - 1)) == 0 && NSP >= LA + D && (D & (D - 1)) == 0, "ring sizes");
     // output-row slot: p^{n-1}, c, psi_x^{n-1} (cells -4 .. 131), zeta_x,
     // zeta_z, psi_z^{n-1} of row z + 4
     static constexpr int O_PP = 0, O_C = 128, O_PSX = 256, O_ZX = 392, O_ZZ = 520, O_PSZ = 648;
@@ -533,13 +534,13 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
     const int zlast = zb - 1 + LA;  // last p^n row the segment reads
 
     auto issue_p = [&](int r) {
-        float *dst = PR + ((r - za) % NSP) * RW;
+        float *dst = PR + ((r - za) & (NSP - 1)) * RW;
         const float *src = pc + (long long)r * P + x0 - H;
         cp_async16(dst + 4 * lane, src + 4 * lane);
         if (lane < RW / 4 - 32) cp_async16(dst + 128 + 4 * lane, src + 128 + 4 * lane);
     };
     auto issue_o = [&](int z) {
-        float *o = OR + ((z - za) % D) * OW;
+        float *o = OR + ((z - za) & (D - 1)) * OW;
         const long long ro = (long long)z * P + gx0;
         cp_async16(o + C::O_PP + 4 * lane, pn + ro);
         cp_async16(o + C::O_C + 4 * lane, chp + ro);
@@ -587,7 +588,7 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
 #pragma unroll
                 for (int m = 0; m < 9; m++) {
                     const int rr = r - 4 + m;
-                    pm[m] = rr >= za ? ld4(PR + ((rr - za) % NSP) * RW + H + 4 * lane)
+                    pm[m] = rr >= za ? ld4(PR + ((rr - za) & (NSP - 1)) * RW + H + 4 * lane)
                                      : ld4(pc + (long long)rr * P + gx0);
                 }
                 const float az = __ldg(caz + r), bz = __ldg(cbz + r);
@@ -627,9 +628,9 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
         const int i = z - za;
         cp_wait<D - 1>();
         __syncwarp();
-        const float *rz = PR + (i % NSP) * RW + H;  // row z; cell x0 at rz[0]
-        q[8] = ld4(PR + ((i + 4) % NSP) * RW + H + 4 * lane);
-        const float *os = OR + (i % D) * OW;
+        const float *rz = PR + (i & (NSP - 1)) * RW + H;  // row z; cell x0 at rz[0]
+        q[8] = ld4(PR + ((i + 4) & (NSP - 1)) * RW + H + 4 * lane);
+        const float *os = OR + (i & (D - 1)) * OW;
         const long long ro = (long long)z * P + gx0;
         L.at(A, S, tz, z, gout != nullptr, has_inj);
         const int lzc = z - L.tz0;
@@ -670,10 +671,10 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
             float4 nz4 = make_float4(0.f, 0.f, 0.f, 0.f);
             const int r = z + 4;
             if (zstrip(r)) {
-                const float4 f5 = ld4(PR + ((i + 5) % NSP) * RW + H + 4 * lane);
-                const float4 f6 = ld4(PR + ((i + 6) % NSP) * RW + H + 4 * lane);
-                const float4 f7 = ld4(PR + ((i + 7) % NSP) * RW + H + 4 * lane);
-                const float4 f8 = ld4(PR + ((i + 8) % NSP) * RW + H + 4 * lane);
+                const float4 f5 = ld4(PR + ((i + 5) & (NSP - 1)) * RW + H + 4 * lane);
+                const float4 f6 = ld4(PR + ((i + 6) & (NSP - 1)) * RW + H + 4 * lane);
+                const float4 f7 = ld4(PR + ((i + 7) & (NSP - 1)) * RW + H + 4 * lane);
+                const float4 f8 = ld4(PR + ((i + 8) & (NSP - 1)) * RW + H + 4 * lane);
                 const float az = __ldg(caz + r), bz = __ldg(cbz + r);
                 const float4 old = ld4(os + C::O_PSZ + 4 * lane);
                 nz4 = psi_z_row(q[4], q[5], q[6], q[7], f5, f6, f7, f8, old, az, bz, gx0, NX);
@@ -703,7 +704,7 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
             }
         }
 
-        if (gout) sample_row(A, t, S, L, lzc, rz, PR + ((i + 1) % NSP) * RW + H, gout, lane);
+        if (gout) sample_row(A, t, S, L, lzc, rz, PR + ((i + 1) & (NSP - 1)) * RW + H, gout, lane);
         float4 inj = make_float4(0.f, 0.f, 0.f, 0.f);
         const bool any_inj = has_inj && inject_row(A, t, S, L, lzc, inj, lane);
 
