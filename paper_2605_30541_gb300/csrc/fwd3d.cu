@@ -375,6 +375,139 @@ __global__ void k_cpml_add3d(const StepArgs<float> A, const int n, const int ax,
     }
 }
 
+// CPML of the z or y axis (stride > 1) in one pass after the update, on
+// float4 columns along the axis. A thread owns one column of one strip range
+// [s0, s1) (the strip widened by 4 cells towards the interior, where D1 psi
+// is non-zero) and marches along it: psi^n at r from p^n at r - 4 .. r + 4
+// (a 13-entry register window of p^n, r - 8 .. r + 4), then, 4 positions
+// behind, zeta^n and the addend at q = r - 4 from the 9 psi^n values
+// q - 4 .. q + 4 (a second window) and D2 p^n at q:
+//   psi^n  = b psi^{n-1}  + a D1 p^n          (strip cells; written back)
+//   zeta^n = b zeta^{n-1} + a (D2 p^n + D1 psi^n)
+//   p^{n+1} += c (D1 psi^n + zeta^n)          (cells of [s0, s1))
+// p^n is still intact after the update kernel (which writes p^{n+1} into the
+// other buffer). Same arithmetic as k_psi3d + k_cpml_add3d, with every value
+// read once. Not used for a z range within reach of a free surface (its D2
+// needs the odd mirror; the two-kernel path handles it).
+__device__ __forceinline__ float comp4(const float4 &v, int c) {
+    return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+
+struct ColRanges {
+    int n;            // ranges (1 or 2)
+    int s0[2], s1[2]; // [s0, s1) along the axis
+};
+
+__global__ void __launch_bounds__(128) k_cpml_col3d(const StepArgs<float> A, const int n, const int ax,
+                                                    const ColRanges R, const int ncols) {
+    const Geom &g = A.g;
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (tid >= (long long)R.n * ncols) return;
+    const int k = (int)(tid / ncols), col = (int)(tid - (long long)k * ncols);
+    const int nx4 = (g.NX + 3) >> 2;
+    const int u = col / nx4, x = 4 * (col - u * nx4);  // u: y (z axis) or z (y axis)
+    const int N = ax == 0 ? g.NZ : g.NY;
+    const int lo = ax == 0 ? g.nbz0 : g.nby0, hi = ax == 0 ? g.nbz1 : g.nby1;
+    const long long s = axis_stride(g, ax);
+    const int s0 = k == 0 ? R.s0[0] : R.s0[1], s1 = k == 0 ? R.s1[0] : R.s1[1];
+    const int shot = blockIdx.y;
+    const long long sh = (long long)shot * g.fstride;
+    const long long o0 = ax == 0 ? cell_off(g, 0, u, x) : cell_off(g, u, 0, x);  // position 0 of the column
+    const float *__restrict__ p = A.pbuf[n & 1] + sh + o0;
+    float *__restrict__ pn = A.pbuf[(n + 1) & 1] + sh + o0;
+    float *__restrict__ psi = A.psi[ax][0] + sh + o0;
+    float *__restrict__ zeta = A.zeta[ax] + sh + o0;
+    const float *__restrict__ ch = A.ch + o0;
+    const float *ca = A.ca[ax], *cb = A.cb[ax];
+    const bool skip_row = g.fs && ax == 1 && u == 0;  // the free-surface row stays zero
+    auto strip = [&](int r) { return (lo > 0 && r >= 0 && r < lo) || (hi > 0 && r >= N - hi && r < N); };
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    // the loads of position r (p^n at r + 4, psi^{n-1} at r, and at q = r - 4
+    // zeta^{n-1}, c, p^{n+1}), issued one position ahead of their use
+    struct Ld {
+        float4 p, ps, zo, c, pv;
+    };
+    auto load = [&](int r, Ld &L) {
+        L.p = ld4g(p + (long long)(r + 4) * s);
+        L.ps = strip(r) ? ld4g(psi + (long long)r * s) : zero;
+        const int q = r - 4;
+        if (q >= s0 && !skip_row) {
+            L.zo = strip(q) ? ld4g(zeta + (long long)q * s) : zero;
+            L.c = ld4g(ch + (long long)q * s);
+            L.pv = ld4g(pn + (long long)q * s);
+        }
+    };
+
+    float4 P[13], S[9];
+#pragma unroll
+    for (int m = 0; m < 4; m++) P[m] = zero;
+#pragma unroll
+    for (int m = 0; m < 8; m++) P[4 + m] = ld4g(p + (long long)(s0 - 8 + m) * s);
+#pragma unroll
+    for (int m = 0; m < 9; m++) S[m] = zero;
+    Ld nx{zero, zero, zero, zero, zero};
+    load(s0 - 4, nx);
+
+    for (int r = s0 - 4; r < s1 + 4; r++) {
+        const Ld cur = nx;
+        if (r + 1 < s1 + 4) load(r + 1, nx);
+        P[12] = cur.p;
+        // psi^n at r (zero off the strips)
+        float4 ps = zero;
+        if (strip(r)) {
+            const float a = __ldg(ca + r), b = __ldg(cb + r);
+            float d[4];
+#pragma unroll
+            for (int c = 0; c < 4; c++)
+                d[c] = float(kD1) * (comp4(P[9], c) - comp4(P[7], c)) +
+                       float(kD2) * (comp4(P[10], c) - comp4(P[6], c)) +
+                       float(kD3) * (comp4(P[11], c) - comp4(P[5], c)) +
+                       float(kD4) * (comp4(P[12], c) - comp4(P[4], c));
+            const float4 old = cur.ps;
+            ps = make_float4(b * old.x + a * d[0], b * old.y + a * d[1], b * old.z + a * d[2], b * old.w + a * d[3]);
+            *reinterpret_cast<float4 *>(psi + (long long)r * s) = ps;
+        }
+        S[8] = ps;
+        // zeta^n and the addend at q = r - 4
+        const int q = r - 4;
+        if (q >= s0 && !skip_row) {
+            float a = 0.f, b = 0.f;
+            const bool in = strip(q);
+            if (in) {
+                a = __ldg(ca + q);
+                b = __ldg(cb + q);
+            }
+            const float4 zo = cur.zo, c4 = cur.c;
+            float4 pv = cur.pv;
+            float zt[4], add[4];
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const float d2 = float(kC0) * comp4(P[4], c) + float(kC1) * (comp4(P[5], c) + comp4(P[3], c)) +
+                                 float(kC2) * (comp4(P[6], c) + comp4(P[2], c)) +
+                                 float(kC3) * (comp4(P[7], c) + comp4(P[1], c)) +
+                                 float(kC4) * (comp4(P[8], c) + comp4(P[0], c));
+                const float dps = float(kD1) * (comp4(S[5], c) - comp4(S[3], c)) +
+                                  float(kD2) * (comp4(S[6], c) - comp4(S[2], c)) +
+                                  float(kD3) * (comp4(S[7], c) - comp4(S[1], c)) +
+                                  float(kD4) * (comp4(S[8], c) - comp4(S[0], c));
+                zt[c] = b * comp4(zo, c) + a * (d2 + dps);
+                add[c] = dps + zt[c];
+            }
+            if (in) *reinterpret_cast<float4 *>(zeta + (long long)q * s) = make_float4(zt[0], zt[1], zt[2], zt[3]);
+            pv.x += c4.x * add[0];
+            pv.y += c4.y * add[1];
+            pv.z += c4.z * add[2];
+            pv.w += c4.w * add[3];
+            *reinterpret_cast<float4 *>(pn + (long long)q * s) = pv;
+        }
+#pragma unroll
+        for (int m = 0; m < 12; m++) P[m] = P[m + 1];
+#pragma unroll
+        for (int m = 0; m < 8; m++) S[m] = S[m + 1];
+    }
+}
+
 // ---------------------------------------------------------------- points (3D)
 
 // p^{n+1} += c w[n] weight / h / (1 + a) at each source corner (one thread per shot and corner)
@@ -532,6 +665,27 @@ cudaError_t launch_cpml3d(const StepArgs<float> &a, int n, int ax, int phase, in
     const Geom &g = a.g;
     const int N[3] = {g.NZ, g.NY, g.NX};
     const int lo[3] = {g.nbz0, g.nby0, g.nbx0}, hi[3] = {g.nbz1, g.nby1, g.nbx1};
+    if (ax != 2) {  // z or y: one marching pass after the update (phase 1), unless a z range nears a free surface
+        ColRanges R{};
+        const int l1 = lo[ax] > 0 ? std::min(N[ax], lo[ax] + 4) : 0;
+        const int h0 = hi[ax] > 0 ? std::max(0, N[ax] - hi[ax] - 4) : N[ax];
+        if (l1 > 0 && h0 < N[ax] && l1 >= h0) {
+            R.n = 1;
+            R.s0[0] = 0;
+            R.s1[0] = N[ax];
+        } else {
+            if (l1 > 0) R.s0[R.n] = 0, R.s1[R.n++] = l1;
+            if (h0 < N[ax]) R.s0[R.n] = h0, R.s1[R.n++] = N[ax];
+        }
+        const bool mirror = ax == 0 && g.fs && R.n > 0 && R.s0[0] < 4;
+        if (!mirror) {
+            if (phase == 0 || R.n == 0) return cudaSuccess;
+            const int ncols = (ax == 0 ? g.NY : g.NZ) * ((g.NX + 3) >> 2);
+            const long long th = (long long)R.n * ncols;
+            k_cpml_col3d<<<dim3((unsigned)((th + 127) / 128), nshots), 128, 0, st>>>(a, n, ax, R, ncols);
+            return cudaGetLastError();
+        }
+    }
     const int widen = phase == 0 ? 0 : 4;
     int a0 = 0, a1 = lo[ax] > 0 ? std::min(N[ax], lo[ax] + widen) : 0;
     int b0 = hi[ax] > 0 ? std::max(0, N[ax] - hi[ax] - widen) : N[ax], b1 = N[ax];

@@ -25,10 +25,11 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / nb) if nb else float(np.linalg.norm(a))
 
 
-def case3d(bc, fs, nb=6, n=(30, 26, 34), nt=160, snaps=False):
+def case3d(bc, fs, nb=6, n=(30, 26, 34), nt=160, snaps=False, top=None):
     nz, ny, nx = n
+    top = (0 if fs else nb) if top is None else top
     cfg = dict(ndim=3, nz=nz, ny=ny, nx=nx, h=10.0, dt=8e-4, nt=nt, bc=bc,
-               nb=[0 if fs else nb, nb, nb, nb, nb, nb], free_surface=fs, R=1e-3, f_ref=15.0)
+               nb=[top, nb, nb, nb, nb, nb], free_surface=fs, R=1e-3, f_ref=15.0)
     if snaps:
         cfg.update(snap_every=9, snap_begin=2, snap_end=nt)
     vel = synth.procedural_3d(nz, ny, nx, 10.0, 17)
@@ -58,6 +59,21 @@ def test_small_3d_parity(pkg, bc, fs):
     for k in range(2):
         assert rel(res["gather"][k], refs[k]["gather"]) <= 1e-4, k
         assert rel(res["snaps"][k], refs[k]["snaps"]) <= 1e-4, k
+
+
+@pytest.mark.parametrize("n,fs", [((6, 5, 9), 0), ((3, 18, 20), 1)])
+def test_3d_cpml_strip_layouts(pkg, n, fs):
+    # z and y strips whose widened ranges meet (one range per marching
+    # column), and a bottom z strip whose widened range reaches the free
+    # surface (the mirrored z-derivative of the two-kernel path)
+    cfg, vel, w = case3d("cpml", fs, n=n, nt=120)
+    nz, ny, nx = n
+    srcs = np.array([[0.55 * (nx - 1) * 10.0, 0.4 * (ny - 1) * 10.0, 0.5 * (nz - 1) * 10.0]])
+    rng = np.random.default_rng(5)
+    rec = np.stack([rng.uniform(0, (nx - 1) * 10.0, 20), rng.uniform(0, (ny - 1) * 10.0, 20),
+                    rng.uniform(0, (nz - 1) * 10.0, 20)], axis=1)
+    res, refs = run(pkg, cfg, vel, w, srcs, rec)
+    assert rel(res["gather"][0], refs[0]["gather"]) <= 1e-4
 
 
 def test_3d_fp16_snapshots(pkg):
