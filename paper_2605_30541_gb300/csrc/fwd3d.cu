@@ -508,6 +508,90 @@ __global__ void __launch_bounds__(128) k_cpml_col3d(const StepArgs<float> A, con
     }
 }
 
+// CPML of the x axis in one pass after the update: a half-warp per (z, y)
+// row and strip end. Lane j holds p^n at the 4 cells xa + 4j (lanes
+// [0, nq + 4)); the neighbours' float4s come by shuffles. Lanes [1, nq + 3)
+// form psi^n (zero off the strip, written back on strip cells), lanes
+// [2, nq + 2) cover the strip widened by 4 cells and update zeta^n and
+// p^{n+1} += c (D1 psi^n + zeta^n). Same arithmetic as k_psi3d +
+// k_cpml_add3d on the x axis.
+struct XEnds {
+    int ne;            // strip ends (1 or 2)
+    int xa[2], nq[2];  // first cell of lane 0 (a multiple of 4), float4 lanes of the widened strip
+};
+
+__device__ __forceinline__ float4 shfl4(const float4 v, int d, bool up) {
+    float4 r;
+    r.x = up ? __shfl_up_sync(0xffffffffu, v.x, d, 16) : __shfl_down_sync(0xffffffffu, v.x, d, 16);
+    r.y = up ? __shfl_up_sync(0xffffffffu, v.y, d, 16) : __shfl_down_sync(0xffffffffu, v.y, d, 16);
+    r.z = up ? __shfl_up_sync(0xffffffffu, v.z, d, 16) : __shfl_down_sync(0xffffffffu, v.z, d, 16);
+    r.w = up ? __shfl_up_sync(0xffffffffu, v.w, d, 16) : __shfl_down_sync(0xffffffffu, v.w, d, 16);
+    return r;
+}
+
+__global__ void __launch_bounds__(128) k_cpml_row3d(const StepArgs<float> A, const int n, const XEnds E,
+                                                    const long long nrows) {
+    const Geom &g = A.g;
+    const long long hw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 4;
+    const int j = threadIdx.x & 15;
+    const bool live = hw < (long long)E.ne * nrows;  // every lane takes part in the shuffles
+    const int e = live && hw >= nrows ? 1 : 0;
+    const long long row = live ? hw - e * nrows : 0;
+    const int z = (int)(row / g.NY), y = (int)(row - (long long)z * g.NY);
+    const int xa = e ? E.xa[1] : E.xa[0], nq = e ? E.nq[1] : E.nq[0];
+    const int xj = xa + 4 * j;
+    const long long o = (long long)blockIdx.y * g.fstride + cell_off(g, z, y, 0) + xj;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int NX = g.NX, nbx0 = g.nbx0, nbx1 = g.nbx1;
+    const bool strip = xj + 3 >= 0 && xj < NX && ((nbx0 > 0 && xj < nbx0) || (nbx1 > 0 && xj + 3 >= NX - nbx1));
+    const bool pl = live && j < nq + 4, sl = live && j >= 1 && j < nq + 3, ql = live && j >= 2 && j < nq + 2;
+
+    const float4 pc = pl ? ld4g(A.pbuf[n & 1] + o) : zero;
+    const float4 pL = shfl4(pc, 1, true), pR = shfl4(pc, 1, false);
+    const float v[12] = {pL.x, pL.y, pL.z, pL.w, pc.x, pc.y, pc.z, pc.w, pR.x, pR.y, pR.z, pR.w};
+    float4 a4 = zero, b4 = zero;
+    if (sl && strip) {
+        a4 = ld4g(A.ca[2] + xj);
+        b4 = ld4g(A.cb[2] + xj);
+    }
+    // psi^n of the lane's cells
+    float4 ps = zero;
+    if (sl && strip) {
+        float *psi = A.psi[2][0] + o;
+        const float4 old = ld4g(psi);
+        float r[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            r[k] = comp4(b4, k) * comp4(old, k) +
+                   comp4(a4, k) * (float(kD1) * (v[5 + k] - v[3 + k]) + float(kD2) * (v[6 + k] - v[2 + k]) +
+                                   float(kD3) * (v[7 + k] - v[1 + k]) + float(kD4) * (v[8 + k] - v[k]));
+        ps = make_float4(r[0], r[1], r[2], r[3]);
+        *reinterpret_cast<float4 *>(psi) = ps;
+    }
+    const float4 sL = shfl4(ps, 1, true), sR = shfl4(ps, 1, false);
+    if (!ql || (g.fs && z == 0)) return;  // the free-surface row stays zero
+    const float w[12] = {sL.x, sL.y, sL.z, sL.w, ps.x, ps.y, ps.z, ps.w, sR.x, sR.y, sR.z, sR.w};
+    const float4 zo = strip ? ld4g(A.zeta[2] + o) : zero, c4 = ld4g(A.ch + (o - (long long)blockIdx.y * g.fstride));
+    float *pn = A.pbuf[(n + 1) & 1] + o;
+    float4 pv = ld4g(pn);
+    float zt[4], add[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const float d2 = float(kC0) * v[4 + k] + float(kC1) * (v[5 + k] + v[3 + k]) + float(kC2) * (v[6 + k] + v[2 + k]) +
+                         float(kC3) * (v[7 + k] + v[1 + k]) + float(kC4) * (v[8 + k] + v[k]);
+        const float dps = float(kD1) * (w[5 + k] - w[3 + k]) + float(kD2) * (w[6 + k] - w[2 + k]) +
+                          float(kD3) * (w[7 + k] - w[1 + k]) + float(kD4) * (w[8 + k] - w[k]);
+        zt[k] = comp4(b4, k) * comp4(zo, k) + comp4(a4, k) * (d2 + dps);
+        add[k] = dps + zt[k];
+    }
+    if (strip) *reinterpret_cast<float4 *>(A.zeta[2] + o) = make_float4(zt[0], zt[1], zt[2], zt[3]);
+    pv.x += c4.x * add[0];
+    pv.y += c4.y * add[1];
+    pv.z += c4.z * add[2];
+    pv.w += c4.w * add[3];
+    *reinterpret_cast<float4 *>(pn) = pv;
+}
+
 // ---------------------------------------------------------------- points (3D)
 
 // p^{n+1} += c w[n] weight / h / (1 + a) at each source corner (one thread per shot and corner)
@@ -665,6 +749,27 @@ cudaError_t launch_cpml3d(const StepArgs<float> &a, int n, int ax, int phase, in
     const Geom &g = a.g;
     const int N[3] = {g.NZ, g.NY, g.NX};
     const int lo[3] = {g.nbz0, g.nby0, g.nbx0}, hi[3] = {g.nbz1, g.nby1, g.nbx1};
+    if (ax == 2) {  // x: one pass after the update (phase 1), when each widened strip spans <= 12 float4s
+        XEnds E{};
+        const int NX = N[2];
+        int qa[2], qb[2], m = 0;  // widened strips [qa, qb)
+        if (lo[2] > 0) qa[m] = 0, qb[m++] = std::min(NX, lo[2] + 4);
+        if (hi[2] > 0) qa[m] = std::max(0, NX - hi[2] - 4), qb[m++] = NX;
+        bool ok = m > 0 && (m < 2 || qa[1] - qb[0] >= 16);  // ends apart: no cell's psi formed twice
+        for (int k = 0; k < m && ok; k++) {
+            const int q4 = qa[k] & ~3, nq = (qb[k] - q4 + 3) >> 2;
+            E.xa[k] = q4 - 8;
+            E.nq[k] = nq;
+            ok = nq + 4 <= 16;
+        }
+        if (ok) {
+            if (phase == 0) return cudaSuccess;
+            E.ne = m;
+            const long long nrows = (long long)g.NZ * g.NY, th = 16 * m * nrows;
+            k_cpml_row3d<<<dim3((unsigned)((th + 127) / 128), nshots), 128, 0, st>>>(a, n, E, nrows);
+            return cudaGetLastError();
+        }
+    }
     if (ax != 2) {  // z or y: one marching pass after the update (phase 1), unless a z range nears a free surface
         ColRanges R{};
         const int l1 = lo[ax] > 0 ? std::min(N[ax], lo[ax] + 4) : 0;
