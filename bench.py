@@ -104,8 +104,9 @@ def algorithmic_bytes_per_launch(cfg, nshots):
 def launches_per_solve(cfg, nsnap, path):
     """Kernels of ours one solve launches: on the resident path one launch for
     the whole time loop; else the fused step kernel per step in 2D; in 3D the
-    z-march plus, per step, receiver sampling, source injection and two CPML
-    kernels per absorbing axis, plus snapshot kernels; plus the final
+    z-march plus, per step, receiver sampling, source injection and one CPML
+    pass per absorbing axis (the bench volumes' strips are far apart and far
+    from the free surface), plus snapshot kernels; plus the final
     finite-value check."""
     if path == PATH_RESIDENT:
         return 2
@@ -113,7 +114,7 @@ def launches_per_solve(cfg, nsnap, path):
         return cfg["nt"] + 1
     nb = cfg["nb"]
     axes = sum(1 for a in range(3) if nb[2 * a] + nb[2 * a + 1] > 0) if cfg.get("bc") == "cpml" else 0
-    return cfg["nt"] * (1 + 2 * axes + 2) + nsnap + 1
+    return cfg["nt"] * (1 + axes + 2) + nsnap + 1
 
 
 class Clocks:
