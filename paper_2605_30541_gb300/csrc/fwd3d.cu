@@ -546,19 +546,28 @@ __global__ void __launch_bounds__(128) k_cpml_row3d(const StepArgs<float> A, con
     const bool strip = xj + 3 >= 0 && xj < NX && ((nbx0 > 0 && xj < nbx0) || (nbx1 > 0 && xj + 3 >= NX - nbx1));
     const bool pl = live && j < nq + 4, sl = live && j >= 1 && j < nq + 3, ql = live && j >= 2 && j < nq + 2;
 
+    // every load of the lane first (one DRAM round trip), then the arithmetic
+    const bool qs = ql && !(g.fs && z == 0);  // the free-surface row stays zero
+    float *__restrict__ psi = A.psi[2][0] + o;
+    float *__restrict__ zeta = A.zeta[2] + o;
+    float *__restrict__ pn = A.pbuf[(n + 1) & 1] + o;
     const float4 pc = pl ? ld4g(A.pbuf[n & 1] + o) : zero;
-    const float4 pL = shfl4(pc, 1, true), pR = shfl4(pc, 1, false);
-    const float v[12] = {pL.x, pL.y, pL.z, pL.w, pc.x, pc.y, pc.z, pc.w, pR.x, pR.y, pR.z, pR.w};
+    const bool ss = sl && strip;
+    const float4 old = ss ? ld4g(psi) : zero;
     float4 a4 = zero, b4 = zero;
-    if (sl && strip) {
+    if (ss) {
         a4 = ld4g(A.ca[2] + xj);
         b4 = ld4g(A.cb[2] + xj);
     }
+    const float4 zo = qs && strip ? ld4g(zeta) : zero;
+    const float4 c4 = qs ? ld4g(A.ch + (o - (long long)blockIdx.y * g.fstride)) : zero;
+    float4 pv = qs ? ld4g(pn) : zero;
+
+    const float4 pL = shfl4(pc, 1, true), pR = shfl4(pc, 1, false);
+    const float v[12] = {pL.x, pL.y, pL.z, pL.w, pc.x, pc.y, pc.z, pc.w, pR.x, pR.y, pR.z, pR.w};
     // psi^n of the lane's cells
     float4 ps = zero;
-    if (sl && strip) {
-        float *psi = A.psi[2][0] + o;
-        const float4 old = ld4g(psi);
+    if (ss) {
         float r[4];
 #pragma unroll
         for (int k = 0; k < 4; k++)
@@ -569,11 +578,8 @@ __global__ void __launch_bounds__(128) k_cpml_row3d(const StepArgs<float> A, con
         *reinterpret_cast<float4 *>(psi) = ps;
     }
     const float4 sL = shfl4(ps, 1, true), sR = shfl4(ps, 1, false);
-    if (!ql || (g.fs && z == 0)) return;  // the free-surface row stays zero
+    if (!qs) return;
     const float w[12] = {sL.x, sL.y, sL.z, sL.w, ps.x, ps.y, ps.z, ps.w, sR.x, sR.y, sR.z, sR.w};
-    const float4 zo = strip ? ld4g(A.zeta[2] + o) : zero, c4 = ld4g(A.ch + (o - (long long)blockIdx.y * g.fstride));
-    float *pn = A.pbuf[(n + 1) & 1] + o;
-    float4 pv = ld4g(pn);
     float zt[4], add[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -584,7 +590,7 @@ __global__ void __launch_bounds__(128) k_cpml_row3d(const StepArgs<float> A, con
         zt[k] = comp4(b4, k) * comp4(zo, k) + comp4(a4, k) * (d2 + dps);
         add[k] = dps + zt[k];
     }
-    if (strip) *reinterpret_cast<float4 *>(A.zeta[2] + o) = make_float4(zt[0], zt[1], zt[2], zt[3]);
+    if (strip) *reinterpret_cast<float4 *>(zeta) = make_float4(zt[0], zt[1], zt[2], zt[3]);
     pv.x += c4.x * add[0];
     pv.y += c4.y * add[1];
     pv.z += c4.z * add[2];
