@@ -749,8 +749,11 @@ cudaError_t launch_inj3d(const StepArgs<float> &a, int n, int row, const Inj3 *g
     return cudaGetLastError();
 }
 
-// CPML side kernels for one axis: boxes = the two strips (psi) or the two
-// strips widened by 4 cells along the axis (zeta and the update addend).
+// CPML of one axis, called with phase 0 before the update kernel and phase 1
+// after it. The one-pass kernels (k_cpml_col3d for z / y, k_cpml_row3d for x)
+// run at phase 1 and launch nothing at phase 0; strip layouts they do not
+// take use k_psi3d at phase 0 (boxes = the two strips) and k_cpml_add3d at
+// phase 1 (the strips widened by 4 cells along the axis).
 cudaError_t launch_cpml3d(const StepArgs<float> &a, int n, int ax, int phase, int nshots, cudaStream_t st) {
     const Geom &g = a.g;
     const int N[3] = {g.NZ, g.NY, g.NX};
