@@ -1,4 +1,4 @@
-// CPML terms of the 2D adjoint sweep (FP32): the exact transpose of the
+// CPML terms of the 2D adjoint sweep (FP32 or FP64): the exact transpose of the
 // forward CPML recursions of the step kernels, in their scaled variables
 // (psi ~ h psi, zeta ~ h^2 zeta, unscaled stencils D1 / D2, c = (v dt / h)^2):
 //   psi^n  = b psi^{n-1}  + a D1 p^n
@@ -23,15 +23,17 @@
 namespace gsim {
 namespace {
 
+template <typename T>
 struct AxisView {
-    const float *a, *b;  // profile of the axis (zero margins beyond the grid)
+    const T *a, *b;      // profile of the axis (zero margins beyond the grid)
     int N, lo, hi;       // extent and strip widths
     long long stride;    // field elements per step along the axis
 };
 
-__device__ __forceinline__ AxisView axis_view(const StepArgs<float> &A, int ax) {
+template <typename T>
+__device__ __forceinline__ AxisView<T> axis_view(const StepArgs<T> &A, int ax) {
     const Geom &g = A.g;
-    AxisView v;
+    AxisView<T> v;
     v.a = A.ca[ax];
     v.b = A.cb[ax];
     if (ax == 0) {
@@ -48,7 +50,8 @@ __device__ __forceinline__ AxisView axis_view(const StepArgs<float> &A, int ax) 
     return v;
 }
 
-__device__ __forceinline__ bool in_strip(const AxisView &v, int q, int margin) {
+template <typename T>
+__device__ __forceinline__ bool in_strip(const AxisView<T> &v, int q, int margin) {
     return (v.lo > 0 && q < v.lo + margin) || (v.hi > 0 && q >= v.N - v.hi - margin);
 }
 
@@ -74,32 +77,33 @@ __device__ __forceinline__ bool box_cell(const Boxes &B, long long i, int &z, in
 }
 
 // pass A: nu_new, mu (in place) on the strip cells of axes z (0) and x (2)
-__global__ void k_cpml_adj_a(const StepArgs<float> A, CpmlAdjArgs C, int parity, const Boxes B) {
+template <typename T>
+__global__ void k_cpml_adj_a(const StepArgs<T> A, CpmlAdjArgs<T> C, int parity, const Boxes B) {
     const Geom &g = A.g;
     const int shot = blockIdx.y;
     int z, x;
     if (!box_cell(B, blockIdx.x * (long long)blockDim.x + threadIdx.x, z, x)) return;
     const long long o = (long long)shot * g.fstride + cell_off(g, z, 0, x);
-    const float *u = C.u;
+    const T *u = C.u;
 #pragma unroll
     for (int k = 0; k < 2; k++) {
         const int ax = k == 0 ? 0 : 2;
         if (!A.ca[ax]) continue;
-        const AxisView v = axis_view(A, ax);
+        const AxisView<T> v = axis_view(A, ax);
         const int q = ax == 0 ? z : x;
         if (!in_strip(v, q, 0)) continue;
-        const float *nuo = C.nu[k][parity ^ 1];
-        float *nun = C.nu[k][parity];
-        float *mu = C.mu[k];
+        const T *nuo = C.nu[k][parity ^ 1];
+        T *nun = C.nu[k][parity];
+        T *mu = C.mu[k];
         nun[o] = v.b[q] * nuo[o] + u[o];
         // D1 of w = u + a (b nu_old + u) = u + a nu_new, at the neighbours along the axis
-        float d1 = 0.f;
+        T d1 = T(0);
 #pragma unroll
         for (int m = 1; m <= 4; m++) {
             const long long op = o + m * v.stride, om = o - m * v.stride;
-            const float wp = u[op] + v.a[q + m] * (v.b[q + m] * nuo[op] + u[op]);
-            const float wm = u[om] + v.a[q - m] * (v.b[q - m] * nuo[om] + u[om]);
-            const float dm = m == 1 ? float(kD1) : (m == 2 ? float(kD2) : (m == 3 ? float(kD3) : float(kD4)));
+            const T wp = u[op] + v.a[q + m] * (v.b[q + m] * nuo[op] + u[op]);
+            const T wm = u[om] + v.a[q - m] * (v.b[q - m] * nuo[om] + u[om]);
+            const T dm = m == 1 ? T(kD1) : (m == 2 ? T(kD2) : (m == 3 ? T(kD3) : T(kD4)));
             d1 += dm * (wp - wm);
         }
         mu[o] = v.b[q] * mu[o] - d1;
@@ -108,29 +112,30 @@ __global__ void k_cpml_adj_a(const StepArgs<float> A, CpmlAdjArgs C, int parity,
 
 // pass B: ext = sum over the axes of -D1 (a mu) + D2 (a nu) on the cells
 // within 4 of a strip
-__global__ void k_cpml_adj_b(const StepArgs<float> A, CpmlAdjArgs C, int parity, const Boxes B) {
+template <typename T>
+__global__ void k_cpml_adj_b(const StepArgs<T> A, CpmlAdjArgs<T> C, int parity, const Boxes B) {
     const Geom &g = A.g;
     const int shot = blockIdx.y;
     int z, x;
     if (!box_cell(B, blockIdx.x * (long long)blockDim.x + threadIdx.x, z, x)) return;
     const long long o = (long long)shot * g.fstride + cell_off(g, z, 0, x);
-    float ext = 0.f;
+    T ext = T(0);
     bool near = false;
 #pragma unroll
     for (int k = 0; k < 2; k++) {
         const int ax = k == 0 ? 0 : 2;
         if (!A.ca[ax]) continue;
-        const AxisView v = axis_view(A, ax);
+        const AxisView<T> v = axis_view(A, ax);
         const int q = ax == 0 ? z : x;
         if (!in_strip(v, q, 4)) continue;
         near = true;
-        const float *nu = C.nu[k][parity], *mu = C.mu[k];
-        float d1 = 0.f, d2 = float(kC0) * v.a[q] * nu[o];
+        const T *nu = C.nu[k][parity], *mu = C.mu[k];
+        T d1 = T(0), d2 = T(kC0) * v.a[q] * nu[o];
 #pragma unroll
         for (int m = 1; m <= 4; m++) {
             const long long op = o + m * v.stride, om = o - m * v.stride;
-            const float dm = m == 1 ? float(kD1) : (m == 2 ? float(kD2) : (m == 3 ? float(kD3) : float(kD4)));
-            const float cm = m == 1 ? float(kC1) : (m == 2 ? float(kC2) : (m == 3 ? float(kC3) : float(kC4)));
+            const T dm = m == 1 ? T(kD1) : (m == 2 ? T(kD2) : (m == 3 ? T(kD3) : T(kD4)));
+            const T cm = m == 1 ? T(kC1) : (m == 2 ? T(kC2) : (m == 3 ? T(kC3) : T(kC4)));
             d1 += dm * (v.a[q + m] * mu[op] - v.a[q - m] * mu[om]);
             d2 += cm * (v.a[q + m] * nu[op] + v.a[q - m] * nu[om]);
         }
@@ -143,7 +148,8 @@ __global__ void k_cpml_adj_b(const StepArgs<float> A, CpmlAdjArgs C, int parity,
 
 namespace {
 // the strips of the active axes widened by `margin`, as disjoint boxes
-Boxes strip_boxes(const StepArgs<float> &a, int margin) {
+template <typename T>
+Boxes strip_boxes(const StepArgs<T> &a, int margin) {
     const Geom &g = a.g;
     const bool zon = a.ca[0] != nullptr, xon = a.ca[2] != nullptr;
     const int zt = zon && g.nbz0 > 0 ? std::min(g.NZ, g.nbz0 + margin) : 0;
@@ -168,16 +174,23 @@ Boxes strip_boxes(const StepArgs<float> &a, int margin) {
 }
 }  // namespace
 
-cudaError_t launch_cpml_adjoint(const StepArgs<float> &a, const CpmlAdjArgs &c, int parity, int nshots,
+template <typename T>
+cudaError_t launch_cpml_adjoint(const StepArgs<T> &a, const CpmlAdjArgs<T> &c, int parity, int nshots,
                                 cudaStream_t st) {
     const Boxes ba = strip_boxes(a, 0), bb = strip_boxes(a, 4);
     if (ba.n > 0) {
-        k_cpml_adj_a<<<dim3((unsigned)((ba.start[ba.n] + 127) / 128), nshots), 128, 0, st>>>(a, c, parity, ba);
+        k_cpml_adj_a<T><<<dim3((unsigned)((ba.start[ba.n] + 127) / 128), nshots), 128, 0, st>>>(a, c, parity, ba);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    if (bb.n > 0) k_cpml_adj_b<<<dim3((unsigned)((bb.start[bb.n] + 127) / 128), nshots), 128, 0, st>>>(a, c, parity, bb);
+    if (bb.n > 0)
+        k_cpml_adj_b<T><<<dim3((unsigned)((bb.start[bb.n] + 127) / 128), nshots), 128, 0, st>>>(a, c, parity, bb);
     return cudaGetLastError();
 }
+
+template cudaError_t launch_cpml_adjoint<float>(const StepArgs<float> &, const CpmlAdjArgs<float> &, int, int,
+                                                cudaStream_t);
+template cudaError_t launch_cpml_adjoint<double>(const StepArgs<double> &, const CpmlAdjArgs<double> &, int, int,
+                                                 cudaStream_t);
 
 }  // namespace gsim

@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(NTH) k_step2d(const StepArgs<T> A, const int n
             *zp = zt;
             rhs += dps + zt;
         }
+        if (MODE == kModeAdjoint && A.cext) rhs += A.cext[sh + o];  // transposed CPML terms of u
         if (has_inj) rhs += A.src_scale * INJ[lz][lx];
         const T chv = A.ch[o];
         const T pp = pnx[o];

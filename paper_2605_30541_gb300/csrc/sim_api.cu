@@ -275,7 +275,7 @@ struct sim_s {
     void *ubuf = nullptr, *Gbuf = nullptr, *qbuf = nullptr, *ckpt = nullptr, *res = nullptr, *dobs = nullptr;
     // 2D FP32 CPML gradient: multipliers nu [z, x][parity], mu [z, x], the
     // adjoint Laplacian term, and checkpoints of (psi_z, zeta_z, psi_x, zeta_x)
-    float *cnu[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}}, *cmu[2] = {nullptr, nullptr}, *cext = nullptr;
+    void *cnu[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}}, *cmu[2] = {nullptr, nullptr}, *cext = nullptr;
     void *ckcpml = nullptr;
     float *ckcpml_scale = nullptr;
     float *qscale = nullptr, *ckscale = nullptr;
@@ -873,7 +873,6 @@ sim_status points3d(sim_t s, int npts, const double *pos, std::vector<Pt3> &out,
 sim_status forward3d(sim_t s, int nshots, const void *wav, const double *src_pos, int nrec, const double *rec_pos,
                      void *gdev, void *sdev, float *scdev) {
     const sim_desc &d = s->d;
-    const Geom &g = s->g;
     if (d.precision != SIM_FP32) return s->fail(SIM_ERR_UNSUPPORTED, "the 3D path runs in FP32");
     std::vector<Pt3> src, rec;
     if (wav)
@@ -1182,8 +1181,8 @@ void plan_march(const std::vector<MarchMember> &mem, long long max_warps, std::v
     }
     wseg.push_back((int)segs.size());
     if (getenv("GSIM_MARCH_LOG"))
-        fprintf(stderr, "[gsim march] %zu members, %lld strip rows, %d warps (at most %d), %zu segments\n", mem.size(),
-                rows, (int)wseg.size() - 1, max_warps, segs.size());
+        fprintf(stderr, "[gsim march] %zu members, %lld strip rows, %d warps (at most %lld), %zu segments\n",
+                mem.size(), rows, (int)wseg.size() - 1, (long long)max_warps, segs.size());
 }
 
 // Dynamic schedule: the step's work as items of `item` rows of one strip of
@@ -1438,16 +1437,16 @@ sim_status ensure_adjoint(sim_t s) {
     auto A = [&](size_t n) { return rc == SIM_OK ? s->alloc(n, &rc) : nullptr; };
     s->ubuf = A(2 * (size_t)ms * g.fstride * s->esz);
     s->Gbuf = A((size_t)ms * g.fstride * s->esz);
-    if (d.bc == SIM_BC_CPML && g.ndim == 2 && d.precision == SIM_FP32) {
-        const size_t fb = (size_t)ms * g.fstride * sizeof(float);
+    if (d.bc == SIM_BC_CPML && g.ndim == 2) {
+        const size_t fb = (size_t)ms * g.fstride * s->esz;
         for (int k = 0; k < 2; k++) {
-            s->cnu[k][0] = static_cast<float *>(A(fb));
-            s->cnu[k][1] = static_cast<float *>(A(fb));
-            s->cmu[k] = static_cast<float *>(A(fb));
+            s->cnu[k][0] = A(fb);
+            s->cnu[k][1] = A(fb);
+            s->cmu[k] = A(fb);
         }
-        s->cext = static_cast<float *>(A(fb));
+        s->cext = A(fb);
         const size_t ck_t = (size_t)((g.NX + kTileX2 - 1) / kTileX2) * ((g.NZ * g.NY + kTileZ2 - 1) / kTileZ2);
-        s->ckcpml = A((size_t)s->nseg * 4 * ms * ncomp * sizeof(float));
+        s->ckcpml = A((size_t)s->nseg * 4 * ms * ncomp * s->esz);
         s->ckcpml_scale = static_cast<float *>(A((size_t)s->nseg * 4 * ms * ck_t * sizeof(float)));
     }
     s->qbuf = A((size_t)s->seg * ms * g.fstride * s->esz);
@@ -1680,8 +1679,7 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
     const sim_desc &d = s->d;
     const Geom &g = s->g;
     if (g.ndim == 3 && d.precision != SIM_FP32) return s->fail(SIM_ERR_UNSUPPORTED, "the 3D path runs in FP32");
-    if (d.bc == SIM_BC_CPML && (g.ndim == 3 || d.precision != SIM_FP32))
-        return s->fail(SIM_ERR_UNSUPPORTED, "the CPML adjoint runs on 2D FP32 handles");
+    if (d.bc == SIM_BC_CPML && g.ndim == 3) return s->fail(SIM_ERR_UNSUPPORTED, "the CPML adjoint runs on 2D handles");
     if (ckpt_fp16 && d.precision != SIM_FP32) return s->fail(SIM_ERR_ARG, "FP16 checkpoints need an FP32 handle");
     if (nrec < 1) return s->fail(SIM_ERR_ARG, "the misfit needs receivers");
     if (!d_obs || !wavelet || !grad_v) return s->fail(SIM_ERR_ARG, "d_obs, wavelet and grad_v are required");
@@ -1790,7 +1788,7 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
     const bool cpml = d.bc == SIM_BC_CPML;
     if (cpml) {
         adj.bc = SIM_BC_NONE;
-        adj.cext = reinterpret_cast<const T *>(s->cext);
+        adj.cext = static_cast<const T *>(s->cext);
     }
     const int ckcx = ckx, ckcz = ckz;
     auto ckc_ptr = [&](int k, int j) {
@@ -1843,7 +1841,7 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
                 e = cudaMemsetAsync(static_cast<char *>(s->ubuf) + (size_t)g.fstride * s->esz * ms, 0, ub, st);
             if (e == cudaSuccess) e = cudaMemsetAsync(s->Gbuf, 0, (size_t)nshots * g.fstride * s->esz, st);
             if (cpml) {
-                const size_t fb = (size_t)nshots * g.fstride * sizeof(float);
+                const size_t fb = (size_t)nshots * g.fstride * s->esz;
                 for (int k = 0; k < 2 && e == cudaSuccess; k++) {
                     e = cudaMemsetAsync(s->cnu[k][0], 0, fb, st);
                     if (e == cudaSuccess) e = cudaMemsetAsync(s->cnu[k][1], 0, fb, st);
@@ -1868,15 +1866,15 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
                     void *slot = static_cast<char *>(s->qbuf) + (size_t)(k - 1 - n0) * qslot_bytes;
                     float *scl = s->qscale + (size_t)(k - 1 - n0) * q_tiles;
                     if (cpml && k <= d.nt - 1) {  // nu^k, mu^k from u^{k+1}, then their term in u^k
-                        CpmlAdjArgs ca{};
-                        ca.u = reinterpret_cast<const float *>(adj.pbuf[(d.nt - k) & 1]);
+                        CpmlAdjArgs<T> ca{};
+                        ca.u = adj.pbuf[(d.nt - k) & 1];
                         for (int q = 0; q < 2; q++) {
-                            ca.nu[q][0] = s->cnu[q][0];
-                            ca.nu[q][1] = s->cnu[q][1];
-                            ca.mu[q] = s->cmu[q];
+                            ca.nu[q][0] = static_cast<T *>(s->cnu[q][0]);
+                            ca.nu[q][1] = static_cast<T *>(s->cnu[q][1]);
+                            ca.mu[q] = static_cast<T *>(s->cmu[q]);
                         }
-                        ca.ext = s->cext;
-                        e = launch_cpml_adjoint(reinterpret_cast<const StepArgs<float> &>(a), ca, k & 1, nshots, st);
+                        ca.ext = static_cast<T *>(s->cext);
+                        e = launch_cpml_adjoint<T>(a, ca, k & 1, nshots, st);
                     }
                     if (e == cudaSuccess) e = launch_step<T>(s, adj, d.nt - k, nshots, kModeAdjoint, st, slot, scl);
                 }

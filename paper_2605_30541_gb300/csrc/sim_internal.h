@@ -122,7 +122,7 @@ struct StepArgs {
     float *qscale;           // FP16 slots: power-of-two scale per [shot][tile]
     int q_fp16;
     T *G;                    // adjoint sweep: G += u^{n+1} Q'^n, field layout per shot
-    const T *cext;           // adjoint sweep of a CPML problem: per-cell term added to the Laplacian (FP32 path)
+    const T *cext;           // adjoint sweep of a CPML problem: per-cell term added to the Laplacian
 };
 
 // Per-launch facts of one step, resolved on the host (so the kernel does no
@@ -141,13 +141,15 @@ struct StepTime {
 // CPML terms of the 2D adjoint sweep (cpml_adj.cu): the multipliers nu (of
 // zeta) and mu (of psi) of axes z and x, ping-ponged nu by step parity, and
 // the term `ext` the step kernel adds to the Laplacian of u (A.cext).
+template <typename T>
 struct CpmlAdjArgs {
-    const float *u;   // u^{k+1}, field layout per shot
-    float *nu[2][2];  // [z, x][parity]
-    float *mu[2];     // [z, x]
-    float *ext;
+    const T *u;   // u^{k+1}, field layout per shot
+    T *nu[2][2];  // [z, x][parity]
+    T *mu[2];     // [z, x]
+    T *ext;
 };
-cudaError_t launch_cpml_adjoint(const StepArgs<float> &a, const CpmlAdjArgs &c, int parity, int nshots,
+template <typename T>
+cudaError_t launch_cpml_adjoint(const StepArgs<T> &a, const CpmlAdjArgs<T> &c, int parity, int nshots,
                                 cudaStream_t st);
 
 // Step kernel modes: plain forward; forward that records Q'^n; adjoint sweep

@@ -2,7 +2,8 @@
 the FP64 dot-product test, all through the C ABI.
 
 Tolerances (relative L2 over the interior): FP32 storage <= 1e-4, FP16-scaled
-checkpoints and imaging terms <= 1e-2; FP64 dot test <= 1e-6."""
+checkpoints and imaging terms <= 1e-2; FP64 dot test <= 1e-6 (sponge and
+CPML)."""
 import multiprocessing as mp
 import os
 
@@ -195,15 +196,66 @@ def test_cpml_gradient_fp16_checkpoints_within_1e2(pkg):
     assert rel(g16, ref) <= 1e-2
 
 
-def test_cpml_adjoint_fp64_is_reported_unsupported(pkg):
-    c = synth.config_c1(nt=50)
-    sim = pkg.Simulator(c, c["vel"].astype(np.float64), max_rec=3, precision=1)
-    grad = torch.zeros(c["vel"].shape, dtype=torch.float64, device="cuda")
-    with pytest.raises(pkg.SimError) as e:
-        pkg.sim_adjoint(sim.handle, 1, torch.as_tensor(c["wavelet"], dtype=torch.float64, device="cuda"), c["src"],
-                        3, c["rec"][:3], torch.zeros((1, 50, 3), dtype=torch.float64, device="cuda"), None, None, 0,
-                        grad)
-    assert e.value.code == pkg.abi.SIM_ERR_UNSUPPORTED
+def test_cpml_gradient_fp64_matches_oracle_and_finite_differences(pkg):
+    # the transposed CPML recursions in FP64: the oracle's gradient to 1e-10
+    # and central differences of the FP64 misfit on 10 cells
+    cfg, vt, v0, w, src, rec = small_case(nt=300, nshots=1, bc="cpml")
+    d = observed(cfg, vt, w, src, rec)
+    ref, _ = oracle_grad(cfg, v0, w, src, rec, d)
+    g, _ = gpu_grad(pkg, cfg, v0.astype(np.float64), w, src, rec, d, precision=1)
+    assert rel(g, ref) <= 1e-10
+    sim = pkg.Simulator(cfg, v0.astype(np.float64), max_shots=1, max_rec=len(rec), precision=1)
+    rng = np.random.default_rng(4100)
+    vmax = float(v0.max())
+
+    def misfit(v):
+        sim.set_model(v)
+        out = sim.forward(w.astype(np.float64), src, rec)["gather"].cpu().numpy()
+        return 0.5 * np.sum((out - d) ** 2)
+    done = 0
+    while done < 10:
+        # the CPML coefficients follow the model's maximum velocity at set-up
+        # and are constants of the differentiated map: keep the maximum
+        iz, ix = rng.integers(0, v0.shape[0]), rng.integers(0, v0.shape[1])
+        e = 1e-4 * v0[iz, ix]
+        if v0[iz, ix] + 2 * e >= vmax:
+            continue
+        done += 1
+        vp = v0.astype(np.float64).copy()
+        vm = vp.copy()
+        vp[iz, ix] += e
+        vm[iz, ix] -= e
+        fd = (misfit(vp) - misfit(vm)) / (2 * e)
+        assert abs(fd - g[iz, ix]) <= 1e-6 * np.abs(g).max() + 1e-6 * abs(g[iz, ix])
+    sim.close()
+
+
+@pytest.mark.parametrize("fs", [0, 1])
+def test_dot_product_fp64_born_cpml(pkg, fs):
+    # <J dv, dd> = <dv, J^T dd> with CPML (the CPML coefficients held fixed,
+    # as in the forward map): J dv by central differences of the FP64 forward
+    cfg, vt, v0, w, src, rec = small_case(nt=300, nshots=1, fs=fs, bc="cpml")
+    v0 = v0.astype(np.float64)
+    rng = np.random.default_rng(32 + fs)
+    dv = rng.standard_normal(v0.shape)
+    dv[v0 >= v0.max() - 1.0] = 0.0  # the model maximum (which sets the CPML coefficients) stays put
+    sim = pkg.Simulator(cfg, v0, max_shots=1, max_rec=len(rec), precision=1)
+    eps = 1e-5 * np.abs(v0).mean() / np.abs(dv).max()
+
+    def fwd(v):
+        sim.set_model(v)
+        return sim.forward(w.astype(np.float64), src, rec)["gather"].cpu().numpy()[0]
+    g0 = fwd(v0)
+    Jdv = (fwd(v0 + eps * dv) - fwd(v0 - eps * dv)) / (2 * eps)
+    dd = rng.standard_normal(g0.shape) * np.abs(g0).max()
+    grad = torch.zeros(v0.shape, dtype=torch.float64, device="cuda")
+    sim.set_model(v0)
+    pkg.sim_adjoint(sim.handle, 1, torch.as_tensor(w, dtype=torch.float64, device="cuda"), np.ascontiguousarray(src),
+                    len(rec), np.ascontiguousarray(rec),
+                    torch.as_tensor((g0 - dd)[None], device="cuda"), None, None, 0, grad)
+    JTdd = grad.cpu().numpy()
+    lhs, rhs = np.vdot(Jdv, dd), np.vdot(dv, JTdd)
+    assert abs(lhs - rhs) / (np.linalg.norm(Jdv) * np.linalg.norm(dd)) <= 1e-6
     sim.close()
 
 
