@@ -17,9 +17,10 @@
 //  - sponge / no absorption: RB = 4 rows per iteration with a 12-row register
 //    window (rows z-4 .. z+7), so the per-row bookkeeping (waits, copies,
 //    list checks, window shifts) is shared by 16 cells per lane;
-//  - CPML: one row per iteration with a 9-row window. psi_x is recomputed on
-//    the strip +-4 cells from a halo-8 row (the x-derivative of psi_x needs its
-//    neighbours), and psi_z^n at row r needs D1 p^n over rows r-4 .. r+4
+//  - CPML (items within 4 cells of a strip, on CPML slices): one row per
+//    iteration with a 9-row window. psi_x is recomputed on the strip's 4-cell
+//    chunks within x0-4 .. x0+131 from a halo-8 row (the x-derivative of psi_x
+//    needs its neighbours), and psi_z^n at row r needs D1 p^n over rows r-4 .. r+4
 //    while the update of row z needs psi_z^n at rows z-4 .. z+4, so psi_z runs
 //    4 rows ahead of the output row (p^n staged 8 rows ahead) in a second
 //    register window.
