@@ -481,24 +481,46 @@ def test_wavelet_filter_gain_is_the_squared_analog_butterworth():
         assert abs(gain - expect) <= 1e-6 + 1e-6 * expect, (f, gain, expect)
 
 
-@pytest.mark.parametrize("fs", [0, 1])
-def test_gradient_3d_matches_complex_step(fs):
-    # the same adjoint-state gradient on a 3D grid (sponge, 2 receivers planes off the source)
+def _small_3d(bc, fs, nt=60):
     nz, ny, nx, nb = 9, 8, 10, 3
-    cfg = dict(ndim=3, nz=nz, ny=ny, nx=nx, h=10.0, dt=8e-4, nt=60, bc="sponge",
+    cfg = dict(ndim=3, nz=nz, ny=ny, nx=nx, h=10.0, dt=8e-4, nt=nt, bc=bc,
                nb=[0 if fs else nb, nb, nb, nb, nb, nb], free_surface=fs, R=1e-3, f_ref=15.0)
     vel = synth.procedural_3d(nz, ny, nx, 10.0, 23).astype(np.float64)
-    w = synth.ricker(25.0, 0.03, 8e-4, 60, np.float64)
+    if bc == "cpml":
+        cfg["cpml_vmax"] = float(vel.max())  # the CPML coefficients are constants of the map
     src = (45.0, 35.0, 20.0)
     rec = np.array([[10.0 * i, 10.0 * j, 60.0] for i in range(1, 9, 3) for j in range(1, 7, 3)])
+    return cfg, vel, src, rec
+
+
+@pytest.mark.parametrize("bc", ["sponge", "cpml"])
+@pytest.mark.parametrize("fs", [0, 1])
+def test_gradient_3d_matches_complex_step(fs, bc):
+    # the same adjoint-state gradient on a 3D grid (2 receiver planes off the
+    # source); with CPML the transposed psi / zeta recursions of all three axes
+    cfg, vel, src, rec = _small_3d(bc, fs)
+    w = synth.ricker(25.0, 0.03, 8e-4, 60, np.float64)
     d = 0.5 * oracle.forward(cfg, vel * 1.03, w, src=src, rec=rec)["gather"]
     out = oracle.gradient(cfg, vel, w, src, rec, d)
     rng = np.random.default_rng(31)
     eps = 1e-30
-    for _ in range(4):
-        iz, iy, ix = (int(rng.integers(0, s)) for s in vel.shape)
+    edge = [(0, 0, 0), tuple(n - 1 for n in vel.shape)]  # cells whose velocity fills absorbing cells
+    for iz, iy, ix in edge + [tuple(int(rng.integers(0, s)) for s in vel.shape) for _ in range(4)]:
         vc = vel.astype(np.complex128)
         vc[iz, iy, ix] += 1j * eps * vel[iz, iy, ix]
         J = oracle.gradient(cfg, vc, w, src, rec, d, complex_=True)["misfit"]
         cs = J.imag / (eps * vel[iz, iy, ix])
         assert abs(cs - out["grad"][iz, iy, ix]) <= 1e-9 * abs(out["grad"]).max(), (iz, iy, ix)
+
+
+@pytest.mark.parametrize("fs", [0, 1])
+def test_cpml_dot_product_source_to_gather_3d(fs):
+    # w -> g is linear; its transpose is the wavelet gradient at w = 0, d = -y
+    cfg, vel, src, rec = _small_3d("cpml", fs, nt=80)
+    rng = np.random.default_rng(14 + fs)
+    x = rng.standard_normal(cfg["nt"])
+    y = rng.standard_normal((cfg["nt"], len(rec)))
+    Ax = oracle.forward(cfg, vel, x, src=src, rec=rec)["gather"]
+    ATy = oracle.gradient(cfg, vel, np.zeros(cfg["nt"]), src, rec, -y)["grad_wavelet"]
+    lhs, rhs = np.vdot(Ax, y), np.vdot(x, ATy)
+    assert abs(lhs - rhs) / (np.linalg.norm(Ax) * np.linalg.norm(y)) < 1e-12
