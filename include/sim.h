@@ -163,11 +163,10 @@ sim_status sim_forward(sim_t s, int nshots, const void *wavelet, const double *s
  *              handles the imaging terms of a segment stay FP32.
  *   grad_v     [nz][ny][nx]        out: dJ/dv ACCUMULATED (+=) in handle
  *              precision, after an FP64 sum over the shots
- * 2D and 3D (FP32) handles; sponge and no-absorption boundaries; CPML on 2D
- * FP32 and FP64 handles (the exact transpose of the psi / zeta recursions,
- * their state kept with every checkpoint, the CPML coefficients, set from the
- * model maximum by sim_set_model, held fixed as constants of the map),
- * SIM_ERR_UNSUPPORTED for CPML on 3D handles. */
+ * 2D and 3D (FP32) handles; sponge, no-absorption and CPML boundaries (for
+ * CPML the exact transpose of the psi / zeta recursions, their state kept
+ * with every checkpoint, the CPML coefficients, set from the model maximum by
+ * sim_set_model, held fixed as constants of the map). */
 sim_status sim_adjoint(sim_t s, int nshots, const void *wavelet, const double *src_pos,
                        int nrec, const double *rec_pos, const void *d_obs,
                        void *gather_out, double *misfit_out, int ckpt_fp16, void *grad_v);

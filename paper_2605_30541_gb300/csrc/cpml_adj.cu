@@ -1,6 +1,7 @@
-// CPML terms of the 2D adjoint sweep (FP32 or FP64): the exact transpose of the
-// forward CPML recursions of the step kernels, in their scaled variables
-// (psi ~ h psi, zeta ~ h^2 zeta, unscaled stencils D1 / D2, c = (v dt / h)^2):
+// CPML terms of the adjoint sweep (2D: FP32 or FP64; 3D: FP32): the exact
+// transpose of the forward CPML recursions, in the scaled variables of the
+// step kernels (psi ~ h psi, zeta ~ h^2 zeta, unscaled stencils D1 / D2,
+// c = (v dt / h)^2), per absorbing axis:
 //   psi^n  = b psi^{n-1}  + a D1 p^n
 //   zeta^n = b zeta^{n-1} + a (D2 p^n + D1 psi^n),  addend D1 psi^n + zeta^n.
 // With the adjoint field u = c lambda and multipliers nu (of zeta) and mu (of
@@ -10,11 +11,13 @@
 //   u^k  = (the sponge-free update of u) + c [-D1 (a mu^k) + D2 (a nu^k)]
 // (D1^T = -D1 and D2^T = D2 on the zero-ghost grid; a free surface never
 // meets a z strip, so its odd mirror does not enter). Pass A updates nu and
-// mu on the strip cells of each absorbing axis; pass B writes the bracket,
-// summed over the axes, on the cells within 4 of a strip into `ext`, which
-// the step kernel adds to the Laplacian of u^{k+1}. a = b = 0 outside the
-// strips, so nu and mu matter only there and the bracket vanishes beyond 4
-// cells from them.
+// mu on the strip cells of each absorbing axis; pass B forms the bracket,
+// summed over the axes, on the cells within 4 of a strip. In 2D it goes to
+// `ext`, which the step kernel adds to the Laplacian of u^{k+1}; in 3D pass B
+// runs after the update and adds c times the bracket to u^k itself and, as
+// the update kernel does for the rest of u^k, its product with the recorded
+// imaging term to G. a = b = 0 outside the strips, so nu and mu matter only
+// there and the bracket vanishes beyond 4 cells from them.
 #include <algorithm>
 
 #include "sim_internal.h"
@@ -41,6 +44,11 @@ __device__ __forceinline__ AxisView<T> axis_view(const StepArgs<T> &A, int ax) {
         v.lo = g.nbz0;
         v.hi = g.nbz1;
         v.stride = (long long)g.PY * g.P;
+    } else if (ax == 1) {
+        v.N = g.NY;
+        v.lo = g.nby0;
+        v.hi = g.nby1;
+        v.stride = g.P;
     } else {
         v.N = g.NX;
         v.lo = g.nbx0;
@@ -55,46 +63,48 @@ __device__ __forceinline__ bool in_strip(const AxisView<T> &v, int q, int margin
     return (v.lo > 0 && q < v.lo + margin) || (v.hi > 0 && q >= v.N - v.hi - margin);
 }
 
-// The launch covers the union of the strips (widened by a margin) as up to 4
-// disjoint boxes: the top and bottom row bands over the full width, then the
-// left and right column bands of the rows between; thread i -> (box, z, x),
-// x fastest.
+// The launch covers the union of the strips (widened by a margin) as up to 6
+// disjoint boxes: the top and bottom z bands over all (y, x), then in the z
+// range between them the low and high y bands over all x, then in the (z, y)
+// range between those the low and high x bands; thread i -> (box, z, y, x),
+// x fastest, then y.
 struct Boxes {
     int n;
-    int z0[4], z1[4], x0[4], x1[4];
-    long long start[5];
+    int z0[6], z1[6], y0[6], y1[6], x0[6], x1[6];
+    long long start[7];
 };
 
-__device__ __forceinline__ bool box_cell(const Boxes &B, long long i, int &z, int &x) {
+__device__ __forceinline__ bool box_cell(const Boxes &B, long long i, int &z, int &y, int &x) {
     if (i >= B.start[B.n]) return false;
     int b = 0;
     while (b + 1 < B.n && B.start[b + 1] <= i) b++;
     const long long r = i - B.start[b];
-    const int w = B.x1[b] - B.x0[b];
-    z = B.z0[b] + (int)(r / w);
-    x = B.x0[b] + (int)(r % w);
+    const int w = B.x1[b] - B.x0[b], h = B.y1[b] - B.y0[b];
+    const long long t = r / w;
+    x = B.x0[b] + (int)(r - t * w);
+    y = B.y0[b] + (int)(t % h);
+    z = B.z0[b] + (int)(t / h);
     return true;
 }
 
-// pass A: nu_new, mu (in place) on the strip cells of axes z (0) and x (2)
+// pass A: nu_new, mu (in place) on the strip cells of every absorbing axis
 template <typename T>
 __global__ void k_cpml_adj_a(const StepArgs<T> A, CpmlAdjArgs<T> C, int parity, const Boxes B) {
     const Geom &g = A.g;
     const int shot = blockIdx.y;
-    int z, x;
-    if (!box_cell(B, blockIdx.x * (long long)blockDim.x + threadIdx.x, z, x)) return;
-    const long long o = (long long)shot * g.fstride + cell_off(g, z, 0, x);
+    int z, y, x;
+    if (!box_cell(B, blockIdx.x * (long long)blockDim.x + threadIdx.x, z, y, x)) return;
+    const long long o = (long long)shot * g.fstride + cell_off(g, z, y, x);
     const T *u = C.u;
 #pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const int ax = k == 0 ? 0 : 2;
+    for (int ax = 0; ax < 3; ax++) {
         if (!A.ca[ax]) continue;
         const AxisView<T> v = axis_view(A, ax);
-        const int q = ax == 0 ? z : x;
+        const int q = ax == 0 ? z : (ax == 1 ? y : x);
         if (!in_strip(v, q, 0)) continue;
-        const T *nuo = C.nu[k][parity ^ 1];
-        T *nun = C.nu[k][parity];
-        T *mu = C.mu[k];
+        const T *nuo = C.nu[ax][parity ^ 1];
+        T *nun = C.nu[ax][parity];
+        T *mu = C.mu[ax];
         nun[o] = v.b[q] * nuo[o] + u[o];
         // D1 of w = u + a (b nu_old + u) = u + a nu_new, at the neighbours along the axis
         T d1 = T(0);
@@ -110,26 +120,26 @@ __global__ void k_cpml_adj_a(const StepArgs<T> A, CpmlAdjArgs<T> C, int parity, 
     }
 }
 
-// pass B: ext = sum over the axes of -D1 (a mu) + D2 (a nu) on the cells
-// within 4 of a strip
+// pass B: the sum over the axes of -D1 (a mu) + D2 (a nu) on the cells
+// within 4 of a strip, into ext (C.uo == NULL) or, times c, into u^k (and
+// its product with the imaging term into G)
 template <typename T>
 __global__ void k_cpml_adj_b(const StepArgs<T> A, CpmlAdjArgs<T> C, int parity, const Boxes B) {
     const Geom &g = A.g;
     const int shot = blockIdx.y;
-    int z, x;
-    if (!box_cell(B, blockIdx.x * (long long)blockDim.x + threadIdx.x, z, x)) return;
-    const long long o = (long long)shot * g.fstride + cell_off(g, z, 0, x);
+    int z, y, x;
+    if (!box_cell(B, blockIdx.x * (long long)blockDim.x + threadIdx.x, z, y, x)) return;
+    const long long cell = cell_off(g, z, y, x), o = (long long)shot * g.fstride + cell;
     T ext = T(0);
     bool near = false;
 #pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const int ax = k == 0 ? 0 : 2;
+    for (int ax = 0; ax < 3; ax++) {
         if (!A.ca[ax]) continue;
         const AxisView<T> v = axis_view(A, ax);
-        const int q = ax == 0 ? z : x;
+        const int q = ax == 0 ? z : (ax == 1 ? y : x);
         if (!in_strip(v, q, 4)) continue;
         near = true;
-        const T *nu = C.nu[k][parity], *mu = C.mu[k];
+        const T *nu = C.nu[ax][parity], *mu = C.mu[ax];
         T d1 = T(0), d2 = T(kC0) * v.a[q] * nu[o];
 #pragma unroll
         for (int m = 1; m <= 4; m++) {
@@ -141,37 +151,49 @@ __global__ void k_cpml_adj_b(const StepArgs<T> A, CpmlAdjArgs<T> C, int parity, 
         }
         ext += d2 - d1;
     }
-    if (near) C.ext[o] = ext;
+    if (!near) return;
+    if (!C.uo) {
+        C.ext[o] = ext;
+    } else if (!(g.fs && z == 0)) {  // the free-surface row of u stays zero
+        const T du = A.ch[cell] * ext;
+        C.uo[o] += du;
+        C.G[o] += du * C.q[o];
+    }
 }
 
-}  // namespace
-
-namespace {
 // the strips of the active axes widened by `margin`, as disjoint boxes
 template <typename T>
 Boxes strip_boxes(const StepArgs<T> &a, int margin) {
     const Geom &g = a.g;
-    const bool zon = a.ca[0] != nullptr, xon = a.ca[2] != nullptr;
-    const int zt = zon && g.nbz0 > 0 ? std::min(g.NZ, g.nbz0 + margin) : 0;
-    const int zb = zon && g.nbz1 > 0 ? std::max(zt, g.NZ - g.nbz1 - margin) : g.NZ;
-    const int xl = xon && g.nbx0 > 0 ? std::min(g.NX, g.nbx0 + margin) : 0;
-    const int xr = xon && g.nbx1 > 0 ? std::max(xl, g.NX - g.nbx1 - margin) : g.NX;
+    const int N[3] = {g.NZ, g.NY, g.NX};
+    const int lo[3] = {g.nbz0, g.nby0, g.nbx0}, hi[3] = {g.nbz1, g.nby1, g.nbx1};
+    int b0[3], b1[3];  // per axis: [0, b0) and [b1, N) are the widened strips
+    for (int ax = 0; ax < 3; ax++) {
+        const bool on = a.ca[ax] != nullptr;
+        b0[ax] = on && lo[ax] > 0 ? std::min(N[ax], lo[ax] + margin) : 0;
+        b1[ax] = on && hi[ax] > 0 ? std::max(b0[ax], N[ax] - hi[ax] - margin) : N[ax];
+    }
     Boxes B{};
-    auto add = [&](int z0, int z1, int x0, int x1) {
-        if (z1 <= z0 || x1 <= x0) return;
+    auto add = [&](int z0, int z1, int y0, int y1, int x0, int x1) {
+        if (z1 <= z0 || y1 <= y0 || x1 <= x0) return;
         B.z0[B.n] = z0;
         B.z1[B.n] = z1;
+        B.y0[B.n] = y0;
+        B.y1[B.n] = y1;
         B.x0[B.n] = x0;
         B.x1[B.n] = x1;
-        B.start[B.n + 1] = B.start[B.n] + (long long)(z1 - z0) * (x1 - x0);
+        B.start[B.n + 1] = B.start[B.n] + (long long)(z1 - z0) * (y1 - y0) * (x1 - x0);
         B.n++;
     };
-    add(0, zt, 0, g.NX);
-    add(zb, g.NZ, 0, g.NX);
-    add(zt, zb, 0, xl);
-    add(zt, zb, xr, g.NX);
+    add(0, b0[0], 0, N[1], 0, N[2]);
+    add(b1[0], N[0], 0, N[1], 0, N[2]);
+    add(b0[0], b1[0], 0, b0[1], 0, N[2]);
+    add(b0[0], b1[0], b1[1], N[1], 0, N[2]);
+    add(b0[0], b1[0], b0[1], b1[1], 0, b0[2]);
+    add(b0[0], b1[0], b0[1], b1[1], b1[2], N[2]);
     return B;
 }
+
 }  // namespace
 
 template <typename T>

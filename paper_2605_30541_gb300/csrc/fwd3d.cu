@@ -328,7 +328,8 @@ __global__ void k_psi3d(const StepArgs<float> A, const int n, const int ax, cons
 
 // zeta^n = b zeta^{n-1} + a (D2 p^n + D1 psi^n); p^{n+1} += c (D1 psi^n + zeta^n)
 // on the strips of one axis widened by 4 cells (where D1 psi is non-zero).
-__global__ void k_cpml_add3d(const StepArgs<float> A, const int n, const int ax, const Box b0, const Box b1) {
+__global__ void k_cpml_add3d(const StepArgs<float> A, const int n, const int ax, const Box b0, const Box b1,
+                             float *qs) {
     const Geom &g = A.g;
     const long long s = axis_stride(g, ax);
     const long long n0 = box_items(b0), n1 = box_items(b1);
@@ -372,6 +373,14 @@ __global__ void k_cpml_add3d(const StepArgs<float> A, const int n, const int ax,
         pv.z += ch.z * (dps.z + zt.z);
         pv.w += ch.w * (dps.w + zt.w);
         *reinterpret_cast<float4 *>(pn + o) = pv;
+        if (qs) {  // record mode: the addend is part of the Laplacian in the imaging term
+            float4 qv = ld4g(qs + sh + o);
+            qv.x -= dps.x + zt.x;
+            qv.y -= dps.y + zt.y;
+            qv.z -= dps.z + zt.z;
+            qv.w -= dps.w + zt.w;
+            *reinterpret_cast<float4 *>(qs + sh + o) = qv;
+        }
     }
 }
 
@@ -399,7 +408,7 @@ struct ColRanges {
 };
 
 __global__ void __launch_bounds__(128) k_cpml_col3d(const StepArgs<float> A, const int n, const int ax,
-                                                    const ColRanges R, const int ncols) {
+                                                    const ColRanges R, const int ncols, float *qs) {
     const Geom &g = A.g;
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (tid >= (long long)R.n * ncols) return;
@@ -418,6 +427,7 @@ __global__ void __launch_bounds__(128) k_cpml_col3d(const StepArgs<float> A, con
     float *__restrict__ psi = A.psi[ax][0] + sh + o0;
     float *__restrict__ zeta = A.zeta[ax] + sh + o0;
     const float *__restrict__ ch = A.ch + o0;
+    float *qcol = qs ? qs + sh + o0 : nullptr;  // record mode: imaging term of the step
     const float *ca = A.ca[ax], *cb = A.cb[ax];
     const bool skip_row = g.fs && ax == 1 && u == 0;  // the free-surface row stays zero
     auto strip = [&](int r) { return (lo > 0 && r >= 0 && r < lo) || (hi > 0 && r >= N - hi && r < N); };
@@ -500,6 +510,14 @@ __global__ void __launch_bounds__(128) k_cpml_col3d(const StepArgs<float> A, con
             pv.z += c4.z * add[2];
             pv.w += c4.w * add[3];
             *reinterpret_cast<float4 *>(pn + (long long)q * s) = pv;
+            if (qcol) {  // the addend is part of the Laplacian in the imaging term
+                float4 qv = ld4g(qcol + (long long)q * s);
+                qv.x -= add[0];
+                qv.y -= add[1];
+                qv.z -= add[2];
+                qv.w -= add[3];
+                *reinterpret_cast<float4 *>(qcol + (long long)q * s) = qv;
+            }
         }
 #pragma unroll
         for (int m = 0; m < 12; m++) P[m] = P[m + 1];
@@ -530,7 +548,7 @@ __device__ __forceinline__ float4 shfl4(const float4 v, int d, bool up) {
 }
 
 __global__ void __launch_bounds__(128) k_cpml_row3d(const StepArgs<float> A, const int n, const XEnds E,
-                                                    const long long nrows) {
+                                                    const long long nrows, float *qrec) {
     const Geom &g = A.g;
     const long long hw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 4;
     const int j = threadIdx.x & 15;
@@ -596,6 +614,14 @@ __global__ void __launch_bounds__(128) k_cpml_row3d(const StepArgs<float> A, con
     pv.z += c4.z * add[2];
     pv.w += c4.w * add[3];
     *reinterpret_cast<float4 *>(pn) = pv;
+    if (qrec) {  // record mode: the addend is part of the Laplacian in the imaging term
+        float4 qv = ld4g(qrec + o);
+        qv.x -= add[0];
+        qv.y -= add[1];
+        qv.z -= add[2];
+        qv.w -= add[3];
+        *reinterpret_cast<float4 *>(qrec + o) = qv;
+    }
 }
 
 // ---------------------------------------------------------------- points (3D)
@@ -750,11 +776,13 @@ cudaError_t launch_inj3d(const StepArgs<float> &a, int n, int row, const Inj3 *g
 }
 
 // CPML of one axis, called with phase 0 before the update kernel and phase 1
-// after it. The one-pass kernels (k_cpml_col3d for z / y, k_cpml_row3d for x)
+// after it; with `qs` (record mode of the gradient) the addend is also taken
+// off the step's imaging term, as it is part of the Laplacian there. The one-pass kernels (k_cpml_col3d for z / y, k_cpml_row3d for x)
 // run at phase 1 and launch nothing at phase 0; strip layouts they do not
 // take use k_psi3d at phase 0 (boxes = the two strips) and k_cpml_add3d at
 // phase 1 (the strips widened by 4 cells along the axis).
-cudaError_t launch_cpml3d(const StepArgs<float> &a, int n, int ax, int phase, int nshots, cudaStream_t st) {
+cudaError_t launch_cpml3d(const StepArgs<float> &a, int n, int ax, int phase, int nshots, cudaStream_t st,
+                          float *qs) {
     const Geom &g = a.g;
     const int N[3] = {g.NZ, g.NY, g.NX};
     const int lo[3] = {g.nbz0, g.nby0, g.nbx0}, hi[3] = {g.nbz1, g.nby1, g.nbx1};
@@ -775,7 +803,7 @@ cudaError_t launch_cpml3d(const StepArgs<float> &a, int n, int ax, int phase, in
             if (phase == 0) return cudaSuccess;
             E.ne = m;
             const long long nrows = (long long)g.NZ * g.NY, th = 16 * m * nrows;
-            k_cpml_row3d<<<dim3((unsigned)((th + 127) / 128), nshots), 128, 0, st>>>(a, n, E, nrows);
+            k_cpml_row3d<<<dim3((unsigned)((th + 127) / 128), nshots), 128, 0, st>>>(a, n, E, nrows, qs);
             return cudaGetLastError();
         }
     }
@@ -796,7 +824,7 @@ cudaError_t launch_cpml3d(const StepArgs<float> &a, int n, int ax, int phase, in
             if (phase == 0 || R.n == 0) return cudaSuccess;
             const int ncols = (ax == 0 ? g.NY : g.NZ) * ((g.NX + 3) >> 2);
             const long long th = (long long)R.n * ncols;
-            k_cpml_col3d<<<dim3((unsigned)((th + 127) / 128), nshots), 128, 0, st>>>(a, n, ax, R, ncols);
+            k_cpml_col3d<<<dim3((unsigned)((th + 127) / 128), nshots), 128, 0, st>>>(a, n, ax, R, ncols, qs);
             return cudaGetLastError();
         }
     }
@@ -835,7 +863,7 @@ cudaError_t launch_cpml3d(const StepArgs<float> &a, int n, int ax, int phase, in
     if (items <= 0) return cudaSuccess;
     const int blocks = (int)std::min<long long>((items + 255) / 256, 152 * 16);
     if (phase == 0) k_psi3d<<<dim3(blocks, nshots), 256, 0, st>>>(a, n, ax, B0, B1);
-    else k_cpml_add3d<<<dim3(blocks, nshots), 256, 0, st>>>(a, n, ax, B0, B1);
+    else k_cpml_add3d<<<dim3(blocks, nshots), 256, 0, st>>>(a, n, ax, B0, B1, qs);
     return cudaGetLastError();
 }
 

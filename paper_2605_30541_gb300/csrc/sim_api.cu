@@ -275,7 +275,8 @@ struct sim_s {
     void *ubuf = nullptr, *Gbuf = nullptr, *qbuf = nullptr, *ckpt = nullptr, *res = nullptr, *dobs = nullptr;
     // 2D FP32 CPML gradient: multipliers nu [z, x][parity], mu [z, x], the
     // adjoint Laplacian term, and checkpoints of (psi_z, zeta_z, psi_x, zeta_x)
-    void *cnu[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}}, *cmu[2] = {nullptr, nullptr}, *cext = nullptr;
+    void *cnu[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}}, *cmu[3] = {nullptr, nullptr, nullptr};
+    void *cext = nullptr;
     void *ckcpml = nullptr;
     float *ckcpml_scale = nullptr;
     float *qscale = nullptr, *ckscale = nullptr;
@@ -1423,6 +1424,25 @@ sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src
 
 constexpr int kResidBlocks = 1024;
 
+// Checkpoint fields of the CPML state: psi and zeta of each axis (2D: z and
+// x, 4 fields; 3D: 6).
+int cpml_ckpt_fields(const Geom &g) { return g.ndim == 3 ? 6 : 4; }
+
+// Zero the CPML multipliers (both parities) and the 2D bracket of `nshots`
+// shots before an adjoint sweep.
+cudaError_t reset_cpml_adjoint(const sim_s *s, int nshots, cudaStream_t st) {
+    const size_t fb = (size_t)nshots * s->g.fstride * s->esz;
+    cudaError_t e = cudaSuccess;
+    for (int ax = 0; ax < 3 && e == cudaSuccess; ax++) {
+        if (!s->cnu[ax][0]) continue;
+        e = cudaMemsetAsync(s->cnu[ax][0], 0, fb, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->cnu[ax][1], 0, fb, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->cmu[ax], 0, fb, st);
+    }
+    if (e == cudaSuccess && s->cext) e = cudaMemsetAsync(s->cext, 0, fb, st);
+    return e;
+}
+
 sim_status ensure_adjoint(sim_t s) {
     if (s->adj_ready) return SIM_OK;
     const sim_desc &d = s->d;
@@ -1437,17 +1457,19 @@ sim_status ensure_adjoint(sim_t s) {
     auto A = [&](size_t n) { return rc == SIM_OK ? s->alloc(n, &rc) : nullptr; };
     s->ubuf = A(2 * (size_t)ms * g.fstride * s->esz);
     s->Gbuf = A((size_t)ms * g.fstride * s->esz);
-    if (d.bc == SIM_BC_CPML && g.ndim == 2) {
+    if (d.bc == SIM_BC_CPML) {  // multipliers of each absorbing axis, and psi / zeta in every checkpoint
         const size_t fb = (size_t)ms * g.fstride * s->esz;
-        for (int k = 0; k < 2; k++) {
-            s->cnu[k][0] = A(fb);
-            s->cnu[k][1] = A(fb);
-            s->cmu[k] = A(fb);
+        for (int ax = 0; ax < 3; ax++) {
+            if (!s->psi[ax][0]) continue;
+            s->cnu[ax][0] = A(fb);
+            s->cnu[ax][1] = A(fb);
+            s->cmu[ax] = A(fb);
         }
-        s->cext = A(fb);
+        if (g.ndim == 2) s->cext = A(fb);
+        const int nf = cpml_ckpt_fields(g);
         const size_t ck_t = (size_t)((g.NX + kTileX2 - 1) / kTileX2) * ((g.NZ * g.NY + kTileZ2 - 1) / kTileZ2);
-        s->ckcpml = A((size_t)s->nseg * 4 * ms * ncomp * s->esz);
-        s->ckcpml_scale = static_cast<float *>(A((size_t)s->nseg * 4 * ms * ck_t * sizeof(float)));
+        s->ckcpml = A((size_t)s->nseg * nf * ms * ncomp * s->esz);
+        s->ckcpml_scale = static_cast<float *>(A((size_t)s->nseg * nf * ms * ck_t * sizeof(float)));
     }
     s->qbuf = A((size_t)s->seg * ms * g.fstride * s->esz);
     s->qscale = static_cast<float *>(A((size_t)s->seg * ms * ntiles * sizeof(float)));
@@ -1575,6 +1597,36 @@ sim_status adjoint3d(sim_t s, int nshots, const void *wavelet, const double *src
     StepArgs<float> a = step_args<float>(s);
     a.sample = 1;
     a.nsnap = 0;
+    // CPML: the passes of each absorbing axis run around the update as in a
+    // forward solve (in the recompute they also take the addend off the
+    // imaging term); psi (kept in place in psi[ax][0]) and zeta of every axis
+    // join each checkpoint; the sweep adds the transposed recursions'
+    // term to u^k after each update (cpml_adj.cu)
+    const bool cpml = d.bc == SIM_BC_CPML;
+    const int on[3] = {s->psi[0][0] != nullptr, s->psi[1][0] != nullptr, s->psi[2][0] != nullptr};
+    const int nfc = cpml_ckpt_fields(g);
+    auto ckc_ptr = [&](int k, int j) {
+        return static_cast<char *>(s->ckcpml) + ((size_t)k * nfc + j) * ck_state * (ckpt_fp16 ? 2 : sizeof(float));
+    };
+    auto ckc_scale = [&](int k, int j) { return s->ckcpml_scale + ((size_t)k * nfc + j) * ck_tiles; };
+    auto cpml_ckpt = [&](int k, bool store, cudaStream_t st) {  // fields j = 2 ax (psi), 2 ax + 1 (zeta)
+        cudaError_t e = cudaSuccess;
+        for (int j = 0; j < 6 && e == cudaSuccess; j++) {
+            if (!on[j / 2]) continue;
+            float *f = static_cast<float *>(j % 2 == 0 ? s->psi[j / 2][0] : s->zeta[j / 2]);
+            e = store ? launch_store_state<float>(g, f, ckc_ptr(k, j), ckc_scale(k, j), ckpt_fp16, nshots, ncomp, ckx,
+                                                  ckz, st)
+                      : launch_load_state<float>(g, f, ckc_ptr(k, j), ckc_scale(k, j), ckpt_fp16, nshots, ncomp, ckx,
+                                                 ckz, st);
+        }
+        return e;
+    };
+    auto cpml_pass = [&](int n, int phase, float *qslot, cudaStream_t st) {
+        cudaError_t e = cudaSuccess;
+        for (int ax = 0; ax < 3 && e == cudaSuccess; ax++)
+            if (on[ax]) e = launch_cpml3d(a, n, ax, phase, nshots, st, qslot);
+        return e;
+    };
     StepArgs<float> adj = a;
     adj.pbuf[0] = static_cast<float *>(s->ubuf);
     adj.pbuf[1] = static_cast<float *>(s->ubuf) + (long long)ms * g.fstride;
@@ -1595,10 +1647,13 @@ sim_status adjoint3d(sim_t s, int nshots, const void *wavelet, const double *src
                     if (e == cudaSuccess)
                         e = launch_store_state<float>(g, a.pbuf[(n + 1) & 1], ck_ptr(k, 0), ck_scale(k, 0),
                                                       ckpt_fp16, nshots, ncomp, ckx, ckz, st);
+                    if (e == cudaSuccess && cpml) e = cpml_ckpt(k, true, st);
                 }
                 if (e == cudaSuccess)
                     e = launch_sample3d(a, step_time(s, a, n, kModeForward, nullptr, nullptr), r3, nrec, nshots, st);
+                if (e == cudaSuccess && cpml) e = cpml_pass(n, 0, nullptr, st);
                 if (e == cudaSuccess) e = launch_step3d(a, n, 1, zc, nshots, st, true, kModeForward);
+                if (e == cudaSuccess && cpml) e = cpml_pass(n, 1, nullptr, st);
                 if (e == cudaSuccess)
                     e = launch_inj3d(a, n, n, s->src3g, nsg, s->src3e, 0, nshots, kModeForward, nullptr, nullptr, st);
             }
@@ -1611,6 +1666,7 @@ sim_status adjoint3d(sim_t s, int nshots, const void *wavelet, const double *src
                 e = cudaMemsetAsync(static_cast<char *>(s->ubuf) + (size_t)g.fstride * sizeof(float) * ms, 0, ub,
                                     st);
             if (e == cudaSuccess) e = cudaMemsetAsync(s->Gbuf, 0, ub, st);
+            if (e == cudaSuccess && cpml) e = reset_cpml_adjoint(s, nshots, st);
             for (int sgi = s->nseg - 1; sgi >= 0 && e == cudaSuccess; sgi--) {
                 const int n0 = sgi * L, n1 = std::min(n0 + L, d.nt);
                 e = launch_load_state<float>(g, a.pbuf[n0 & 1], ck_ptr(sgi, 1), ck_scale(sgi, 1), ckpt_fp16, nshots,
@@ -1618,9 +1674,12 @@ sim_status adjoint3d(sim_t s, int nshots, const void *wavelet, const double *src
                 if (e == cudaSuccess)
                     e = launch_load_state<float>(g, a.pbuf[(n0 + 1) & 1], ck_ptr(sgi, 0), ck_scale(sgi, 0),
                                                  ckpt_fp16, nshots, ncomp, ckx, ckz, st);
+                if (e == cudaSuccess && cpml) e = cpml_ckpt(sgi, false, st);
                 for (int n = n0; n < n1 && e == cudaSuccess; n++) {
                     float *slot = static_cast<float *>(s->qbuf) + (size_t)(n - n0) * qslot;
-                    e = launch_step3d(a, n, 1, zc, nshots, st, true, kModeRecord, slot, nullptr);
+                    if (cpml) e = cpml_pass(n, 0, nullptr, st);
+                    if (e == cudaSuccess) e = launch_step3d(a, n, 1, zc, nshots, st, true, kModeRecord, slot, nullptr);
+                    if (e == cudaSuccess && cpml) e = cpml_pass(n, 1, slot, st);
                     if (e == cudaSuccess)
                         e = launch_inj3d(a, n, n, s->src3g, nsg, s->src3e, 0, nshots, kModeRecord, slot, nullptr, st);
                 }
@@ -1630,6 +1689,19 @@ sim_status adjoint3d(sim_t s, int nshots, const void *wavelet, const double *src
                     e = launch_step3d(adj, n, 1, zc, nshots, st, true, kModeAdjoint, slot, Gs);
                     if (e == cudaSuccess)
                         e = launch_inj3d(adj, n, k, s->res3g, nrg, s->res3e, 1, nshots, kModeAdjoint, slot, Gs, st);
+                    if (e == cudaSuccess && cpml && k <= d.nt - 1) {  // nu^k, mu^k from u^{k+1}; c [.] into u^k
+                        CpmlAdjArgs<float> ca{};
+                        ca.u = adj.pbuf[(d.nt - k) & 1];
+                        for (int ax = 0; ax < 3; ax++) {
+                            ca.nu[ax][0] = static_cast<float *>(s->cnu[ax][0]);
+                            ca.nu[ax][1] = static_cast<float *>(s->cnu[ax][1]);
+                            ca.mu[ax] = static_cast<float *>(s->cmu[ax]);
+                        }
+                        ca.uo = adj.pbuf[(n + 1) & 1];
+                        ca.q = slot;
+                        ca.G = Gs;
+                        e = launch_cpml_adjoint<float>(a, ca, k & 1, nshots, st);
+                    }
                 }
             }
             if (e == cudaSuccess) e = cudaMemsetAsync(s->acc, 0, nint * sizeof(double), st);
@@ -1679,7 +1751,6 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
     const sim_desc &d = s->d;
     const Geom &g = s->g;
     if (g.ndim == 3 && d.precision != SIM_FP32) return s->fail(SIM_ERR_UNSUPPORTED, "the 3D path runs in FP32");
-    if (d.bc == SIM_BC_CPML && g.ndim == 3) return s->fail(SIM_ERR_UNSUPPORTED, "the CPML adjoint runs on 2D handles");
     if (ckpt_fp16 && d.precision != SIM_FP32) return s->fail(SIM_ERR_ARG, "FP16 checkpoints need an FP32 handle");
     if (nrec < 1) return s->fail(SIM_ERR_ARG, "the misfit needs receivers");
     if (!d_obs || !wavelet || !grad_v) return s->fail(SIM_ERR_ARG, "d_obs, wavelet and grad_v are required");
@@ -1840,15 +1911,7 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
             if (e == cudaSuccess)
                 e = cudaMemsetAsync(static_cast<char *>(s->ubuf) + (size_t)g.fstride * s->esz * ms, 0, ub, st);
             if (e == cudaSuccess) e = cudaMemsetAsync(s->Gbuf, 0, (size_t)nshots * g.fstride * s->esz, st);
-            if (cpml) {
-                const size_t fb = (size_t)nshots * g.fstride * s->esz;
-                for (int k = 0; k < 2 && e == cudaSuccess; k++) {
-                    e = cudaMemsetAsync(s->cnu[k][0], 0, fb, st);
-                    if (e == cudaSuccess) e = cudaMemsetAsync(s->cnu[k][1], 0, fb, st);
-                    if (e == cudaSuccess) e = cudaMemsetAsync(s->cmu[k], 0, fb, st);
-                }
-                if (e == cudaSuccess) e = cudaMemsetAsync(s->cext, 0, fb, st);
-            }
+            if (cpml) e = reset_cpml_adjoint(s, nshots, st);
             for (int sgi = s->nseg - 1; sgi >= 0 && e == cudaSuccess; sgi--) {
                 const int n0 = sgi * L, n1 = std::min(n0 + L, d.nt);
                 e = launch_load_state<T>(g, a.pbuf[n0 & 1], ck_ptr(sgi, 1), ck_scale(sgi, 1), ckpt_fp16, nshots,
@@ -1868,10 +1931,10 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
                     if (cpml && k <= d.nt - 1) {  // nu^k, mu^k from u^{k+1}, then their term in u^k
                         CpmlAdjArgs<T> ca{};
                         ca.u = adj.pbuf[(d.nt - k) & 1];
-                        for (int q = 0; q < 2; q++) {
-                            ca.nu[q][0] = static_cast<T *>(s->cnu[q][0]);
-                            ca.nu[q][1] = static_cast<T *>(s->cnu[q][1]);
-                            ca.mu[q] = static_cast<T *>(s->cmu[q]);
+                        for (int ax = 0; ax < 3; ax++) {
+                            ca.nu[ax][0] = static_cast<T *>(s->cnu[ax][0]);
+                            ca.nu[ax][1] = static_cast<T *>(s->cnu[ax][1]);
+                            ca.mu[ax] = static_cast<T *>(s->cmu[ax]);
                         }
                         ca.ext = static_cast<T *>(s->cext);
                         e = launch_cpml_adjoint<T>(a, ca, k & 1, nshots, st);

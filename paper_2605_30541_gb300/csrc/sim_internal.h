@@ -138,15 +138,19 @@ struct StepTime {
     float *qscale;
 };
 
-// CPML terms of the 2D adjoint sweep (cpml_adj.cu): the multipliers nu (of
-// zeta) and mu (of psi) of axes z and x, ping-ponged nu by step parity, and
-// the term `ext` the step kernel adds to the Laplacian of u (A.cext).
+// CPML terms of the adjoint sweep (cpml_adj.cu): the multipliers nu (of
+// zeta) and mu (of psi) of each absorbing axis, nu ping-ponged by step
+// parity; in 2D the term `ext` the step kernel adds to the Laplacian of u
+// (A.cext), in 3D c times that term added to u^k after the update.
 template <typename T>
 struct CpmlAdjArgs {
     const T *u;   // u^{k+1}, field layout per shot
-    T *nu[2][2];  // [z, x][parity]
-    T *mu[2];     // [z, x]
-    T *ext;
+    T *nu[3][2];  // [axis][parity] (absent axes unused)
+    T *mu[3];     // [axis]
+    T *ext;       // 2D: the bracket, added to the Laplacian by the step kernel
+    T *uo;        // 3D: u^k, receives c times the bracket (NULL in 2D)
+    const T *q;   // 3D: the recorded imaging term of the step
+    T *G;         // 3D: gradient accumulator
 };
 template <typename T>
 cudaError_t launch_cpml_adjoint(const StepArgs<T> &a, const CpmlAdjArgs<T> &c, int parity, int nshots,
@@ -238,7 +242,8 @@ struct InjE3 {
 };
 cudaError_t launch_inj3d(const StepArgs<float> &a, int n, int row, const Inj3 *grp, int ngrp, const InjE3 *ent,
                          int kind, int nshots, int mode, float *qs, float *Gs, cudaStream_t st);
-cudaError_t launch_cpml3d(const StepArgs<float> &a, int n, int ax, int phase, int nshots, cudaStream_t st);
+cudaError_t launch_cpml3d(const StepArgs<float> &a, int n, int ax, int phase, int nshots, cudaStream_t st,
+                          float *qs = nullptr);
 cudaError_t launch_sample3d(const StepArgs<float> &a, const StepTime &t, const void *rec, int nrec, int nshots,
                             cudaStream_t st);
 cudaError_t launch_inject3d(const StepArgs<float> &a, const StepTime &t, const void *src, int nshots,
