@@ -7,7 +7,7 @@
  * blocking or fusion: one plain pass per term, OpenMP over rows only where the
  * pass is a pure gather (no change of arithmetic order per cell).
  *
- * Readings of what the paper leaves open (each one is also a design doc line):
+ * Readings of what the paper leaves open (the design notes list each one too):
  *  R1 time discretisation: centred 2nd-order leapfrog; the damping term
  *     eta p_t is centred too: eta (p^{n+1} - p^{n-1}) / (2 dt)   (Eq. cerjan_pde)
  *  R2 sponge units: eta_SI = 1e-3 s/m * (c_damp/h) [rho - sin(2 pi rho)/(2 pi)]
