@@ -270,6 +270,70 @@ def test_absorbing_layers_against_large_domain_reference():
     assert _truncation_case("sponge", 60, 1500.0) < 1e-2
 
 
+_OFFS3 = [(0, 0, 150), (0, 0, -150), (0, 150, 0), (0, -150, 0), (150, 0, 0), (-150, 0, 0),
+          (140, 140, 140), (-140, 140, -140)]
+
+
+def _truncation_3d(v, cases):
+    """Per-receiver relative L2 error of 3D runs with absorbing layers on all
+    six faces against a large-domain reference (Dirichlet, no absorption) whose
+    edges are far enough that no reflection returns within nt. Receivers face
+    each of the six faces and two corners (where the per-axis layers overlap)."""
+    h, dt, nt, n, E, c = 10.0, 1e-3, 300, 41, 35, 200.0
+    w = synth.ricker(15.0, 1 / 15.0, dt, nt, np.float64)
+    rec = [(c + a, c + b, c + d) for a, b, d in _OFFS3]
+    N = n + 2 * E
+    big = dict(ndim=3, nz=N, ny=N, nx=N, h=h, dt=dt, nt=nt, bc="none", nb=[0] * 6)
+    ref = oracle.forward(big, np.full((N, N, N), v), w, src=(c + E * h,) * 3,
+                         rec=[(x + E * h, y + E * h, z + E * h) for x, y, z in rec])["gather"]
+    out = {}
+    for bc, nb in cases:
+        cfg = dict(ndim=3, nz=n, ny=n, nx=n, h=h, dt=dt, nt=nt, bc=bc, nb=[nb] * 6, f_ref=15.0)
+        g = oracle.forward(cfg, np.full((n, n, n), v), w, src=(c, c, c), rec=rec)["gather"]
+        out[(bc, nb)] = np.array([rel(g[:, k], ref[:, k]) for k in range(len(rec))])
+    return out
+
+
+def test_absorbing_layers_3d_against_large_domain_reference():
+    # the 3D layers on every face (z, y and x, edges and corners): the CPML must
+    # leave a small error at every receiver and beat the sponge of equal width;
+    # a wider layer must absorb better; the cube is symmetric, so the six face
+    # receivers see the same error, whatever axis they face
+    for v in (1500.0, 2500.0):
+        e = _truncation_3d(v, [("sponge", 10), ("sponge", 20), ("cpml", 5), ("cpml", 10)])
+        assert e[("cpml", 10)].max() < 1e-3
+        assert np.all(e[("cpml", 10)] < e[("sponge", 10)] / 100)
+        assert np.all(e[("cpml", 10)] < e[("cpml", 5)] / 3)
+        assert np.all(e[("sponge", 20)] < e[("sponge", 10)] / 2.5)
+        for k in e.values():
+            assert np.ptp(k[:6]) <= 1e-6 * k[:6].max()
+    assert _truncation_3d(1500.0, [("cpml", 10)])[("cpml", 10)].max() < 1e-5
+
+
+@pytest.mark.parametrize("bc", ["cpml", "sponge"])
+def test_3d_axis_permutation_with_unequal_layers(bc):
+    # swapping two axes of the whole problem (model, positions and the widths
+    # of the absorbing faces) permutes the solution: the y axis (profiles, face
+    # widths, strides, corner sums) is treated exactly as x and z
+    nz, ny, nx, nt = 22, 26, 30, 200
+    vel = synth.procedural_3d(nz, ny, nx, 10.0, 31).astype(np.float64)
+    nb = [5, 7, 6, 9, 8, 4]
+    cfg = dict(ndim=3, nz=nz, ny=ny, nx=nx, h=10.0, dt=8e-4, nt=nt, bc=bc, nb=nb, f_ref=12.0)
+    w = synth.ricker(12.0, 0.09, 8e-4, nt, np.float64)
+    src = (123.4, 151.7, 88.2)
+    rec = np.array([[10.0, 20.0, 30.0], [280.0, 240.0, 200.0], [5.0, 250.0, 111.0], [150.5, 3.3, 207.0]])
+    g = oracle.forward(cfg, vel, w, src=src, rec=rec)["gather"]
+    assert np.abs(g).max() > 0
+    cxy = dict(cfg, ny=nx, nx=ny, nb=[nb[0], nb[1], nb[4], nb[5], nb[2], nb[3]])
+    gxy = oracle.forward(cxy, vel.transpose(0, 2, 1).copy(), w, src=(src[1], src[0], src[2]),
+                         rec=rec[:, [1, 0, 2]])["gather"]
+    czy = dict(cfg, nz=ny, ny=nz, nb=[nb[2], nb[3], nb[0], nb[1], nb[4], nb[5]])
+    gzy = oracle.forward(czy, vel.transpose(1, 0, 2).copy(), w, src=(src[0], src[2], src[1]),
+                         rec=rec[:, [0, 2, 1]])["gather"]
+    assert rel(gxy, g) < 1e-12
+    assert rel(gzy, g) < 1e-12
+
+
 def test_sponge_profile_constants():
     # Eq. cerjan_damp: eta = (c_damp/h)[rho - sin(2 pi rho)/(2 pi)], c_damp = 1.5 ln(1/R)/n_bl
     nb = 60
