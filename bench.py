@@ -1,15 +1,21 @@
 """Benchmark of the acoustic FDTD hot path on GB300.
 
-Default workload (one "step" = one full solve): the field-scale 2D slice —
-619 x 1000 cells at 10 m + 50-cell CPML left/right/bottom, free surface, seeded
-procedural velocity, one Ricker source at the surface centre, 1000 receivers,
-nt = 8000 steps of 1 ms, FP32 snapshots every 10 steps for the first 5 s.
+Default workload (one "step" = one full solve): the field-scale 3D volume —
+619 x 1000 x 1000 cells at 10 m + 30-cell CPML on x, y and bottom, free
+surface (1060 x 1060 x 649 = 729.2 M padded cells), seeded procedural
+velocity, one Ricker source (8 Hz) at the surface centre, a 201 x 201
+receiver grid, dt = 0.8 ms, nt = 2500 (the 2 s record at a stable step).
+`--workload` selects the 2D slice (c2), 32 shots on it (c2x32), the batched
+uneven slices (c3), the production runs (c6g, c6w) or the model builder.
 
 Metric: cell-updates per second over the padded grid (Gcell/s). `value` is
 device-timed (CUDA events on the solver's stream, inputs resident, L2 flushed
 between timed solves); `e2e` repeats the solve through the C ABI with pinned
 host buffers (model upload, gather and snapshot download inside the timing).
-`--impl reference` times the FP64 CPU oracle on the host cores instead.
+`gradient` times the adjoint-state gradient (2D: 16 shots of the 201 x 201
+slice, FP16 vs FP32 checkpoints; 3D: one shot of the full volume with FP16
+checkpoints). `--impl reference` times the FP64 CPU oracle on the host cores
+instead, on a bounded sample of the same workload.
 Under torchrun every rank runs an independent replica (the single-shot solve
 does not shard); value = all ranks' cell-updates / max-over-ranks time.
 """
@@ -38,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c2x32", "c3", "c5", "c5s", "c6g", "c6w", "model"])
+    ap.add_argument("--workload", default="c5", choices=["c2", "c2x32", "c3", "c5", "c5s", "c6g", "c6w", "model"])
     ap.add_argument("--nt", type=int, default=0, help="override nt (profiling runs only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -99,6 +105,35 @@ def algorithmic_bytes_per_launch(cfg, nshots):
         nsnap = (end - cfg["snap_begin"] + cfg["snap_every"] - 1) // cfg["snap_every"]
     snap = nsnap * cfg["nz"] * cfg.get("ny", 1) * cfg["nx"] * 4 / cfg["nt"]
     return nshots * (16 * cells + 16 * strip + rec + snap)
+
+
+def strip_cell_axes(cfg):
+    """CPML strip cells counted once per absorbing axis whose strip holds them."""
+    if cfg.get("bc") != "cpml":
+        return 0
+    nb = cfg["nb"]
+    NZ = nb[0] + cfg["nz"] + nb[1]
+    NY = nb[2] + cfg["ny"] + nb[3] if cfg["ndim"] == 3 else 1
+    NX = nb[4] + cfg["nx"] + nb[5]
+    s = (nb[4] + nb[5]) * NZ * NY + (nb[0] + nb[1]) * NX * NY
+    if cfg["ndim"] == 3:
+        s += (nb[2] + nb[3]) * NZ * NX
+    return s
+
+
+def gradient_bytes_per_shot(cfg, fp16, qbytes=None):
+    """Least DRAM bytes of one shot's adjoint-state gradient: per cell and
+    step, the forward sweep 16 B (read p^n, p^{n-1}, c; write p^{n+1}), the
+    recompute 16 B plus the imaging-term store, the adjoint sweep 16 B plus
+    the imaging-term read and the gradient read + write (8 B); per CPML strip
+    cell and axis and step, 16 B (psi, zeta read + write) in each forward-type
+    sweep and 24 B in the adjoint (multipliers nu, mu read + write, the
+    bracket written and read). Imaging terms are 2 B in FP16 storage, else
+    4 B (qbytes overrides). Checkpoint traffic (a few states per segment) is
+    not counted."""
+    q = qbytes if qbytes is not None else (2 if fp16 else 4)
+    cells = padded_cells(cfg)
+    return cfg["nt"] * (cells * (16 + 16 + q + 16 + q + 8) + strip_cell_axes(cfg) * (16 + 16 + 24))
 
 
 def launches_per_solve(cfg, nsnap, path):
@@ -198,60 +233,93 @@ def ncu_traffic(kernel_file, key):
     return None
 
 
+def oracle_sample(cfg):
+    """The problem the FP64 oracle times as a bounded sample of the workload.
+    2D: the workload itself (its first steps). 3D: the volume's top corner
+    block of 100 x 200 x 200 interior cells (the same velocities) with its
+    -x and -y CPML faces and the free top, a source at the block's surface
+    centre and the receivers of the grid that fall in the block."""
+    if cfg["ndim"] == 2:
+        return cfg, cfg["src"][0], cfg["rec"], "the same slice solve"
+    nz, ny, nx = 100, 200, 200
+    h = cfg["h"]
+    nb = cfg["nb"]
+    samp = dict(cfg, nz=nz, ny=ny, nx=nx, nb=[0, 0, nb[2], 0, nb[4], 0], cpml_vmax=float(cfg["vel"].max()),
+                vel=np.ascontiguousarray(cfg["vel"][:nz, :ny, :nx]))
+    rec = cfg["rec"]
+    keep = (rec[:, 0] <= (nx - 1) * h) & (rec[:, 1] <= (ny - 1) * h) & (rec[:, 2] <= (nz - 1) * h)
+    return samp, np.array([nx // 2 * h, ny // 2 * h, h]), rec[keep], \
+        "the volume's top corner block (100 x 200 x 200 cells + its -x, -y CPML, free top)"
+
+
 def cpu_oracle_rate(cfg, target_s=12.0):
-    """FP64 oracle throughput on a bounded sample of the workload (first steps
-    of the same solve), sized to about target_s seconds of CPU work."""
+    """FP64 oracle throughput on a bounded sample of the workload (the first
+    steps of the sample problem), sized to about target_s seconds of CPU work."""
     import oracle
     oracle.build()
-    cells = padded_cells(cfg)
-    probe = dict(cfg, nt=40, snap_every=0, snap_end=0)
-    v64 = cfg["vel"].astype(np.float64)
-    w64 = cfg["wavelet"].astype(np.float64)
+    samp, src, rec, what = oracle_sample(cfg)
+    cells = padded_cells(samp)
+    v64 = samp["vel"].astype(np.float64)
+    w64 = samp["wavelet"].astype(np.float64)
+    probe = dict(samp, nt=20, snap_every=0, snap_end=0)
     t0 = time.perf_counter()
-    oracle.forward(probe, v64, w64[:40], src=cfg["src"][0], rec=cfg["rec"])
-    rate = 40 * cells / (time.perf_counter() - t0)
-    nt = int(max(40, min(cfg["nt"], target_s * rate / cells)))
-    samp = dict(cfg, nt=nt, snap_end=min(cfg.get("snap_end", 0), nt))
+    oracle.forward(probe, v64, w64[:20], src=src, rec=rec)
+    rate = 20 * cells / (time.perf_counter() - t0)
+    nt = int(max(20, min(samp["nt"], target_s * rate / cells)))
+    run = dict(samp, nt=nt, snap_end=min(samp.get("snap_end", 0), nt))
     t0 = time.perf_counter()
-    oracle.forward(samp, v64, w64[:nt], src=cfg["src"][0], rec=cfg["rec"], snaps=samp.get("snap_every", 0) > 0)
+    oracle.forward(run, v64, w64[:nt], src=src, rec=rec, snaps=run.get("snap_every", 0) > 0)
     dt = time.perf_counter() - t0
     return {"value": nt * cells / dt / 1e9, "unit": "Gcell/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "first %d of %d steps of the same slice solve (FP64, OpenMP over rows), %.1f s" %
-                      (nt, cfg["nt"], dt)}
+            "sample": "first %d of %d steps of %s (FP64, OpenMP over rows), %.1f s" % (nt, cfg["nt"], what, dt)}
+
+
+def workload_name(args, cfg, nshots, nsnap):
+    nt, nrec = cfg["nt"], len(cfg["rec"])
+    if cfg["ndim"] == 3:
+        return ("%s: 3D volume %dx%dx%d (+30-cell CPML on x, y, bottom, free top), dt=0.8 ms, nt=%d, "
+                "%d receivers, %d shot(s) per GPU" % (args.workload, cfg["nz"], cfg["ny"], cfg["nx"], nt, nrec, nshots))
+    if args.workload == "c6w":
+        return ("c6w: production wavefield, 2D slice 619x1000 (+60-cell sponge left/right/bottom, free top), "
+                "band-passed 3-6 Hz source, nt=%d, %d FP32 snapshots (every 14 steps)" % (nt, nsnap))
+    return ("c2: 2D slice 619x1000 (+50-cell CPML left/right/bottom, free top), nt=%d, %d receivers, "
+            "%d FP32 snapshots, %d shot(s) per GPU" % (nt, nrec, nsnap, nshots))
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    cfg, _ = workload(args)
+    cfg, nshots = workload(args)
     import oracle
     oracle.build()
-    cells = padded_cells(cfg)
-    v64 = cfg["vel"].astype(np.float64)
-    w64 = cfg["wavelet"].astype(np.float64)
-    probe = dict(cfg, nt=30, snap_every=0, snap_end=0)
+    samp, src, rec, what = oracle_sample(cfg)
+    cells = padded_cells(samp)
+    v64 = samp["vel"].astype(np.float64)
+    w64 = samp["wavelet"].astype(np.float64)
+    probe = dict(samp, nt=20, snap_every=0, snap_end=0)
     t0 = time.perf_counter()
-    oracle.forward(probe, v64, w64[:30], src=cfg["src"][0], rec=cfg["rec"])
-    rate = 30 * cells / (time.perf_counter() - t0)
+    oracle.forward(probe, v64, w64[:20], src=src, rec=rec)
+    rate = 20 * cells / (time.perf_counter() - t0)
     budget = 150.0 / max(1, args.steps + args.warmup)   # whole run within a few minutes
-    nt = int(max(30, min(cfg["nt"], budget * rate / cells)))
-    samp = dict(cfg, nt=nt, snap_end=min(cfg.get("snap_end", 0), nt))
+    nt = int(max(20, min(samp["nt"], budget * rate / cells)))
+    run = dict(samp, nt=nt, snap_end=min(samp.get("snap_end", 0), nt))
     times = []
     for it in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.forward(samp, v64, w64[:nt], src=cfg["src"][0], rec=cfg["rec"], snaps=samp.get("snap_every", 0) > 0)
+        oracle.forward(run, v64, w64[:nt], src=src, rec=rec, snaps=run.get("snap_every", 0) > 0)
         if it >= args.warmup:
             times.append(time.perf_counter() - t0)
     per = statistics.mean(times)
     value = nt * cells / per / 1e9
+    sample = "first %d of %d steps of %s per step" % (nt, cfg["nt"], what)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gcell/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "c2 slice 619x1000 + 50-cell CPML, free top (bounded sample: first %d of %d steps)"
-                       % (nt, cfg["nt"]), "l2": "n/a (CPU)"},
+            "config": {"workload": workload_name(args, cfg, nshots, 0) + " (bounded sample: %s)" % sample,
+                       "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": "Gcell/s", "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": "first %d of %d steps per step" % (nt, cfg["nt"])},
+                             "sample": sample},
             "e2e": {"value": value, "unit": "Gcell/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -364,11 +432,19 @@ def gradient_timing(reps=2):
         out[name] = (e0.elapsed_time(e1) / 1e3 / reps / ns, g)
     sim.close()
     g16, g32 = out["batched_fp16"][1], out["one_shot_fp32"][1]
+    peak, peak_kind = read_peaks()
+    t16 = out["batched_fp16"][0]
+    ach = gradient_bytes_per_shot(c, True) / t16 / 1e9
     return {"workload": "c4: 201x201 + 20-cell CPML on every side, 16 shots, nt=4000, sqrt(nt) checkpoints",
-            "s_per_shot_batched_fp16": out["batched_fp16"][0], "s_per_shot_one_shot_fp32": out["one_shot_fp32"][0],
-            "speedup": out["one_shot_fp32"][0] / out["batched_fp16"][0],
+            "s_per_shot_batched_fp16": t16, "s_per_shot_one_shot_fp32": out["one_shot_fp32"][0],
+            "speedup": out["one_shot_fp32"][0] / t16,
             "rel_l2_fp16_vs_fp32": float(torch.linalg.norm(g16 - g32) / torch.linalg.norm(g32)),
-            "tolerance_vs_fp64_oracle": {"fp32": 1e-4, "fp16": 1e-2}}
+            "tolerance_vs_fp64_oracle": {"fp32": 1e-4, "fp16": 1e-2},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "peak_kind": peak_kind, "case": "batched FP16 gradient, whole call per shot",
+                         "algorithmic_bytes_per_shot": gradient_bytes_per_shot(c, True),
+                         "note": "16 shots of 58,081 cells: fields L2-resident, imaging terms and checkpoints "
+                                 "(~350 MB) are not; an effective rate on algorithmic bytes"}}
 
 
 def run_ours(args):
@@ -459,8 +535,10 @@ def run_ours(args):
         for _ in range(max(1, min(2, args.warmup))):
             pkg.sim_set_model(sim.handle, vel_h)
             pkg.sim_forward(sim.handle, nshots, wav_h, src, len(rec), rec, gather_h, snaps_h, None)
+        # long solves (the 3D volume: seconds each) repeat a few times only
+        ke = args.steps if total / args.steps < 2.0 else max(1, min(args.steps, 3))
         et = []
-        for _ in range(args.steps):
+        for _ in range(ke):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -473,32 +551,22 @@ def run_ours(args):
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         h2d = vel_h.numel() * 4 + wav_h.numel() * 4
         d2h = gather_h.numel() * 4 + (snaps_h.numel() * 4 if snaps_h is not None else 0)
-        e2e = {"value": world * args.steps * nshots * nt * cells / float(te.item()) / 1e9, "unit": "Gcell/s",
+        e2e = {"value": world * ke * nshots * nt * cells / float(te.item()) / 1e9, "unit": "Gcell/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": float(te.item()) / args.steps * 1e3}
+               "ms_per_step": float(te.item()) / ke * 1e3, "steps": ke}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_oracle_rate(cfg)
     grad = None
-    if rank == 0 and not args.no_grad and cfg["ndim"] == 2:
+    if rank == 0 and not args.no_grad:
         grad = gradient_timing()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Gcell/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": (("%s: 3D volume %dx%dx%d (+30-cell CPML on x, y, bottom, free top), "
-                                         "dt=0.8 ms, nt=%d, %d receivers, %d shot(s) per GPU"
-                                         % (args.workload, cfg["nz"], cfg["ny"], cfg["nx"], nt, len(rec), nshots))
-                                        if cfg["ndim"] == 3 else
-                                        ("c6w: production wavefield, 2D slice 619x1000 (+60-cell sponge left/right/"
-                                         "bottom, free top), band-passed 3-6 Hz source, nt=%d, %d FP32 snapshots "
-                                         "(every 14 steps)" % (nt, nsnap))
-                                        if args.workload == "c6w" else
-                                        ("c2: 2D slice 619x1000 (+50-cell CPML left/right/bottom, free top), "
-                                         "nt=%d, %d receivers, %d FP32 snapshots, %d shot(s) per GPU"
-                                         % (nt, len(rec), nsnap, nshots))),
+                "config": {"workload": workload_name(args, cfg, nshots, nsnap),
                            "padded_cells": cells, "l2": "flushed between timed solves (%d MB write)" %
                                                         (L2_FLUSH_BYTES >> 20),
                            "parallelism": "replicas x%d" % world},

@@ -33,7 +33,11 @@
  *    IEEE half with a float scale per snapshot).
  *  - The caller owns every argument buffer. The library owns its padded
  *    fields, coefficients, absorbing-layer memory, checkpoints and staging
- *    buffers; all are allocated in sim_create and freed by sim_destroy.
+ *    buffers, all freed by sim_destroy. The forward buffers are allocated in
+ *    sim_create; the adjoint-state buffers (checkpoints, imaging terms,
+ *    adjoint fields) by the first sim_adjoint call on the handle, and a
+ *    staging buffer for host-memory snapshots by the first call that asks
+ *    for them.
  *  - Calls are ordered on the handle's CUDA stream and return after enqueue
  *    (unless an output is host memory). Device-side failures (non-finite
  *    values, a bounded wait that gave up) surface at the next call or at
@@ -191,27 +195,30 @@ typedef struct {
 sim_status sim_batch(int nitems, const sim_batch_item *items, void *cuda_stream);
 
 /* No counterpart in the paper. A forward solve for callers that cannot
- * allocate device memory at the time they call: code running while their own
- * application records a CUDA graph (an allocation there would not be
- * replayed), processes whose device memory is already reserved in full by a
- * framework's pool, and latency-critical paths where cudaMalloc / cudaFree,
+ * allocate device memory at the time they call: processes whose device
+ * memory is already reserved in full by a framework's pool (a cudaMalloc
+ * there would fail), and latency-critical paths where cudaMalloc / cudaFree,
  * which may synchronise the device, are not acceptable.
  * 2D, FP32, one shot, gather only: vel [nz][nx], wavelet [nt] and
  * gather [nt][nrec] are device pointers; src_pos [2] and rec_pos [nrec][2]
  * are host arrays as in sim_forward. Every intermediate lives in one 32 MiB
  * array built into the library (each GPU that loads the library holds it
  * until the process exits); a problem that does not fit returns SIM_ERR_ARG
- * before any GPU work. Nothing is allocated. The first call on a device looks
- * up that array's address with the device current and configures the step
- * kernel: make that first call before any stream capture. All calls share the
- * array: each clears what must start at zero, and calls whose GPU work
- * overlaps (other streams or threads) race on it. Returns after the solve
- * has completed on cuda_stream (NULL: legacy stream). Errors: sim_last_error(NULL). */
+ * before any GPU work. Nothing is allocated. Every call reads the velocity
+ * range back and waits for cuda_stream, and copies host-built lists in, so
+ * no call may be made while that stream (or, in global capture mode, any
+ * stream) is being captured. The first call on a device looks up that
+ * array's address with the device current and keeps it for the life of the
+ * process: do not use the entry point across a cudaDeviceReset. All calls
+ * share the array: each clears what must start at zero, and calls whose GPU
+ * work overlaps (other streams or threads) race on it. Returns after the
+ * solve has completed on cuda_stream (NULL: legacy stream); non-finite values
+ * in the final field or the gather give SIM_ERR_UNSTABLE. Errors:
+ * sim_last_error(NULL). */
 sim_status sim_forward_noalloc(const sim_desc *d, const float *vel, const float *wavelet,
                                const double *src_pos, int nrec, const double *rec_pos, float *gather,
                                void *cuda_stream);
 
-/* Wait for the handle's stream and report any device-side failure. */
 /* Band-passed Ricker source wavelet of the paper's production runs (Sec.
  * "Source Wavelet", Tab. bands): w(t) = Ricker of peak frequency f0 centred at
  * t0 = 1/f0, sampled at t = n dt (n = 0 .. nt-1), filtered by a digital
@@ -314,6 +321,7 @@ sim_status sim_model_deposit(int nz, int ny, int nx, const float *v_in, const in
                              const float *bounds, const float *vbed, const int *offsets, const float *eta,
                              float *v_out, int *lab_out, void *stream);
 
+/* Wait for the handle's stream and report any device-side failure. */
 sim_status sim_sync(sim_t s);
 
 /* Layout and model facts of a live handle. */

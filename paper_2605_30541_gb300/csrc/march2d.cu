@@ -790,32 +790,20 @@ __global__ void __launch_bounds__(KCfg<CPML>::WPB * 32, KCfg<CPML>::MINB) k_marc
         if (CPML && cpml_segment(A, S)) march_cpml(A, t, S, M.tz, W + K::ARGS, lane);
         else march_lean(A, t, S, M.tz, W + K::ARGS, lane);
     };
-    if (M.ctr) {
-        // dynamic: segments in order from this step's counter, the next one
-        // claimed while the current one runs; after the previous step is
-        // complete (every counter use of it included), zero the next step's
-        cudaGridDependencySynchronize();
-        unsigned *ctr = M.ctr + (t.n & 1);
-        if (gw == 0 && lane == 0) M.ctr[(t.n + 1) & 1] = 0u;
-        unsigned next = 0;
+    // segments in order from this step's counter, the next one claimed while
+    // the current one runs; after the previous step is complete (every
+    // counter use of it included), zero the next step's
+    cudaGridDependencySynchronize();
+    unsigned *ctr = M.ctr + (t.n & 1);
+    if (gw == 0 && lane == 0) M.ctr[(t.n + 1) & 1] = 0u;
+    unsigned next = 0;
+    if (lane == 0) next = atomicAdd(ctr, 1u);
+    next = __shfl_sync(0xffffffffu, next, 0);
+    while (next < (unsigned)M.nitems) {
+        const MarchSeg S = M.segs[next];
         if (lane == 0) next = atomicAdd(ctr, 1u);
+        run(S);
         next = __shfl_sync(0xffffffffu, next, 0);
-        while (next < (unsigned)M.nitems) {
-            const MarchSeg S = M.segs[next];
-            if (lane == 0) next = atomicAdd(ctr, 1u);
-            run(S);
-            next = __shfl_sync(0xffffffffu, next, 0);
-        }
-        return;
-    }
-    const int s0 = M.wseg[gw], s1 = M.wseg[gw + 1];
-    bool waited = false;
-    for (int si = s0; si < s1; si++) {
-        if (!waited) {  // fields of the previous step from here on
-            cudaGridDependencySynchronize();
-            waited = true;
-        }
-        run(M.segs[si]);
     }
 }
 

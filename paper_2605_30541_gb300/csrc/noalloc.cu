@@ -1,10 +1,9 @@
 // sim_forward_noalloc: a forward solve that allocates no device memory.
 //
 // Some callers cannot allocate GPU memory at the moment they need a solve:
-// code that runs while an application is recording a CUDA graph (where an
-// allocation would not be replayed), processes whose device memory has been
-// fully reserved up front by a framework's pool, and latency-critical paths
-// where cudaMalloc / cudaFree (which may synchronise the whole device) are
+// processes whose device memory has been reserved in full up front by a
+// framework's pool (a cudaMalloc there fails), and latency-critical paths
+// where cudaMalloc / cudaFree, which may synchronise the whole device, are
 // not acceptable. For them this entry point takes the caller's inputs and
 // outputs and keeps every intermediate (pressure fields, the c field, the
 // absorbing-layer profiles, the receiver and source lists, the I/O block) in
@@ -16,9 +15,14 @@
 //    pointers, positions are host arrays.
 //  - Problems whose working set exceeds kScratchBytes are rejected with
 //    SIM_ERR_ARG before any GPU work.
+//  - Every call reads the velocity range back to the host and waits for its
+//    stream (twice), and copies host-built lists in; so no call may be made
+//    while its stream (or, in global capture mode, any stream) is being
+//    captured into a CUDA graph.
 //  - The first call on a device looks up the array's device address
-//    (cudaGetSymbolAddress) with that device current; make that first call
-//    before any stream capture.
+//    (cudaGetSymbolAddress) with that device current and keeps it for the
+//    life of the process; do not use the entry point across a
+//    cudaDeviceReset, which reloads the module and moves the array.
 //  - Every call reuses the same array and clears what must start at zero;
 //    calls whose GPU work overlaps (other streams, other threads) race on
 //    it. Calls on one stream are ordered and safe.
@@ -371,10 +375,13 @@ extern "C" sim_status sim_forward_noalloc(const sim_desc *din, const float *vel,
         t.inj_row = n;
         if (sim_status r = cuda(launch_step2d_f32(a, t, TZ, 1, kModeForward, st, false), "step kernel")) return r;
     }
+    // non-finite values anywhere in the final field (the step kernel only
+    // checks the samples it records)
+    if (sim_status r = cuda(launch_check_finite<float>(g, a.pbuf[d.nt & 1], 1, flags, st), "finite check")) return r;
     unsigned hflags = 0;
     if (sim_status r = cuda(cudaMemcpyAsync(&hflags, flags, sizeof hflags, cudaMemcpyDeviceToHost, st), "flags"))
         return r;
     if (sim_status r = cuda(cudaStreamSynchronize(st), "completion")) return r;
-    if (hflags & kFlagUnstable) return nfail(SIM_ERR_UNSTABLE, "non-finite values in the outputs");
+    if (hflags & kFlagUnstable) return nfail(SIM_ERR_UNSTABLE, "non-finite values in the wavefield or outputs");
     return SIM_OK;
 }

@@ -261,12 +261,11 @@ struct sim_s {
     const TileMap *tmap = nullptr;         // set while lists are built for a non-uniform tiling
     std::list<std::pair<int, ResidentPlan>> rplans;  // per shot count
     MarchSeg *mseg = nullptr;              // row march: segments, warp ranges, slice arguments
-    int *mwseg = nullptr;
     StepArgs<float> *mslice = nullptr;
-    size_t cap_mseg = 0, cap_mwseg = 0;
+    size_t cap_mseg = 0;
     long long march_key = -1;              // (shot count, item rows, tile height) of the plan on the device
     int march_nwarps = 0, march_nitems = 0;
-    unsigned *mctr = nullptr;              // dynamic schedule: per-step item counters
+    unsigned *mctr = nullptr;              // row march: per-step item counters
     int last_path = 0, last_rows = 0;      // see sim_info
     int zchunk = 0;                        // z-march chunk of the 3D kernel
     // adjoint-state buffers, allocated by the first sim_adjoint call
@@ -1084,107 +1083,11 @@ sim_status run_resident<float>(sim_t s, const StepArgs<float> &a, const Resident
 }
 
 // ---------------------------------------------------------------- row march plan
-//
-// The step's work as (member, strip, row) items in member-major order, cut
-// into pieces of equal estimated cost, one per warp that fits on the GPU at
-// once; fewer warps when rows are few, so each marches at least
-// kMarchMinRows rows (a warp re-reads 8 halo rows at the start of each
-// segment). Segments start on multiples of 4 rows (the list tiles are 8, 16
-// or 32 rows high). Cost of one row of a strip: its active lanes plus a fixed share
-// for the row's waits and halo, more where CPML memory terms are updated.
-constexpr int kMarchMinRows = 16;
+
 struct MarchMember {
     int slice, shot;
     const sim_s *s;
 };
-
-void plan_march(const std::vector<MarchMember> &mem, long long max_warps, std::vector<MarchSeg> &segs,
-                std::vector<int> &wseg) {
-    struct Strip {
-        double base;
-        bool cpml;
-    };
-    // cost weights: per active lane, per row, and extra per row of a strip
-    // with x-sponge / x-CPML cells and per row of z-sponge / z-CPML
-    // (GSIM_MARCH_COST="lane,row,spx,cpx,spz,cpz" overrides them)
-    double wl = 0.0, wr = 40.0, wspx = 40.0, wcpx = 40.0, wspz = 40.0, wcpz = 12.0;
-    if (const char *f = getenv("GSIM_MARCH_COST"))
-        sscanf(f, "%lf,%lf,%lf,%lf,%lf,%lf", &wl, &wr, &wspx, &wcpx, &wspz, &wcpz);
-    auto strips = [&](const sim_s *s) {
-        const Geom &g = s->g;
-        std::vector<Strip> v;
-        const bool cp = s->d.bc == SIM_BC_CPML, sp = s->d.bc == SIM_BC_SPONGE;
-        for (int x0 = 0; x0 < g.NX; x0 += kMarchW) {
-            const int lanes = std::min(32, (g.NX - x0 + 3) / 4);
-            const bool ax = (g.nbx0 > 0 && x0 - 4 < g.nbx0) || (g.nbx1 > 0 && x0 + kMarchW + 4 > g.NX - g.nbx1);
-            v.push_back({wl * lanes + wr + (cp && ax ? wcpx : 0.0) + (sp && ax ? wspx : 0.0), cp});
-        }
-        return v;
-    };
-    auto zextra = [&](const sim_s *s, int z) {
-        const Geom &g = s->g;
-        const bool az = (g.nbz0 > 0 && z < g.nbz0 + 4) || (g.nbz1 > 0 && z >= g.NZ - g.nbz1 - 4);
-        if (!az) return 0.0;
-        return s->d.bc == SIM_BC_CPML ? wcpz : s->d.bc == SIM_BC_SPONGE ? wspz : 0.0;
-    };
-    double total = 0;
-    long long rows = 0;
-    for (const MarchMember &m : mem) {
-        const int NZ = m.s->g.NZ;
-        double zx = 0;
-        for (int z = 0; z < NZ; z++) zx += zextra(m.s, z);
-        for (const Strip &st : strips(m.s)) total += st.base * NZ + zx;
-        rows += (long long)NZ * ((m.s->g.NX + kMarchW - 1) / kMarchW);
-    }
-    int min_rows = kMarchMinRows;
-    if (const char *f = getenv("GSIM_MARCH_MINROWS")) min_rows = std::max(1, atoi(f));
-    if (const char *f = getenv("GSIM_MARCH_WAVES")) max_warps *= std::max(1, atoi(f));
-    const int nw = (int)std::max<long long>(1, std::min<long long>(max_warps, rows / min_rows));
-    const double target = total / nw;
-    segs.clear();
-    wseg.assign(1, 0);
-    // Order of the items: by member, then by bands of H rows, then by strip,
-    // then by row. With H about the rows one warp gets, the warps of a CTA
-    // (consecutive pieces) march the neighbouring strips of the same rows
-    // side by side, so HBM sees whole rows rather than 512-byte pieces of
-    // rows far apart. H = 0 (GSIM_MARCH_BAND=0): strip after strip.
-    int H = (int)std::min<long long>(1 << 20, std::max<long long>(16, rows / nw));
-    H = (H + 3) & ~3;
-    if (const char *f = getenv("GSIM_MARCH_BAND")) {
-        const int v = atoi(f);
-        if (v == 0) H = 1 << 30;
-        else if (v > 0) H = (v + 3) & ~3;
-    }
-    double acc = 0, next = target;
-    int w = 0;
-    for (const MarchMember &m : mem) {
-        const std::vector<Strip> sv = strips(m.s);
-        const int NZ = m.s->g.NZ;
-        for (int zc = 0; zc < NZ; zc += H) {
-            const int ze = (int)std::min<long long>(NZ, (long long)zc + H);
-            for (int bx = 0; bx < (int)sv.size(); bx++) {
-                int z0 = zc;
-                for (int z = zc; z < ze; z++) {
-                    acc += sv[bx].base + zextra(m.s, z);
-                    // cuts after rows 4k + 3: segments start on multiples of 4 rows,
-                    // so a 4-row block never straddles two list tiles
-                    if (acc >= next && w < nw - 1 && (z & 3) == 3 && z + 1 < ze) {
-                        segs.push_back(MarchSeg{m.slice, m.shot, bx, z0, z + 1, {0, 0, 0}});
-                        z0 = z + 1;
-                        wseg.push_back((int)segs.size());
-                        w++;
-                        next = target * (w + 1);
-                    }
-                }
-                if (z0 < ze) segs.push_back(MarchSeg{m.slice, m.shot, bx, z0, ze, {0, 0, 0}});
-            }
-        }
-    }
-    wseg.push_back((int)segs.size());
-    if (getenv("GSIM_MARCH_LOG"))
-        fprintf(stderr, "[gsim march] %zu members, %lld strip rows, %d warps (at most %lld), %zu segments\n",
-                mem.size(), rows, (int)wseg.size() - 1, (long long)max_warps, segs.size());
-}
 
 // Dynamic schedule: the step's work as items of `item` rows of one strip of
 // one member. Items that update CPML memory (their strip within 4 cells of
@@ -1194,8 +1097,8 @@ void plan_march(const std::vector<MarchMember> &mem, long long max_warps, std::v
 // rows. Returns the number of warps to launch (one per item at most).
 int march_item_rows() {
     int k = 16;
-    if (const char *f = getenv("GSIM_MARCH_ITEM")) k = atoi(f);
-    return k <= 0 ? 0 : (k + 3) & ~3;
+    if (const char *f = getenv("GSIM_MARCH_ITEM")) k = std::max(4, atoi(f));
+    return (k + 3) & ~3;
 }
 int plan_march_items(const std::vector<MarchMember> &mem, long long max_warps, int item, std::vector<MarchSeg> &segs) {
     segs.clear();
@@ -1237,17 +1140,9 @@ sim_status march_prepare(sim_t s, const StepArgs<float> &a, int nshots, MarchArg
         std::vector<MarchMember> mem;
         for (int k = 0; k < nshots; k++) mem.push_back({0, k, s});
         std::vector<MarchSeg> segs;
-        std::vector<int> wseg;
         const int maxw = device_sms(s->dev) * std::max(1, march2d_warps_per_sm(s->d.bc == SIM_BC_CPML));
-        if (item) {
-            s->march_nwarps = plan_march_items(mem, maxw, item, segs);
-            s->march_nitems = (int)segs.size();
-        } else {
-            plan_march(mem, maxw, segs, wseg);
-            if (sim_status r = upload(s, s->mwseg, wseg, s->cap_mwseg, "march warps")) return r;
-            s->march_nwarps = (int)wseg.size() - 1;
-            s->march_nitems = 0;
-        }
+        s->march_nwarps = plan_march_items(mem, maxw, item, segs);
+        s->march_nitems = (int)segs.size();
         if (sim_status r = upload(s, s->mseg, segs, s->cap_mseg, "march segments")) return r;
         s->march_key = key;
     }
@@ -1255,8 +1150,7 @@ sim_status march_prepare(sim_t s, const StepArgs<float> &a, int nshots, MarchArg
         return r;
     m.slices = s->mslice;
     m.segs = s->mseg;
-    m.wseg = s->mwseg;
-    m.ctr = s->march_nitems ? s->mctr : nullptr;
+    m.ctr = s->mctr;
     m.nwarps = s->march_nwarps;
     m.nitems = s->march_nitems;
     m.tz = s->tile_z;
@@ -1277,10 +1171,8 @@ sim_status run_march<float>(sim_t s, const StepArgs<float> &a, int nshots) {
     const bool cpml = s->d.bc == SIM_BC_CPML;
     return run_graph(s, ((long long)nshots << 16) | ((long long)march_item_rows() << 8) | ((long long)s->tile_z << 2) | 3,
                      [&](cudaStream_t st) {
-        if (m.ctr) {
-            cudaError_t e = cudaMemsetAsync(m.ctr, 0, 2 * sizeof(unsigned), st);
-            if (e != cudaSuccess) return e;
-        }
+        cudaError_t e0 = cudaMemsetAsync(m.ctr, 0, 2 * sizeof(unsigned), st);
+        if (e0 != cudaSuccess) return e0;
         for (int n = 0; n < s->d.nt; n++) {
             cudaError_t e = launch_march2d(m, cpml, step_time(s, a, n, kModeForward, nullptr, nullptr), st,
                                            s->use_graphs);
@@ -1996,8 +1888,8 @@ struct BatchCtx {
     unsigned long long *head = nullptr;
     unsigned *flags = nullptr, *flags_host = nullptr;
     size_t cap_slices = 0, cap_groups = 0, cap_members = 0, cap_done = 0;
-    void *msegs = nullptr, *mwseg = nullptr;  // row march plan
-    size_t cap_msegs = 0, cap_mwseg = 0;
+    void *msegs = nullptr;  // row march items
+    size_t cap_msegs = 0;
     unsigned *mctr = nullptr;                  // row march: per-step item counters
     cudaGraphExec_t exec = nullptr;
     std::vector<char> key;
@@ -2187,34 +2079,22 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
         std::vector<MarchMember> mm;
         for (const BatchMember &m : members) mm.push_back({m.slice, m.shot, items[m.slice].sim});
         std::vector<MarchSeg> segs;
-        std::vector<int> wseg;
         const long long maxw = (long long)sms * std::max(1, march2d_warps_per_sm(any_cpml));
-        const int item = march_item_rows();
-        int nw = 0;
-        if (item) {
-            nw = plan_march_items(mm, maxw, item, segs);
-            wseg.assign(1, 0);
-        } else {
-            plan_march(mm, maxw, segs, wseg);
-            nw = (int)wseg.size() - 1;
-        }
+        const int nw = plan_march_items(mm, maxw, march_item_rows(), segs);
         if (!ctx->mctr && (e = cudaMalloc(&ctx->mctr, 2 * sizeof(unsigned)))) return fail(e, "allocation");
-        if ((e = grow(&ctx->msegs, &ctx->cap_msegs, segs.size() * sizeof(MarchSeg))) ||
-            (e = grow(&ctx->mwseg, &ctx->cap_mwseg, wseg.size() * sizeof(int)))) {
+        if ((e = grow(&ctx->msegs, &ctx->cap_msegs, segs.size() * sizeof(MarchSeg)))) {
             if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
             ctx->exec = nullptr;
             return fail(e, "allocation");
         }
         if ((e = cudaMemcpyAsync(ctx->msegs, segs.data(), segs.size() * sizeof(MarchSeg), cudaMemcpyHostToDevice,
-                                 bst)) ||
-            (e = cudaMemcpyAsync(ctx->mwseg, wseg.data(), wseg.size() * sizeof(int), cudaMemcpyHostToDevice, bst)))
+                                 bst)))
             return fail(e, "upload");
         mb.slices = static_cast<const StepArgs<float> *>(ctx->slices);
         mb.segs = static_cast<const MarchSeg *>(ctx->msegs);
-        mb.wseg = static_cast<const int *>(ctx->mwseg);
-        mb.ctr = item ? ctx->mctr : nullptr;
+        mb.ctr = ctx->mctr;
         mb.nwarps = nw;
-        mb.nitems = item ? (int)segs.size() : 0;
+        mb.nitems = (int)segs.size();
         mb.tz = tz;
     }
     if (stepped) {  // members with global tile offsets
@@ -2387,8 +2267,9 @@ sim_status sim_create(const sim_desc *din, const void *vel, void *cuda_stream, s
         const int on[3] = {nbz > 0, nby > 0, nbx > 0};
         for (int ax = 0; ax < 3; ax++)
             if (on[ax]) {
+                // 2D kernels keep psi of two parities; 3D passes update psi in place
                 s->psi[ax][0] = A(fb * ms);
-                s->psi[ax][1] = A(fb * ms);
+                if (d.ndim == 2) s->psi[ax][1] = A(fb * ms);
                 s->zeta[ax] = A(fb * ms);
             }
     }
@@ -2418,12 +2299,9 @@ sim_status sim_create(const sim_desc *din, const void *vel, void *cuda_stream, s
         if (rc == SIM_OK) rc = s->cuda(configure_march2d(), "kernel configuration");
         s->rdone = static_cast<int *>(A(sizeof(int) * ms * max_tiles(s)));
         s->rtiles = static_cast<RTile *>(A(sizeof(RTile) * max_tiles(s)));
-        // row march: at most one segment start per warp plus one per (shot, strip)
-        const size_t maxw = (size_t)device_sms(s->dev) * 128;
-        s->cap_mwseg = maxw + 2;
-        s->cap_mseg = maxw + (size_t)ms * ((g.NX + kMarchW - 1) / kMarchW) * ((g.NZ + 3) / 4) + 2;
+        // row march: one item per (shot, strip, 4 rows) at most
+        s->cap_mseg = (size_t)ms * ((g.NX + kMarchW - 1) / kMarchW) * ((g.NZ + 3) / 4) + 2;
         s->mseg = static_cast<MarchSeg *>(A(sizeof(MarchSeg) * s->cap_mseg));
-        s->mwseg = static_cast<int *>(A(sizeof(int) * s->cap_mwseg));
         s->mslice = static_cast<StepArgs<float> *>(A(sizeof(StepArgs<float>)));
         s->mctr = static_cast<unsigned *>(A(2 * sizeof(unsigned)));
     }

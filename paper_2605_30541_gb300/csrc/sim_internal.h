@@ -199,11 +199,10 @@ int batch_blocks_per_sm(int tz, bool cpml);
 
 // Row march (march2d.cu): the 2D FP32 forward step as warps that each walk
 // down the rows [z0, z1) of one 128-column strip (bx) of one member (slice,
-// shot). Two schedules: static (ctr == NULL), where wseg[w] .. wseg[w + 1]
-// are warp w's segments, and dynamic, where the warps take the nitems
-// segments in order from the step's counter ctr[n & 1] (ctr[0] zeroed before
-// the first step; each step zeroes the next step's). tz is the tile height of
-// the slices' receiver and injection lists.
+// shot). The warps take the nitems segments in order from the step's
+// counter ctr[n & 1] (ctr[0] zeroed before the first step; each step zeroes
+// the next step's). tz is the tile height of the slices' receiver and
+// injection lists.
 constexpr int kMarchW = 128;
 struct MarchSeg {
     int slice, shot, bx, z0, z1;
@@ -212,7 +211,6 @@ struct MarchSeg {
 struct MarchArgs {
     const StepArgs<float> *slices;
     const MarchSeg *segs;
-    const int *wseg;
     unsigned *ctr;
     int nwarps;
     int nitems;

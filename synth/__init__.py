@@ -110,18 +110,40 @@ def procedural_3d(nz, ny, nx, h, seed, dtype=np.float32):
 
     v = np.empty((nz, ny, nx), dtype=dtype)
     Y, X = np.meshgrid(y, x, indexing="ij")
-    for z0 in range(nz):
+
+    def slab(z0):
         zv = np.full_like(X, z0 * h)
         yv, xv = Y.copy(), X.copy()
+        hd, t = np.empty_like(X), np.empty_like(X)
+        hang = np.empty(X.shape, dtype=bool)
         # faults are applied in order: each pulls its hanging wall down-dip
+        # (in-place form of hd = (x - fx) cos s + (y - fy) sin s; hanging
+        # where hd - z / tan(dip) > 0, moved by the throw along the dip)
         for dip, strike, throw, fx, fy in reversed(faults):
-            hd = (xv - fx) * math.cos(strike) + (yv - fy) * math.sin(strike)
-            hang = hd - zv / math.tan(dip) > 0
-            zv = np.where(hang, zv - throw * math.sin(dip), zv)
-            xv = np.where(hang, xv - throw * math.cos(dip) * math.cos(strike), xv)
-            yv = np.where(hang, yv - throw * math.cos(dip) * math.sin(strike), yv)
+            np.subtract(xv, fx, out=hd)
+            hd *= math.cos(strike)
+            np.subtract(yv, fy, out=t)
+            t *= math.sin(strike)
+            hd += t
+            np.divide(zv, math.tan(dip), out=t)
+            hd -= t
+            np.greater(hd, 0, out=hang)
+            np.subtract(zv, throw * math.sin(dip), out=zv, where=hang)
+            np.subtract(xv, throw * math.cos(dip) * math.cos(strike), out=xv, where=hang)
+            np.subtract(yv, throw * math.cos(dip) * math.sin(strike), out=yv, where=hang)
         zs = np.clip(np.rint(zv / h), 0, nz - 1) * h
         v[z0] = layered(zs, yv, xv)
+
+    # slabs are independent: large volumes build them on a thread pool (numpy
+    # releases the interpreter lock in these array operations)
+    if nz * ny * nx >= (1 << 24):
+        import os
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(max(1, min(32, os.cpu_count() or 1))) as ex:
+            list(ex.map(slab, range(nz)))
+    else:
+        for z0 in range(nz):
+            slab(z0)
     return np.clip(v, VMIN, VMAX, out=v)
 
 

@@ -1,13 +1,15 @@
 """The forward entry point for callers that cannot allocate device memory when
-they call (inside their own graph capture, with a fully reserved pool, or on
-paths where cudaMalloc's device synchronisation is not acceptable). It keeps
-its working set in a fixed array inside the library; here its gathers must
-match sim_forward's within the tolerance of the other parity tests, on two
-calls in a row (the second reuses the array the first left behind), and a
-problem larger than the array must be refused before any GPU work."""
+they call: processes whose device memory a framework's pool has reserved in
+full, and paths where cudaMalloc's device synchronisation is not acceptable.
+It keeps its working set in a fixed array inside the library. Here its gathers
+must match sim_forward's within the tolerance of the other parity tests, and
+the FP64 oracle's, on two calls in a row (the second reuses the array the
+first left behind); a call must leave the device's free memory unchanged; and
+a problem larger than the array must be refused before any GPU work."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -30,7 +32,7 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("bc", ["cpml", "sponge"])
-def test_noalloc_matches_forward_on_two_calls(pkg, bc):
+def test_noalloc_matches_forward_and_oracle_on_two_calls(pkg, bc):
     c = synth.config_c1(nt=600, bc=bc)
     rec = np.ascontiguousarray(c["rec"])
     nrec = len(rec)
@@ -38,13 +40,35 @@ def test_noalloc_matches_forward_on_two_calls(pkg, bc):
     sim = pkg.Simulator(c, c["vel"], max_shots=1, max_rec=nrec)
     refs = [sim.forward(c["wavelet"], s, rec)["gather"][0].cpu().numpy() for s in sources]
     sim.close()
+    v64, w64 = c["vel"].astype(np.float64), c["wavelet"].astype(np.float64)
+    exact = [oracle.forward(c, v64, w64, src=s[0], rec=rec)["gather"] for s in sources]
     desc = pkg.make_desc(c, max_shots=1, max_rec=nrec)
     vel = torch.as_tensor(c["vel"], device="cuda")
     w = torch.as_tensor(c["wavelet"], device="cuda")
-    for s, ref in zip(sources, refs):
+    for s, ref, ex in zip(sources, refs, exact):
         g = torch.full((c["nt"], nrec), float("nan"), device="cuda")
         pkg.sim_forward_noalloc(desc, vel, w, np.ascontiguousarray(s[0]), nrec, rec, g)
-        assert rel(g.cpu().numpy(), ref) <= 1e-4
+        out = g.cpu().numpy()
+        assert rel(out, ref) <= 1e-4
+        assert rel(out, ex) <= 1e-4
+
+
+def test_noalloc_leaves_free_device_memory_unchanged(pkg):
+    # driver-level free memory (outside torch's caching allocator) after a
+    # warm-up call and after a second call: the call allocates nothing
+    c = synth.config_c1(nt=200)
+    rec = np.ascontiguousarray(c["rec"])
+    desc = pkg.make_desc(c, max_shots=1, max_rec=len(rec))
+    vel = torch.as_tensor(c["vel"], device="cuda")
+    w = torch.as_tensor(c["wavelet"], device="cuda")
+    g = torch.empty((c["nt"], len(rec)), device="cuda")
+    src = np.ascontiguousarray(c["src"][0])
+    pkg.sim_forward_noalloc(desc, vel, w, src, len(rec), rec, g)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    pkg.sim_forward_noalloc(desc, vel, w, src, len(rec), rec, g)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
 
 
 def test_noalloc_refuses_problems_larger_than_its_array(pkg):
