@@ -121,7 +121,7 @@ def strip_cell_axes(cfg):
     return s
 
 
-def gradient_bytes_per_shot(cfg, fp16, qbytes=None):
+def gradient_bytes_per_shot(cfg, fp16, qbytes=None, levels=1):
     """Least DRAM bytes of one shot's adjoint-state gradient: per cell and
     step, the forward sweep 16 B (read p^n, p^{n-1}, c; write p^{n+1}), the
     recompute 16 B plus the imaging-term store, the adjoint sweep 16 B plus
@@ -129,11 +129,14 @@ def gradient_bytes_per_shot(cfg, fp16, qbytes=None):
     cell and axis and step, 16 B (psi, zeta read + write) in each forward-type
     sweep and 24 B in the adjoint (multipliers nu, mu read + write, the
     bracket written and read). Imaging terms are 2 B in FP16 storage, else
-    4 B (qbytes overrides). Checkpoint traffic (a few states per segment) is
-    not counted."""
+    4 B (qbytes overrides). A two-level checkpoint schedule adds one more
+    forward sweep. Checkpoint traffic (a few states per segment) is not
+    counted."""
     q = qbytes if qbytes is not None else (2 if fp16 else 4)
     cells = padded_cells(cfg)
-    return cfg["nt"] * (cells * (16 + 16 + q + 16 + q + 8) + strip_cell_axes(cfg) * (16 + 16 + 24))
+    extra = 16 * (levels - 1)
+    return cfg["nt"] * (cells * (16 + extra + 16 + q + 16 + q + 8) +
+                        strip_cell_axes(cfg) * (16 + extra + 16 + 24))
 
 
 def launches_per_solve(cfg, nsnap, path):
@@ -447,6 +450,54 @@ def gradient_timing(reps=2):
                                  "(~350 MB) are not; an effective rate on algorithmic bytes"}}
 
 
+def gradient3d_timing(pkg, sim, cfg, wav_d, src, rec, dev):
+    """The 3D volume's gradient: one shot, sim_adjoint with FP16 checkpoints
+    on the same handle (d_obs = 0, so the residual is the gather), timed on
+    its second call (the first plans and allocates the buffers and captures
+    the graph). The checkpoint schedule is the one the device-memory budget
+    allows; FP32 checkpoints are then tried and reported (on the full volume
+    they do not fit)."""
+    import torch
+    nt, nrec = cfg["nt"], len(rec)
+    d = torch.zeros((1, nt, nrec), device=dev)
+    grad = torch.zeros((cfg["nz"], cfg["ny"], cfg["nx"]), device=dev)
+    mis = np.zeros(1)
+
+    def call(fp16):
+        pkg.sim_adjoint(sim.handle, 1, wav_d, src, nrec, rec, d, None, mis, fp16, grad)
+
+    t0 = time.perf_counter()
+    call(1)
+    torch.cuda.synchronize()
+    first = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    call(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    info = pkg.sim_get_info(sim.handle)
+    peak, peak_kind = read_peaks()
+    algo = gradient_bytes_per_shot(cfg, True, qbytes=4, levels=info.adj_levels)
+    out = {"workload": "3D volume (the forward workload), 1 shot, nt=%d, FP16 checkpoints (FP32 imaging terms)" % nt,
+           "s_per_shot_3d": t, "first_call_s": first, "misfit": float(mis[0]),
+           "checkpoints": {"levels": info.adj_levels, "imaging_slots": info.adj_slots,
+                           "inner_segments": info.adj_inner, "top_checkpoints": info.adj_top,
+                           "inner_checkpoint_slots": info.adj_sub},
+           "adjoint_bytes": info.adj_bytes, "handle_device_bytes": info.device_bytes,
+           "roofline": {"bound": "hbm", "achieved": algo / t / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": algo / t / 1e9 / peak, "peak_kind": peak_kind,
+                        "algorithmic_bytes_per_shot": algo}}
+    try:
+        call(0)
+        torch.cuda.synchronize()
+        out["fp32_checkpoints"] = "fit: %d level(s)" % pkg.sim_get_info(sim.handle).adj_levels
+    except pkg.SimError as e:
+        out["fp32_checkpoints"] = "do not fit: " + str(e)
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -561,6 +612,8 @@ def run_ours(args):
     grad = None
     if rank == 0 and not args.no_grad:
         grad = gradient_timing()
+        if cfg["ndim"] == 3:
+            grad["volume"] = gradient3d_timing(pkg, sim, cfg, wav_d, src, rec, dev)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Gcell/s", "n_gpus": world, "steps": args.steps,

@@ -93,6 +93,11 @@ typedef struct {
     int max_rec;          /* most receivers one call carries */
     int precision;        /* sim_precision */
     int skip_cfl_check;   /* 1: accept dt above the stability bound (tests only) */
+    int pad0;
+    long long adj_budget; /* device bytes the gradient's buffers may take (checkpoints,
+                             imaging terms, adjoint fields); <= 0: the free device memory
+                             at the first sim_adjoint call, less max(2 GiB, 4% of the
+                             device). Sets the checkpoint schedule (see sim_adjoint). */
 } sim_desc;
 
 /* Host-side facts about a description (no GPU needed). */
@@ -114,6 +119,14 @@ typedef struct {
                                  4 row march: one launch per step in which every warp streams
                                  down a 128-column strip of rows (2D FP32, when not resident) */
     int last_rows;            /* path 2: rows of the tallest resident subdomain (x 128 columns) */
+    /* checkpoint schedule of the gradient (0 before the first sim_adjoint call) */
+    int adj_levels;           /* 1: one checkpoint level; 2: two */
+    int adj_slots;            /* L: imaging-term slots = steps of an innermost segment */
+    int adj_inner;            /* m: innermost segments per top segment (1 with one level) */
+    int adj_top;              /* top-level checkpoints, every m L steps */
+    int adj_sub;              /* second-level checkpoint slots */
+    int pad1;
+    size_t adj_bytes;         /* device memory of the gradient's buffers */
 } sim_info;
 
 typedef struct sim_s *sim_t;
@@ -157,23 +170,43 @@ sim_status sim_forward(sim_t s, int nshots, const void *wavelet, const double *s
 
 /* Misfit J = 1/2 sum (g - d_obs)^2 over shots, steps and receivers, and its
  * exact gradient with respect to the interior velocity, by the adjoint-state
- * method on the discrete scheme. The forward pass keeps sqrt(nt)-spaced
- * checkpoints and recomputes each segment in reverse.
+ * method on the discrete scheme.
  *   d_obs      [nshots][nt][nrec]  observed data
  *   gather_out [nshots][nt][nrec]  out: modelled gather (NULL ok)
  *   misfit_out [1] (host)          out: J, accumulated over shots in FP64
  *   ckpt_fp16  1: checkpoints (2D: and the stored imaging terms) in FP16
- *              with a power-of-two scale per tile; 0: handle precision. On 3D
- *              handles the imaging terms of a segment stay FP32.
+ *              with a power-of-two scale per tile (the CPML memory: per row
+ *              of its strips); 0: handle precision. On 3D handles the
+ *              imaging terms stay FP32.
  *   grad_v     [nz][ny][nx]        out: dJ/dv ACCUMULATED (+=) in handle
  *              precision, after an FP64 sum over the shots
  * 2D and 3D (FP32) handles; sponge, no-absorption and CPML boundaries (for
  * CPML the exact transpose of the psi / zeta recursions, their state kept
  * with every checkpoint, the CPML coefficients, set from the model maximum by
- * sim_set_model, held fixed as constants of the map). */
+ * sim_set_model, held fixed as constants of the map).
+ * Checkpointing (optimal checkpointing is the trade-off the paper names,
+ * Sec. 5): the forward sweep keeps the state at the start of each segment
+ * and the reverse sweep recomputes the segments. The first call allocates
+ * the buffers for the cheapest schedule that fits desc.adj_budget: sqrt(nt)
+ * segments (two forward sweeps), else the one-level split needing least
+ * memory, else two levels (a top segment is recomputed once keeping inner
+ * checkpoints: three forward sweeps); SIM_ERR_OOM when even that does not
+ * fit. Each checkpoint holds p^{n-1}, p^n and the CPML memory on its strips
+ * only, at the storage precision. A later FP32-storage call on buffers sized
+ * for FP16 frees and re-plans them. sim_get_info reports the schedule. */
 sim_status sim_adjoint(sim_t s, int nshots, const void *wavelet, const double *src_pos,
                        int nrec, const double *rec_pos, const void *d_obs,
                        void *gather_out, double *misfit_out, int ckpt_fp16, void *grad_v);
+
+/* Vector-Jacobian product of the gather map: grad_v += (dg/dv)^T cot, for a
+ * cotangent cot [nshots][nt][nrec] of the gathers g(v) (what a
+ * torch.autograd backward pass needs). The same sweeps as sim_adjoint with
+ * cot injected directly as the adjoint source, so a cotangent much smaller
+ * than the gathers loses no precision to a difference g - d. Arguments and
+ * errors as in sim_adjoint (no misfit). */
+sim_status sim_adjoint_vjp(sim_t s, int nshots, const void *wavelet, const double *src_pos,
+                           int nrec, const double *rec_pos, const void *cot,
+                           void *gather_out, int ckpt_fp16, void *grad_v);
 
 /* One entry of a batch: a handle (model + grid) and its shots. */
 typedef struct {
@@ -184,15 +217,31 @@ typedef struct {
     int nrec;
     const double *rec_pos;    /* [nrec][ndim] (host) */
     void *gather;             /* [nshots][nt][nrec] out (NULL: not recorded) */
+    /* gradient mode only (NULL in forward mode): */
+    const void *d_obs;        /* [nshots][nt][nrec] observed data */
+    double *grad_sum_fp64;    /* [nz][ny][nx] DEVICE, += dJ/dv of this item's shots, summed in FP64 */
+    double *misfit;           /* [1] host, out: J of this item's shots */
 } sim_batch_item;
 
-/* Forward modelling of many shots on many (uneven) grids as ONE persistent
- * kernel launch, replayed from a captured CUDA graph. All handles must share
- * dt, nt and precision. Tiles of all shots are scheduled as a work list whose
- * entries wait only on their spatial neighbours of the previous step; every
- * such wait is bounded and returns SIM_ERR_TIMEOUT rather than hanging.
+/* Forward modelling of many shots on many (uneven) 2D FP32 grids in one
+ * batch. All handles must share dt and nt. Default schedule: per time step
+ * ONE launch of the row-march kernel over every (slice, shot, strip) of the
+ * batch, warps taking row items from a per-step counter; the nt launches are
+ * captured as one CUDA graph and replayed. The schedule (row march, the
+ * stepped tile kernel, or one persistent dataflow launch for all steps whose
+ * tiles wait on their neighbours with bounded waits, SIM_ERR_TIMEOUT when a
+ * wait gives up) and the tile height are picked by timing on the first call
+ * for a batch shape; GSIM_BATCH=march|stepped|persistent forces one.
  * `cuda_stream` as in sim_create. */
 sim_status sim_batch(int nitems, const sim_batch_item *items, void *cuda_stream);
+
+/* The batch with a mode: 0 forward (sim_batch); 1 gradient: for each item,
+ * the misfit of its shots against d_obs and its velocity gradient (as in
+ * sim_adjoint, checkpoints in FP16 when ckpt_fp16) added in FP64 to the
+ * item's grad_sum_fp64 (one array per slice; the caller sums slices that
+ * share a model). 2D and 3D handles of any precision in mode 1. Items run
+ * one after another, ordered on cuda_stream. */
+sim_status sim_batch_ex(int nitems, const sim_batch_item *items, int mode, int ckpt_fp16, void *cuda_stream);
 
 /* No counterpart in the paper. A forward solve for callers that cannot
  * allocate device memory at the time they call: processes whose device

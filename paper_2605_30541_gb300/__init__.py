@@ -15,7 +15,7 @@ from . import abi
 from .abi import SIM_BC, SIM_FP32, SIM_FP64, SimBatchItem, SimDesc, SimInfo
 
 __all__ = ["SimError", "make_desc", "sim_plan", "sim_create", "sim_set_model", "sim_forward",
-           "sim_adjoint", "sim_batch", "sim_sync", "sim_get_info", "sim_last_error", "sim_destroy",
+           "sim_adjoint", "sim_adjoint_vjp", "sim_batch", "sim_batch_ex", "batch_gradient", "sim_sync", "sim_get_info", "sim_last_error", "sim_destroy",
            "Simulator", "batch", "sim_forward_noalloc", "sim_wavelet_bandpass", "bandpass_ricker",
            "sim_model_squish", "sim_model_fault", "sim_model_deposit"]
 
@@ -37,8 +37,9 @@ def _check(code, handle=None):
 
 
 def make_desc(cfg, max_shots=1, max_rec=0, precision=SIM_FP32, snap_fp16=False, f_max=0.0,
-              skip_cfl_check=False):
-    """sim_desc from a problem dict (keys as produced by ``synth``)."""
+              skip_cfl_check=False, adj_budget=0):
+    """sim_desc from a problem dict (keys as produced by ``synth``);
+    adj_budget: device bytes the gradient's buffers may take (0: automatic)."""
     d = SimDesc()
     abi.load().sim_desc_init(ctypes.byref(d))
     d.ndim = int(cfg["ndim"])
@@ -60,6 +61,7 @@ def make_desc(cfg, max_shots=1, max_rec=0, precision=SIM_FP32, snap_fp16=False, 
     d.max_rec = int(max_rec)
     d.precision = int(precision)
     d.skip_cfl_check = int(bool(skip_cfl_check))
+    d.adj_budget = int(adj_budget)
     return d
 
 
@@ -127,10 +129,20 @@ def sim_adjoint(handle, nshots, wavelet, src_pos, nrec, rec_pos, d_obs, gather_o
                                   _ptr(grad_v)), handle)
 
 
+def sim_adjoint_vjp(handle, nshots, wavelet, src_pos, nrec, rec_pos, cot, gather_out, ckpt_fp16, grad_v):
+    _check(abi.load().sim_adjoint_vjp(handle, nshots, _ptr(wavelet), _ptr(src_pos), nrec, _ptr(rec_pos),
+                                      _ptr(cot), _ptr(gather_out), int(ckpt_fp16), _ptr(grad_v)), handle)
+
+
 def sim_batch(items, stream=None):
     """items: sequence of SimBatchItem (see batch() for a friendlier form)."""
     arr = (SimBatchItem * len(items))(*items)
     _check(abi.load().sim_batch(len(items), arr, _stream(stream)))
+
+
+def sim_batch_ex(items, mode, ckpt_fp16=0, stream=None):
+    arr = (SimBatchItem * len(items))(*items)
+    _check(abi.load().sim_batch_ex(len(items), arr, int(mode), int(ckpt_fp16), _stream(stream)))
 
 
 def batch(entries, stream=None):
@@ -154,6 +166,33 @@ def batch(entries, stream=None):
         outs.append(g)
     sim_batch(items, stream)
     return outs
+
+
+def batch_gradient(entries, ckpt_fp16=False, stream=None):
+    """Gradient mode of the batch (sim_batch_ex mode 1). entries: dicts with
+    sim, wavelet, src, rec, d_obs [nshots, nt, nrec] and optionally
+    grad (FP64 device tensor of the interior shape, accumulated; allocated
+    zeroed if absent). Returns (list of FP64 gradients, list of misfits)."""
+    import torch
+    keep, items, grads, mis = [], [], [], []
+    for e in entries:
+        sim = e["sim"]
+        d = sim.desc
+        src, nshots = _positions(e["src"], d.ndim)
+        rec, nrec = _positions(e["rec"], d.ndim)
+        w = sim._tensor(e["wavelet"])
+        dob = sim._tensor(e["d_obs"]).contiguous()
+        g = e.get("grad")
+        if g is None:
+            g = torch.zeros(sim.interior_shape, dtype=torch.float64, device="cuda")
+        m = np.zeros(1)
+        keep += [src, rec, w, dob, g, m]
+        items.append(SimBatchItem(sim.handle, nshots, _ptr(w), _ptr(src), nrec, _ptr(rec), None, _ptr(dob), _ptr(g),
+                                  m.ctypes.data))
+        grads.append(g)
+        mis.append(m)
+    sim_batch_ex(items, 1, ckpt_fp16, stream)
+    return grads, [float(m[0]) for m in mis]
 
 
 def sim_forward_noalloc(desc, vel, wavelet, src_pos, nrec, rec_pos, gather, stream=None):
@@ -222,10 +261,10 @@ class Simulator:
     handle's device unless host buffers are passed in."""
 
     def __init__(self, cfg, vel=None, max_shots=1, max_rec=0, precision=SIM_FP32, snap_fp16=False,
-                 f_max=0.0, skip_cfl_check=False, stream=None):
+                 f_max=0.0, skip_cfl_check=False, stream=None, adj_budget=0):
         import torch
         self.cfg = dict(cfg)
-        self.desc = make_desc(cfg, max_shots, max_rec, precision, snap_fp16, f_max, skip_cfl_check)
+        self.desc = make_desc(cfg, max_shots, max_rec, precision, snap_fp16, f_max, skip_cfl_check, adj_budget)
         self.dtype = torch.float64 if precision == SIM_FP64 else torch.float32
         self.handle = None
         if vel is not None:

@@ -33,6 +33,7 @@ class SimDesc(ctypes.Structure):
         ("f_max", ctypes.c_double), ("snap_every", ctypes.c_int), ("snap_begin", ctypes.c_int),
         ("snap_end", ctypes.c_int), ("snap_fp16", ctypes.c_int), ("max_shots", ctypes.c_int),
         ("max_rec", ctypes.c_int), ("precision", ctypes.c_int), ("skip_cfl_check", ctypes.c_int),
+        ("pad0", ctypes.c_int), ("adj_budget", ctypes.c_longlong),
     ]
 
 
@@ -44,6 +45,9 @@ class SimInfo(ctypes.Structure):
         ("c_damp", ctypes.c_double * 6), ("cells_per_shot", ctypes.c_longlong),
         ("device_bytes", ctypes.c_size_t), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
         ("tile_z", ctypes.c_int), ("last_path", ctypes.c_int), ("last_rows", ctypes.c_int),
+        ("adj_levels", ctypes.c_int), ("adj_slots", ctypes.c_int), ("adj_inner", ctypes.c_int),
+        ("adj_top", ctypes.c_int), ("adj_sub", ctypes.c_int), ("pad1", ctypes.c_int),
+        ("adj_bytes", ctypes.c_size_t),
     ]
 
 
@@ -51,7 +55,8 @@ class SimBatchItem(ctypes.Structure):
     _fields_ = [
         ("sim", ctypes.c_void_p), ("nshots", ctypes.c_int), ("wavelet", ctypes.c_void_p),
         ("src_pos", ctypes.c_void_p), ("nrec", ctypes.c_int), ("rec_pos", ctypes.c_void_p),
-        ("gather", ctypes.c_void_p),
+        ("gather", ctypes.c_void_p), ("d_obs", ctypes.c_void_p), ("grad_sum_fp64", ctypes.c_void_p),
+        ("misfit", ctypes.c_void_p),
     ]
 
 
@@ -82,7 +87,9 @@ _PROTOS = {
     "sim_set_model": (_I, [_VP, _VP]),
     "sim_forward": (_I, [_VP, _I, _VP, _VP, _I, _VP, _VP, _VP, _VP]),
     "sim_adjoint": (_I, [_VP, _I, _VP, _VP, _I, _VP, _VP, _VP, _VP, _I, _VP]),
+    "sim_adjoint_vjp": (_I, [_VP, _I, _VP, _VP, _I, _VP, _VP, _VP, _I, _VP]),
     "sim_batch": (_I, [_I, ctypes.POINTER(SimBatchItem), _VP]),
+    "sim_batch_ex": (_I, [_I, ctypes.POINTER(SimBatchItem), _I, _I, _VP]),
     "sim_forward_noalloc": (_I, [ctypes.POINTER(SimDesc), _VP, _VP, _VP, _I, _VP, _VP, _VP]),
     "sim_wavelet_bandpass": (_I, [_I, _D, _D, _D, _D, _I, _I, _VP, _VP]),
     "sim_model_squish": (_I, [_I, _I, _I, _VP, _VP, _VP, _F, _I, _VP, _VP, _VP]),

@@ -1,13 +1,14 @@
 """torch.autograd binding of the solver: velocity -> shot gathers, with the
-backward pass done by libsim's adjoint-state kernels (sim_adjoint).
+backward pass done by libsim's adjoint-state kernels.
 
 For a cotangent c = dL/dg of the gathers, the vector-Jacobian product J^T c is
-the gradient of 1/2 ||g - d||^2 with d = g - c, which is exactly what
-sim_adjoint returns; the forward states are recomputed from checkpoints."""
+what sim_adjoint_vjp returns: the adjoint sweep driven by c itself (no
+difference g - d is formed, so a cotangent far smaller than the gathers keeps
+its precision); the forward states are recomputed from checkpoints."""
 import numpy as np
 import torch
 
-from . import sim_adjoint, sim_forward, sim_set_model
+from . import sim_adjoint_vjp, sim_forward, sim_set_model
 
 
 class _Gathers(torch.autograd.Function):
@@ -30,10 +31,10 @@ class _Gathers(torch.autograd.Function):
         vel_c, w, g = ctx.saved_tensors
         sim = ctx.sim
         sim_set_model(sim.handle, vel_c)
-        d_obs = (g - cot.to(g.dtype)).contiguous()
+        c = cot.to(g.dtype).contiguous()
         grad = torch.zeros_like(vel_c)
-        sim_adjoint(sim.handle, ctx.src.shape[0], w, ctx.src, ctx.rec.shape[0], ctx.rec, d_obs, None, None,
-                    int(ctx.fp16), grad)
+        sim_adjoint_vjp(sim.handle, ctx.src.shape[0], w, ctx.src, ctx.rec.shape[0], ctx.rec, c, None,
+                        int(ctx.fp16), grad)
         return grad.to(vel_c.dtype), None, None, None, None, None
 
 

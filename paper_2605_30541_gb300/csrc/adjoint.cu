@@ -1,5 +1,7 @@
 // Support kernels of the adjoint-state gradient: checkpoint store/restore
-// (FP32/FP64 copy or FP16 with a power-of-two scale per tile), the data
+// (FP32/FP64 copy or FP16 with a power-of-two scale per tile; the CPML
+// memory of an axis only on the boxes of its strips, where it can be
+// non-zero, with a scale per row), the data
 // residual with its misfit, and the final FP64 fold of the per-shot imaging
 // sums onto the interior velocity cells (absorbing cells replicate the
 // nearest interior cell, so their contributions land on the edge cells).
@@ -81,6 +83,53 @@ __global__ void __launch_bounds__(NTH) k_load(const Geom g, T *field, const void
     }
 }
 
+// Boxes of the computational grid (the CPML strips of one axis): one warp per
+// (row of a box, shot). A box row is the x run [x0, x1) at one (z, y); the
+// compact copy is [shot][rows of box 0, box 1, ...][x] and, in FP16, carries
+// one power-of-two scale per (shot, row).
+__device__ __forceinline__ int box_of(const CkBoxes &B, long long r) {
+    int k = 0;
+    while (k + 1 < B.n && B.row0[k + 1] <= r) k++;
+    return k;
+}
+
+template <typename T, bool STORE>
+__global__ void __launch_bounds__(256) k_boxes(const Geom g, const CkBoxes B, T *field, void *cmp, float *scale,
+                                               int fp16, int nshots) {
+    const int lane = threadIdx.x & 31;
+    const long long rows = B.row0[B.n];
+    const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (w >= rows * nshots) return;
+    const int shot = (int)(w / rows);
+    const long long r = w - (long long)shot * rows;
+    const int k = box_of(B, r);
+    const CkBox &b = B.b[k];
+    const long long lr = r - B.row0[k];
+    const int ny = b.y1 - b.y0, len = b.x1 - b.x0;
+    const int z = b.z0 + (int)(lr / ny), y = b.y0 + (int)(lr % ny);
+    T *f = field + (long long)shot * g.fstride + cell_off(g, z, y, b.x0);
+    const long long e0 = (long long)shot * B.elem0[B.n] + B.elem0[k] + lr * len;
+    const long long si = (long long)shot * rows + r;
+    if (STORE) {
+        float inv = 1.f;
+        if (fp16) {
+            float m = 0.f;
+            for (int i = lane; i < len; i += 32) m = fmaxf(m, fabsf((float)f[i]));
+            const float sc = pow2_scale(warp_max(m));
+            inv = 1.f / sc;
+            if (lane == 0) scale[si] = sc;
+        }
+        for (int i = lane; i < len; i += 32) {
+            if (fp16) static_cast<__half *>(cmp)[e0 + i] = __float2half_rn((float)f[i] * inv);
+            else static_cast<T *>(cmp)[e0 + i] = f[i];
+        }
+    } else {
+        const float sc = fp16 ? scale[si] : 1.f;
+        for (int i = lane; i < len; i += 32)
+            f[i] = fp16 ? T(__half2float(static_cast<const __half *>(cmp)[e0 + i]) * sc) : static_cast<const T *>(cmp)[e0 + i];
+    }
+}
+
 template <typename T>
 __global__ void k_residual(const T *__restrict__ gath, const T *__restrict__ d, T *res, long long n, double *part) {
     __shared__ double sm[256];
@@ -147,6 +196,26 @@ cudaError_t launch_load_state(const Geom &g, T *field, const void *src, const fl
 }
 
 template <typename T>
+cudaError_t launch_store_boxes(const Geom &g, const CkBoxes &b, const T *field, void *dst, float *scale, int fp16,
+                               int nshots, cudaStream_t st) {
+    const long long warps = b.row0[b.n] * nshots;
+    if (warps == 0) return cudaSuccess;
+    k_boxes<T, true><<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(g, b, const_cast<T *>(field), dst, scale, fp16,
+                                                                  nshots);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_load_boxes(const Geom &g, const CkBoxes &b, T *field, const void *src, const float *scale,
+                              int fp16, int nshots, cudaStream_t st) {
+    const long long warps = b.row0[b.n] * nshots;
+    if (warps == 0) return cudaSuccess;
+    k_boxes<T, false><<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(g, b, field, const_cast<void *>(src),
+                                                                   const_cast<float *>(scale), fp16, nshots);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_residual(const T *g, const T *d, T *res, long long n, double *part, int nblocks, cudaStream_t st) {
     k_residual<T><<<nblocks, 256, 0, st>>>(g, d, res, n, part);
     return cudaGetLastError();
@@ -170,6 +239,10 @@ cudaError_t launch_add_gradient(const double *acc, T *grad, long long n, cudaStr
                                                int, int, cudaStream_t);                                       \
     template cudaError_t launch_load_state<T>(const Geom &, T *, const void *, const float *, int, int,        \
                                               long long, int, int, cudaStream_t);                             \
+    template cudaError_t launch_store_boxes<T>(const Geom &, const CkBoxes &, const T *, void *, float *, int, int, \
+                                               cudaStream_t);                                                \
+    template cudaError_t launch_load_boxes<T>(const Geom &, const CkBoxes &, T *, const void *, const float *, int, \
+                                              int, cudaStream_t);                                            \
     template cudaError_t launch_residual<T>(const T *, const T *, T *, long long, double *, int, cudaStream_t); \
     template cudaError_t launch_fold_gradient<T>(const Geom &, const T *, long long, int, const T *,      \
                                                  double, double *, cudaStream_t);                             \

@@ -215,6 +215,20 @@ struct ResidentPlan {
     TileMap map;
 };
 
+// Checkpoint schedule of the gradient and the sizes it was planned for
+// (see plan_adjoint).
+struct AdjPlan {
+    int fp16 = 0;      // storage precision the buffers were sized for
+    int levels = 1;
+    int L = 1;         // imaging-term slots = steps of an innermost segment
+    int m = 1;         // innermost segments per top segment (1 with one level)
+    int n1 = 1;        // top-level checkpoints
+    int n2 = 0;        // second-level checkpoint slots (m - 2: the first inner
+                       // segment restarts from the top checkpoint, the last
+                       // from the recompute itself)
+    size_t ck_bytes = 0, q_bytes = 0, fixed_bytes = 0, total = 0;
+};
+
 struct sim_s {
     sim_desc d{};
     Geom g{};
@@ -268,17 +282,18 @@ struct sim_s {
     unsigned *mctr = nullptr;              // row march: per-step item counters
     int last_path = 0, last_rows = 0;      // see sim_info
     int zchunk = 0;                        // z-march chunk of the 3D kernel
-    // adjoint-state buffers, allocated by the first sim_adjoint call
+    // adjoint-state buffers, allocated by the first sim_adjoint call (on
+    // their own list: a call that needs a larger plan frees and re-plans them)
     bool adj_ready = false;
-    int seg = 0, nseg = 0;
+    AdjPlan plan;
+    std::vector<void *> adj_allocs;
+    size_t adj_bytes = 0;
     void *ubuf = nullptr, *Gbuf = nullptr, *qbuf = nullptr, *ckpt = nullptr, *res = nullptr, *dobs = nullptr;
     // 2D FP32 CPML gradient: multipliers nu [z, x][parity], mu [z, x], the
     // adjoint Laplacian term, and checkpoints of (psi_z, zeta_z, psi_x, zeta_x)
     void *cnu[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}}, *cmu[3] = {nullptr, nullptr, nullptr};
     void *cext = nullptr;
-    void *ckcpml = nullptr;
-    float *ckcpml_scale = nullptr;
-    float *qscale = nullptr, *ckscale = nullptr;
+    float *qscale = nullptr;
     double *acc = nullptr, *mpart = nullptr;
     void *gradst = nullptr;
     int *inj2_start = nullptr;
@@ -1316,9 +1331,204 @@ sim_status forward_t(sim_t s, int nshots, const void *wavelet, const double *src
 
 constexpr int kResidBlocks = 1024;
 
-// Checkpoint fields of the CPML state: psi and zeta of each axis (2D: z and
-// x, 4 fields; 3D: 6).
-int cpml_ckpt_fields(const Geom &g) { return g.ndim == 3 ? 6 : 4; }
+// ---------------------------------------------------------------- adjoint plan
+//
+// The gradient needs the forward states in reverse order. They are rebuilt
+// from checkpoints: the forward sweep keeps the state (p^{n-1}, p^n and the
+// CPML memory) at the start of every top segment; in reverse, each top
+// segment is restored and recomputed. With one level, the recompute records
+// the imaging terms Q' of the whole segment into L slots and the adjoint
+// sweep consumes them (two forward sweeps in all). With two levels, a top
+// segment of m L steps is first recomputed once keeping a second-level
+// checkpoint every L steps, then each inner segment is restored, recorded
+// and swept as above (three forward sweeps). Memory: checkpoint slots
+// (n1 + n2) x one state at the storage precision, plus L imaging-term slots.
+// The plan is the cheapest that fits the device-memory budget: sqrt(nt)
+// segments if they fit, else the one-level split that needs least memory,
+// else the two-level one that needs least (the trade-off of optimal
+// checkpointing; Sec. 5 names it).
+
+// Checkpoint fields of the CPML state: psi and zeta of each absorbing axis.
+// Field j of a checkpoint: axis cpml_axes[j / 2], psi (even j) or zeta (odd).
+int cpml_ckpt_axes(const sim_s *s, int axes[3]) {
+    int k = 0;
+    for (int ax = 0; ax < 3; ax++)
+        if (s->psi[ax][0]) axes[k++] = ax;
+    return k;
+}
+
+// The strip boxes of axis ax (where its CPML memory can be non-zero).
+CkBoxes strip_boxes(const Geom &g, int ax) {
+    CkBoxes B{};
+    const int N[3] = {g.NZ, g.NY, g.NX}, lo[3] = {g.nbz0, g.nby0, g.nbx0}, hi[3] = {g.nbz1, g.nby1, g.nbx1};
+    const int r0[2] = {0, N[ax] - hi[ax]}, r1[2] = {lo[ax], N[ax]};
+    for (int side = 0; side < 2; side++) {
+        if (r1[side] <= r0[side]) continue;
+        CkBox b{0, g.NZ, 0, g.NY, 0, g.NX};
+        if (ax == 0) b.z0 = r0[side], b.z1 = r1[side];
+        if (ax == 1) b.y0 = r0[side], b.y1 = r1[side];
+        if (ax == 2) b.x0 = r0[side], b.x1 = r1[side];
+        B.b[B.n++] = b;
+    }
+    for (int k = 0; k < B.n; k++) {
+        const CkBox &b = B.b[k];
+        const long long rows = (long long)(b.z1 - b.z0) * (b.y1 - b.y0);
+        B.row0[k + 1] = B.row0[k] + rows;
+        B.elem0[k + 1] = B.elem0[k] + rows * (b.x1 - b.x0);
+    }
+    return B;
+}
+
+// Layout of one checkpoint slot (all max_shots shots): the two pressure
+// states, their per-tile FP16 scales, then per CPML field its strip boxes
+// and per-row scales. Byte offsets within the slot.
+struct CkLayout {
+    int ckx = 0, ckz = 0;          // store tiles of the pressure states
+    size_t state = 0;              // elements of one pressure state (all shots)
+    size_t off_scale = 0;          // byte offset of the state scales
+    int nf = 0;                    // CPML fields
+    int ax[6] = {0, 0, 0, 0, 0, 0};
+    CkBoxes box[3];                // per axis (index into ax order)
+    size_t off_f[6] = {0, 0, 0, 0, 0, 0}, off_fs[6] = {0, 0, 0, 0, 0, 0};
+    size_t bytes = 0;              // per slot
+};
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+CkLayout ck_layout(const sim_s *s, int fp16) {
+    const Geom &g = s->g;
+    const int ms = s->d.max_shots;
+    const size_t es = fp16 ? 2 : s->esz;
+    CkLayout c;
+    c.ckx = (g.NX + kTileX2 - 1) / kTileX2;
+    c.ckz = (g.NZ * g.NY + kTileZ2 - 1) / kTileZ2;
+    c.state = (size_t)ms * g.NZ * g.NY * g.NX;
+    size_t off = align256(2 * c.state * es);
+    c.off_scale = off;
+    off += align256((size_t)2 * ms * c.ckx * c.ckz * sizeof(float));
+    int axes[3];
+    const int na = s->d.bc == SIM_BC_CPML ? cpml_ckpt_axes(s, axes) : 0;
+    for (int k = 0; k < na; k++) {
+        c.box[k] = strip_boxes(g, axes[k]);
+        for (int z = 0; z < 2; z++) {
+            const int j = 2 * k + z;
+            c.ax[j] = axes[k];
+            c.off_f[j] = off;
+            off += align256((size_t)ms * c.box[k].elem0[c.box[k].n] * es);
+            c.off_fs[j] = off;
+            off += align256((size_t)ms * c.box[k].row0[c.box[k].n] * sizeof(float));
+        }
+    }
+    c.nf = 2 * na;
+    c.bytes = off;
+    return c;
+}
+
+// Bytes of one imaging-term slot (all max_shots shots) and its scales.
+size_t q_slot_bytes(const sim_s *s, int fp16) {
+    const int ms = s->d.max_shots;
+    if (s->g.ndim == 3) return align256((size_t)ms * s->g.fstride * sizeof(float));  // 3D slots are FP32
+    return align256((size_t)ms * s->g.fstride * (fp16 ? 2 : s->esz));
+}
+size_t q_scale_bytes(const sim_s *s) { return align256((size_t)s->d.max_shots * max_tiles(s) * sizeof(float)); }
+
+// Buffers of the gradient other than checkpoints and imaging-term slots.
+size_t adjoint_fixed_bytes(const sim_s *s) {
+    const Geom &g = s->g;
+    const sim_desc &d = s->d;
+    const size_t fb = align256((size_t)d.max_shots * g.fstride * s->esz);
+    const size_t nint = (size_t)g.nz * g.ny * g.nx;
+    const size_t nrows = (size_t)d.max_shots * d.nt * std::max(1, d.max_rec);
+    size_t b = 3 * fb;  // u (two parities), G
+    if (d.bc == SIM_BC_CPML) {
+        int axes[3];
+        b += (size_t)cpml_ckpt_axes(s, axes) * 3 * fb;  // nu (two parities), mu
+        if (g.ndim == 2) b += fb;                       // the bracket
+    }
+    b += 2 * align256(nrows * s->esz) + align256(nint * sizeof(double)) + align256(nint * s->esz);
+    b += align256(kResidBlocks * sizeof(double)) + 3 * align256(s->cap_grp * sizeof(InjEntryT<double>) + s->cap_start * 4);
+    if (g.ndim == 3) b += 4 * align256(8 * (size_t)std::max(d.max_shots, std::max(1, d.max_rec)) * sizeof(Inj3));
+    return b;
+}
+
+sim_status plan_adjoint(sim_t s, int fp16, AdjPlan &P) {
+    const int nt = s->d.nt;
+    P = AdjPlan{};
+    P.fp16 = fp16;
+    P.ck_bytes = ck_layout(s, fp16).bytes;
+    P.q_bytes = q_slot_bytes(s, fp16) + (s->g.ndim == 2 ? q_scale_bytes(s) : 0);
+    P.fixed_bytes = adjoint_fixed_bytes(s);
+    long long budget = s->d.adj_budget;
+    size_t freeb = 0, totalb = 0;
+    if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) {
+        cudaGetLastError();
+        return s->fail(SIM_ERR_CUDA, "cudaMemGetInfo failed");
+    }
+    if (budget <= 0) {
+        const size_t margin = std::max<size_t>(2ull << 30, totalb / 25);
+        budget = freeb > margin ? (long long)(freeb - margin) : 0;
+    }
+    auto mem = [&](int levels, int L, int m, int &n1, int &n2) {
+        n1 = (nt + L * m - 1) / (L * m);
+        n2 = levels == 2 ? std::max(0, m - 2) : 0;
+        return (double)(n1 + n2) * P.ck_bytes + (double)L * P.q_bytes;
+    };
+    const double room = (double)budget - (double)P.fixed_bytes;
+    auto take = [&](int levels, int L, int m) {
+        P.levels = levels;
+        P.L = L;
+        P.m = m;
+        P.total = (size_t)(mem(levels, L, m, P.n1, P.n2) + P.fixed_bytes);
+        return SIM_OK;
+    };
+    int n1, n2;
+    const int Ls = (int)std::ceil(std::sqrt((double)nt));
+    if (mem(1, Ls, 1, n1, n2) <= room) return take(1, Ls, 1);
+    double best = 1e300;
+    int bl = 1;
+    for (int L = 1; L <= nt; L++) {
+        const double v = mem(1, L, 1, n1, n2);
+        if (v < best) best = v, bl = L;
+    }
+    if (best <= room) return take(1, bl, 1);
+    best = 1e300;
+    int bm = 2;
+    for (int L = 1; L <= nt; L++) {
+        const int mmax = (nt + L - 1) / L;
+        const int mhi = std::min(mmax, 2 * (int)std::ceil(std::sqrt((double)nt / L)) + 2);
+        for (int m = 2; m <= mhi; m++) {
+            const double v = mem(2, L, m, n1, n2);
+            if (v < best) best = v, bl = L, bm = m;
+        }
+    }
+    if (best <= room) return take(2, bl, bm);
+    return s->fail(SIM_ERR_OOM,
+                   "the gradient needs %.2f GB of device memory at least (%.2f GB of checkpoints and imaging terms "
+                   "with two checkpoint levels) and %.2f GB are available",
+                   (best + P.fixed_bytes) / 1e9, best / 1e9, (double)budget / 1e9);
+}
+
+// Free the adjoint buffers (and every captured graph, which may use them).
+void free_adjoint(sim_t s) {
+    cudaStreamSynchronize(s->st);
+    if (s->cst) cudaStreamSynchronize(s->cst);
+    for (auto &kv : s->graphs) cudaGraphExecDestroy(kv.second);
+    s->graphs.clear();
+    for (void *p : s->adj_allocs) cudaFree(p);
+    s->adj_allocs.clear();
+    s->bytes -= s->adj_bytes;
+    s->adj_bytes = 0;
+    s->adj_ready = false;
+    s->ubuf = s->Gbuf = s->qbuf = s->ckpt = s->res = s->dobs = s->cext = s->gradst = nullptr;
+    for (int ax = 0; ax < 3; ax++) s->cnu[ax][0] = s->cnu[ax][1] = s->cmu[ax] = nullptr;
+    s->qscale = nullptr;
+    s->acc = s->mpart = nullptr;
+    s->inj2_start = nullptr;
+    s->inj2_grp = nullptr;
+    s->inj2_ent = nullptr;
+    s->src3g = s->res3g = nullptr;
+    s->src3e = s->res3e = nullptr;
+}
 
 // Zero the CPML multipliers (both parities) and the 2D bracket of `nshots`
 // shots before an adjoint sweep.
@@ -1335,22 +1545,34 @@ cudaError_t reset_cpml_adjoint(const sim_s *s, int nshots, cudaStream_t st) {
     return e;
 }
 
-sim_status ensure_adjoint(sim_t s) {
-    if (s->adj_ready) return SIM_OK;
+// Allocate the adjoint buffers for checkpoints at the requested storage
+// precision (re-planned when earlier buffers were sized for FP16 and FP32
+// storage is asked for).
+sim_status ensure_adjoint(sim_t s, int fp16) {
+    if (s->adj_ready && (!s->plan.fp16 || fp16)) return SIM_OK;
+    if (s->adj_ready) free_adjoint(s);
     const sim_desc &d = s->d;
     const Geom &g = s->g;
-    s->seg = (int)std::ceil(std::sqrt((double)d.nt));
-    s->nseg = (d.nt + s->seg - 1) / s->seg;
+    AdjPlan P;
+    if (sim_status r = plan_adjoint(s, fp16, P)) return r;
     const int ms = d.max_shots;
-    const size_t ncomp = (size_t)g.NZ * g.NY * g.NX;
-    const long long ntiles = max_tiles(s);
+    const size_t nint = (size_t)g.nz * g.ny * g.nx;
     const size_t nrows = (size_t)ms * d.nt * std::max(1, d.max_rec);
+    const size_t fb = (size_t)ms * g.fstride * s->esz;
     sim_status rc = SIM_OK;
-    auto A = [&](size_t n) { return rc == SIM_OK ? s->alloc(n, &rc) : nullptr; };
-    s->ubuf = A(2 * (size_t)ms * g.fstride * s->esz);
-    s->Gbuf = A((size_t)ms * g.fstride * s->esz);
-    if (d.bc == SIM_BC_CPML) {  // multipliers of each absorbing axis, and psi / zeta in every checkpoint
-        const size_t fb = (size_t)ms * g.fstride * s->esz;
+    const size_t before = s->bytes;
+    auto A = [&](size_t n) {
+        if (rc != SIM_OK) return (void *)nullptr;
+        void *p = s->alloc(n, &rc);
+        if (p) {
+            s->allocs.pop_back();  // owned by the adjoint list, freed on re-plan
+            s->adj_allocs.push_back(p);
+        }
+        return p;
+    };
+    s->ubuf = A(2 * fb);
+    s->Gbuf = A(fb);
+    if (d.bc == SIM_BC_CPML) {
         for (int ax = 0; ax < 3; ax++) {
             if (!s->psi[ax][0]) continue;
             s->cnu[ax][0] = A(fb);
@@ -1358,20 +1580,14 @@ sim_status ensure_adjoint(sim_t s) {
             s->cmu[ax] = A(fb);
         }
         if (g.ndim == 2) s->cext = A(fb);
-        const int nf = cpml_ckpt_fields(g);
-        const size_t ck_t = (size_t)((g.NX + kTileX2 - 1) / kTileX2) * ((g.NZ * g.NY + kTileZ2 - 1) / kTileZ2);
-        s->ckcpml = A((size_t)s->nseg * nf * ms * ncomp * s->esz);
-        s->ckcpml_scale = static_cast<float *>(A((size_t)s->nseg * nf * ms * ck_t * sizeof(float)));
     }
-    s->qbuf = A((size_t)s->seg * ms * g.fstride * s->esz);
-    s->qscale = static_cast<float *>(A((size_t)s->seg * ms * ntiles * sizeof(float)));
-    s->ckpt = A((size_t)s->nseg * 2 * ms * ncomp * s->esz);
-    const size_t ck_tiles = (size_t)((g.NX + kTileX2 - 1) / kTileX2) * ((g.NZ * g.NY + kTileZ2 - 1) / kTileZ2);
-    s->ckscale = static_cast<float *>(A((size_t)s->nseg * 2 * ms * ck_tiles * sizeof(float)));
+    s->ckpt = A((size_t)(P.n1 + P.n2) * P.ck_bytes);
+    s->qbuf = A((size_t)P.L * q_slot_bytes(s, fp16));
+    if (g.ndim == 2) s->qscale = static_cast<float *>(A((size_t)P.L * q_scale_bytes(s)));
     s->res = A(nrows * s->esz);
     s->dobs = A(nrows * s->esz);
-    s->acc = static_cast<double *>(A((size_t)g.nz * g.ny * g.nx * sizeof(double)));
-    s->gradst = A((size_t)g.nz * g.ny * g.nx * s->esz);
+    s->acc = static_cast<double *>(A(nint * sizeof(double)));
+    s->gradst = A(nint * s->esz);
     s->mpart = static_cast<double *>(A(kResidBlocks * sizeof(double)));
     s->inj2_start = static_cast<int *>(A(s->cap_start * sizeof(int)));
     s->inj2_grp = static_cast<InjGroup *>(A(s->cap_grp * sizeof(InjGroup)));
@@ -1382,8 +1598,81 @@ sim_status ensure_adjoint(sim_t s) {
         s->res3g = static_cast<Inj3 *>(A(8 * (size_t)std::max(1, d.max_rec) * sizeof(Inj3)));
         s->res3e = static_cast<InjE3 *>(A(8 * (size_t)std::max(1, d.max_rec) * sizeof(InjE3)));
     }
-    if (rc == SIM_OK) s->adj_ready = true;
-    return rc;
+    s->adj_bytes = s->bytes - before;
+    if (rc != SIM_OK) {
+        free_adjoint(s);
+        return rc;
+    }
+    s->plan = P;
+    s->adj_ready = true;
+    return SIM_OK;
+}
+
+// Checkpoint slot k: store (or restore) the state entering step n: p^n,
+// p^{n-1} and the CPML memory of every absorbing axis (2D: psi of the
+// parity step n reads; 3D: psi kept in place).
+template <typename T>
+cudaError_t checkpoint(sim_t s, const StepArgs<T> &a, const CkLayout &c, int k, int n, bool store, int fp16,
+                       int nshots, cudaStream_t st) {
+    const Geom &g = s->g;
+    char *slot = static_cast<char *>(s->ckpt) + (size_t)k * s->plan.ck_bytes;
+    const size_t es = fp16 ? 2 : sizeof(T);
+    float *scale = reinterpret_cast<float *>(slot + c.off_scale);
+    const size_t ck_tiles = (size_t)s->d.max_shots * c.ckx * c.ckz;
+    const long long ncomp = (long long)g.NZ * g.NY * g.NX;
+    cudaError_t e = cudaSuccess;
+    for (int w = 0; w < 2 && e == cudaSuccess; w++) {  // w = 1: p^n, w = 0: p^{n-1}
+        T *f = a.pbuf[(n + 1 + w) & 1];
+        void *dst = slot + w * c.state * es;
+        e = store ? launch_store_state<T>(g, f, dst, scale + w * ck_tiles, fp16, nshots, ncomp, c.ckx, c.ckz, st)
+                  : launch_load_state<T>(g, f, dst, scale + w * ck_tiles, fp16, nshots, ncomp, c.ckx, c.ckz, st);
+    }
+    for (int j = 0; j < c.nf && e == cudaSuccess; j++) {
+        const int ax = c.ax[j];
+        T *f = static_cast<T *>(j % 2 ? s->zeta[ax] : s->psi[ax][g.ndim == 2 ? (n + 1) & 1 : 0]);
+        const CkBoxes &B = c.box[j / 2];
+        e = store ? launch_store_boxes<T>(g, B, f, slot + c.off_f[j], reinterpret_cast<float *>(slot + c.off_fs[j]),
+                                          fp16, nshots, st)
+                  : launch_load_boxes<T>(g, B, f, slot + c.off_f[j], reinterpret_cast<const float *>(slot + c.off_fs[j]),
+                                         fp16, nshots, st);
+    }
+    return e;
+}
+
+// The reverse schedule of a plan as a sequence of launches:
+//   fwd_first(n): forward step n of the first sweep (samples the gather);
+//   fwd(n): forward step n of a recompute that keeps checkpoints only;
+//   rec(n, slot): forward step n recording its imaging term into slot;
+//   adj(k, slot): adjoint step k (the slot recorded by forward step k - 1);
+//   ck(slot, n, store): store / restore the state entering step n;
+//   mid(): between the forward sweep and the reverse (residual, zeroing).
+template <typename F1, typename F2, typename F3, typename F4, typename F5, typename F6>
+cudaError_t emit_gradient(const AdjPlan &P, int nt, F1 fwd_first, F2 fwd, F3 rec, F4 adj, F5 ck, F6 mid) {
+    const int S1 = P.L * P.m;
+    cudaError_t e = cudaSuccess;
+    for (int n = 0; n < nt && e == cudaSuccess; n++) {
+        if (n % S1 == 0) e = ck(n / S1, n, true);
+        if (e == cudaSuccess) e = fwd_first(n);
+    }
+    if (e == cudaSuccess) e = mid();
+    for (int t = (nt + S1 - 1) / S1 - 1; t >= 0 && e == cudaSuccess; t--) {
+        const int t0 = t * S1, t1 = std::min(nt, t0 + S1);
+        const int msub = (t1 - t0 + P.L - 1) / P.L;
+        e = ck(t, t0, false);
+        // recompute up to the last inner segment, keeping the inner starts
+        // 1 .. msub - 2 (the first restarts from slot t, the last from here)
+        for (int n = t0; n < t0 + (msub - 1) * P.L && e == cudaSuccess; n++) {
+            if (n > t0 && (n - t0) % P.L == 0 && (n - t0) / P.L <= msub - 2) e = ck(P.n1 + (n - t0) / P.L - 1, n, true);
+            if (e == cudaSuccess) e = fwd(n);
+        }
+        for (int j = msub - 1; j >= 0 && e == cudaSuccess; j--) {
+            const int s0 = t0 + j * P.L, s1 = std::min(t1, s0 + P.L);
+            if (j < msub - 1) e = ck(j == 0 ? t : P.n1 + j - 1, s0, false);
+            for (int n = s0; n < s1 && e == cudaSuccess; n++) e = rec(n, n - s0);
+            for (int k = s1; k >= s0 + 1 && e == cudaSuccess; k--) e = adj(k, k - 1 - s0);
+        }
+    }
+    return e;
 }
 
 // Injection groups of 3D points (adjoint path): every corner with a non-zero
@@ -1420,20 +1709,87 @@ void group3d(const std::vector<Pt3> &pts, bool per_shot, std::vector<Inj3> &grp,
     }
 }
 
-// The adjoint-state gradient on the 3D path: the 2D path's sweeps (forward
-// with checkpoints, residual, per segment a recompute recording Q' and the
-// adjoint sweep accumulating u^{n+1} Q'), with the z-march in its record /
-// adjoint modes and point injection grouped by cell. Q' slots are FP32
-// (checkpoints may be FP16); sponge or no absorption.
+// Options of one gradient call beyond sim_adjoint's arguments.
+struct AdjOpts {
+    bool vjp = false;          // d_obs holds the adjoint source itself (the residual): gradient = J^T r
+    double *grad_fp64 = nullptr;  // device FP64 accumulator to add the gradient to (instead of grad_v)
+};
+
+// After the graph: add the FP64 gradient to the caller's array, check the
+// final field, copy outputs and (when an output is host memory or the misfit
+// is asked for) wait and report.
+template <typename T>
+sim_status finish_gradient(sim_t s, const StepArgs<T> &a, int nshots, size_t nrows, void *grad_v, void *grdev,
+                           bool gr_host, void *gather_out, bool g_host, double *misfit_out, const AdjOpts &o) {
+    const Geom &g = s->g;
+    const long long nint = (long long)g.nz * g.ny * g.nx;
+    if (o.grad_fp64) {
+        if (sim_status r = s->cuda(launch_add_gradient<double>(s->acc, o.grad_fp64, nint, s->st), "gradient add"))
+            return r;
+    } else if (sim_status r = s->cuda(launch_add_gradient<T>(s->acc, static_cast<T *>(grdev), nint, s->st),
+                                      "gradient add"))
+        return r;
+    if (sim_status r = s->cuda(launch_check_finite<T>(g, a.pbuf[s->d.nt & 1], nshots, s->flags, s->st),
+                               "finite check"))
+        return r;
+    if (sim_status r = s->cuda(cudaMemcpyAsync(s->flags_host, s->flags, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                               s->st), "flag readback"))
+        return r;
+    if (gr_host)
+        if (sim_status r = s->cuda(cudaMemcpyAsync(grad_v, grdev, nint * sizeof(T), cudaMemcpyDeviceToHost, s->st),
+                                   "gradient download"))
+            return r;
+    if (gather_out)
+        if (sim_status r = s->cuda(cudaMemcpyAsync(gather_out, s->gath, nrows * sizeof(T), cudaMemcpyDefault, s->st),
+                                   "gather copy"))
+            return r;
+    std::vector<double> part(kResidBlocks);
+    const bool want_misfit = misfit_out && !o.vjp;
+    if (want_misfit)
+        if (sim_status r = s->cuda(cudaMemcpyAsync(part.data(), s->mpart, part.size() * sizeof(double),
+                                                   cudaMemcpyDeviceToHost, s->st), "misfit readback"))
+            return r;
+    if (misfit_out || gr_host || g_host) {
+        if (sim_status r = poll_flags(s, true)) return r;
+        if (misfit_out) {
+            double J = 0;
+            if (want_misfit)
+                for (double v : part) J += v;
+            *misfit_out = J;
+        }
+    }
+    return SIM_OK;
+}
+
+// Residual (g - d_obs, with the misfit) or the given adjoint source, then
+// zero the adjoint state: the step between the forward sweep and the reverse.
+template <typename T>
+cudaError_t gradient_mid(sim_t s, int nshots, size_t nrows, bool vjp, cudaStream_t st) {
+    cudaError_t e = vjp ? cudaMemcpyAsync(s->res, s->dobs, nrows * sizeof(T), cudaMemcpyDeviceToDevice, st)
+                        : launch_residual<T>(static_cast<const T *>(s->gath), static_cast<const T *>(s->dobs),
+                                             static_cast<T *>(s->res), (long long)nrows, s->mpart, kResidBlocks, st);
+    const size_t ub = (size_t)s->g.fstride * s->esz * nshots;
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->ubuf, 0, ub, st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(static_cast<char *>(s->ubuf) + (size_t)s->g.fstride * s->esz * s->d.max_shots, 0, ub, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->Gbuf, 0, ub, st);
+    if (e == cudaSuccess && s->d.bc == SIM_BC_CPML) e = reset_cpml_adjoint(s, nshots, st);
+    return e;
+}
+
+// The adjoint-state gradient on the 3D path: the z-march in its record /
+// adjoint modes, point injection grouped by cell, the CPML passes of each
+// absorbing axis around the update (in the recompute they also take the
+// addend off the imaging term) and the transposed CPML recursions after
+// each adjoint update. Imaging-term slots are FP32 (checkpoints may be FP16).
 sim_status adjoint3d(sim_t s, int nshots, const void *wavelet, const double *src_pos, int nrec,
                      const double *rec_pos, const void *d_obs, void *gather_out, double *misfit_out, int ckpt_fp16,
-                     void *grad_v) {
+                     void *grad_v, const AdjOpts &o) {
     const sim_desc &d = s->d;
     const Geom &g = s->g;
-    if (sim_status r = ensure_adjoint(s)) return r;
+    if (sim_status r = ensure_adjoint(s, ckpt_fp16)) return r;
     const size_t nt = d.nt;
     const int ms = d.max_shots;
-    const long long ncomp = (long long)g.NZ * g.NY * g.NX;
     const long long nint = (long long)g.nz * g.ny * g.nx;
     const size_t nrows = (size_t)nshots * nt * nrec;
     const void *wav = wavelet;
@@ -1447,7 +1803,7 @@ sim_status adjoint3d(sim_t s, int nshots, const void *wavelet, const double *src
                                "d_obs copy"))
         return r;
     const bool g_host = gather_out && !is_device_ptr(gather_out);
-    const bool gr_host = !is_device_ptr(grad_v);
+    const bool gr_host = !o.grad_fp64 && !is_device_ptr(grad_v);
     void *grdev = gr_host ? s->gradst : grad_v;
     if (gr_host)
         if (sim_status r = s->cuda(cudaMemcpyAsync(grdev, grad_v, nint * sizeof(float), cudaMemcpyHostToDevice, s->st),
@@ -1478,41 +1834,16 @@ sim_status adjoint3d(sim_t s, int nshots, const void *wavelet, const double *src
     if (sim_status r = s->cuda(cudaMemcpyAsync(s->io, &io, sizeof io, cudaMemcpyHostToDevice, s->st), "io upload"))
         return r;
 
-    const int L = s->seg, zc = zchunk_for(s, nshots);
-    const size_t ck_state = (size_t)ms * ncomp;
-    const int ckx = (g.NX + kTileX2 - 1) / kTileX2, ckz = (g.NZ * g.NY + kTileZ2 - 1) / kTileZ2;
-    const size_t ck_tiles = (size_t)ms * ckx * ckz;
-    auto ck_ptr = [&](int k, int which) {
-        return static_cast<char *>(s->ckpt) + ((size_t)k * 2 + which) * ck_state * (ckpt_fp16 ? 2 : sizeof(float));
-    };
-    auto ck_scale = [&](int k, int which) { return s->ckscale + ((size_t)k * 2 + which) * ck_tiles; };
+    const AdjPlan &P = s->plan;
+    const int zc = zchunk_for(s, nshots);
+    const CkLayout ckl = ck_layout(s, ckpt_fp16);
     StepArgs<float> a = step_args<float>(s);
     a.sample = 1;
     a.nsnap = 0;
-    // CPML: the passes of each absorbing axis run around the update as in a
-    // forward solve (in the recompute they also take the addend off the
-    // imaging term); psi (kept in place in psi[ax][0]) and zeta of every axis
-    // join each checkpoint; the sweep adds the transposed recursions'
-    // term to u^k after each update (cpml_adj.cu)
+    StepArgs<float> quiet = a;  // recompute: no sampling
+    quiet.sample = 0;
     const bool cpml = d.bc == SIM_BC_CPML;
     const int on[3] = {s->psi[0][0] != nullptr, s->psi[1][0] != nullptr, s->psi[2][0] != nullptr};
-    const int nfc = cpml_ckpt_fields(g);
-    auto ckc_ptr = [&](int k, int j) {
-        return static_cast<char *>(s->ckcpml) + ((size_t)k * nfc + j) * ck_state * (ckpt_fp16 ? 2 : sizeof(float));
-    };
-    auto ckc_scale = [&](int k, int j) { return s->ckcpml_scale + ((size_t)k * nfc + j) * ck_tiles; };
-    auto cpml_ckpt = [&](int k, bool store, cudaStream_t st) {  // fields j = 2 ax (psi), 2 ax + 1 (zeta)
-        cudaError_t e = cudaSuccess;
-        for (int j = 0; j < 6 && e == cudaSuccess; j++) {
-            if (!on[j / 2]) continue;
-            float *f = static_cast<float *>(j % 2 == 0 ? s->psi[j / 2][0] : s->zeta[j / 2]);
-            e = store ? launch_store_state<float>(g, f, ckc_ptr(k, j), ckc_scale(k, j), ckpt_fp16, nshots, ncomp, ckx,
-                                                  ckz, st)
-                      : launch_load_state<float>(g, f, ckc_ptr(k, j), ckc_scale(k, j), ckpt_fp16, nshots, ncomp, ckx,
-                                                 ckz, st);
-        }
-        return e;
-    };
     auto cpml_pass = [&](int n, int phase, float *qslot, cudaStream_t st) {
         cudaError_t e = cudaSuccess;
         for (int ax = 0; ax < 3 && e == cudaSuccess; ax++)
@@ -1524,64 +1855,37 @@ sim_status adjoint3d(sim_t s, int nshots, const void *wavelet, const double *src
     adj.pbuf[1] = static_cast<float *>(s->ubuf) + (long long)ms * g.fstride;
     adj.src_scale = (float)(d.h * d.h);
     float *Gs = static_cast<float *>(s->Gbuf);
-    const size_t qslot = (size_t)ms * g.fstride;  // floats per slot
-    const size_t ub = (size_t)g.fstride * sizeof(float) * nshots;
+    const size_t qstride = q_slot_bytes(s, ckpt_fp16);
     const int nsg = (int)sg.size(), nrg = (int)rg.size();
     const Pt3 *r3 = s->rec3;
-    const long long gkey = ((long long)nshots << 40) ^ ((long long)nrec << 16) ^ ((long long)ckpt_fp16 << 3) ^ 6;
+    const long long gkey = ((long long)nshots << 40) ^ ((long long)nrec << 16) ^ ((long long)ckpt_fp16 << 3) ^
+                           ((long long)o.vjp << 5) ^ 6;
     if (sim_status r = run_graph(s, gkey, [&](cudaStream_t st) {
             cudaError_t e = reset_state_on(s, nshots, st);
-            for (int n = 0; n < d.nt && e == cudaSuccess; n++) {
-                if (n % L == 0) {
-                    const int k = n / L;
-                    e = launch_store_state<float>(g, a.pbuf[n & 1], ck_ptr(k, 1), ck_scale(k, 1), ckpt_fp16,
-                                                  nshots, ncomp, ckx, ckz, st);
-                    if (e == cudaSuccess)
-                        e = launch_store_state<float>(g, a.pbuf[(n + 1) & 1], ck_ptr(k, 0), ck_scale(k, 0),
-                                                      ckpt_fp16, nshots, ncomp, ckx, ckz, st);
-                    if (e == cudaSuccess && cpml) e = cpml_ckpt(k, true, st);
-                }
-                if (e == cudaSuccess)
-                    e = launch_sample3d(a, step_time(s, a, n, kModeForward, nullptr, nullptr), r3, nrec, nshots, st);
-                if (e == cudaSuccess && cpml) e = cpml_pass(n, 0, nullptr, st);
-                if (e == cudaSuccess) e = launch_step3d(a, n, 1, zc, nshots, st, true, kModeForward);
-                if (e == cudaSuccess && cpml) e = cpml_pass(n, 1, nullptr, st);
-                if (e == cudaSuccess)
-                    e = launch_inj3d(a, n, n, s->src3g, nsg, s->src3e, 0, nshots, kModeForward, nullptr, nullptr, st);
-            }
-            if (e == cudaSuccess)
-                e = launch_residual<float>(static_cast<const float *>(s->gath), static_cast<const float *>(s->dobs),
-                                           static_cast<float *>(s->res), (long long)nrows, s->mpart, kResidBlocks,
-                                           st);
-            if (e == cudaSuccess) e = cudaMemsetAsync(s->ubuf, 0, ub, st);
-            if (e == cudaSuccess)
-                e = cudaMemsetAsync(static_cast<char *>(s->ubuf) + (size_t)g.fstride * sizeof(float) * ms, 0, ub,
-                                    st);
-            if (e == cudaSuccess) e = cudaMemsetAsync(s->Gbuf, 0, ub, st);
-            if (e == cudaSuccess && cpml) e = reset_cpml_adjoint(s, nshots, st);
-            for (int sgi = s->nseg - 1; sgi >= 0 && e == cudaSuccess; sgi--) {
-                const int n0 = sgi * L, n1 = std::min(n0 + L, d.nt);
-                e = launch_load_state<float>(g, a.pbuf[n0 & 1], ck_ptr(sgi, 1), ck_scale(sgi, 1), ckpt_fp16, nshots,
-                                             ncomp, ckx, ckz, st);
-                if (e == cudaSuccess)
-                    e = launch_load_state<float>(g, a.pbuf[(n0 + 1) & 1], ck_ptr(sgi, 0), ck_scale(sgi, 0),
-                                                 ckpt_fp16, nshots, ncomp, ckx, ckz, st);
-                if (e == cudaSuccess && cpml) e = cpml_ckpt(sgi, false, st);
-                for (int n = n0; n < n1 && e == cudaSuccess; n++) {
-                    float *slot = static_cast<float *>(s->qbuf) + (size_t)(n - n0) * qslot;
-                    if (cpml) e = cpml_pass(n, 0, nullptr, st);
-                    if (e == cudaSuccess) e = launch_step3d(a, n, 1, zc, nshots, st, true, kModeRecord, slot, nullptr);
-                    if (e == cudaSuccess && cpml) e = cpml_pass(n, 1, slot, st);
-                    if (e == cudaSuccess)
-                        e = launch_inj3d(a, n, n, s->src3g, nsg, s->src3e, 0, nshots, kModeRecord, slot, nullptr, st);
-                }
-                for (int k = n1; k >= n0 + 1 && e == cudaSuccess; k--) {
-                    float *slot = static_cast<float *>(s->qbuf) + (size_t)(k - 1 - n0) * qslot;
+            if (e != cudaSuccess) return e;
+            auto step = [&](const StepArgs<float> &A, int n, int mode, float *slot, bool sample) {
+                cudaError_t e2 = cudaSuccess;
+                if (sample) e2 = launch_sample3d(A, step_time(s, A, n, kModeForward, nullptr, nullptr), r3, nrec,
+                                                 nshots, st);
+                if (e2 == cudaSuccess && cpml) e2 = cpml_pass(n, 0, nullptr, st);
+                if (e2 == cudaSuccess) e2 = launch_step3d(A, n, 1, zc, nshots, st, true, mode, slot, nullptr);
+                if (e2 == cudaSuccess && cpml) e2 = cpml_pass(n, 1, slot, st);
+                if (e2 == cudaSuccess)
+                    e2 = launch_inj3d(A, n, n, s->src3g, nsg, s->src3e, 0, nshots, mode, slot, nullptr, st);
+                return e2;
+            };
+            auto slot_of = [&](int i) { return reinterpret_cast<float *>(static_cast<char *>(s->qbuf) + (size_t)i * qstride); };
+            e = emit_gradient(
+                P, d.nt, [&](int n) { return step(a, n, kModeForward, nullptr, true); },
+                [&](int n) { return step(quiet, n, kModeForward, nullptr, false); },
+                [&](int n, int i) { return step(quiet, n, kModeRecord, slot_of(i), false); },
+                [&](int k, int i) {
+                    float *slot = slot_of(i);
                     const int n = d.nt - k;
-                    e = launch_step3d(adj, n, 1, zc, nshots, st, true, kModeAdjoint, slot, Gs);
-                    if (e == cudaSuccess)
-                        e = launch_inj3d(adj, n, k, s->res3g, nrg, s->res3e, 1, nshots, kModeAdjoint, slot, Gs, st);
-                    if (e == cudaSuccess && cpml && k <= d.nt - 1) {  // nu^k, mu^k from u^{k+1}; c [.] into u^k
+                    cudaError_t e2 = launch_step3d(adj, n, 1, zc, nshots, st, true, kModeAdjoint, slot, Gs);
+                    if (e2 == cudaSuccess)
+                        e2 = launch_inj3d(adj, n, k, s->res3g, nrg, s->res3e, 1, nshots, kModeAdjoint, slot, Gs, st);
+                    if (e2 == cudaSuccess && cpml && k <= d.nt - 1) {  // nu^k, mu^k from u^{k+1}; c [.] into u^k
                         CpmlAdjArgs<float> ca{};
                         ca.u = adj.pbuf[(d.nt - k) & 1];
                         for (int ax = 0; ax < 3; ax++) {
@@ -1592,10 +1896,13 @@ sim_status adjoint3d(sim_t s, int nshots, const void *wavelet, const double *src
                         ca.uo = adj.pbuf[(n + 1) & 1];
                         ca.q = slot;
                         ca.G = Gs;
-                        e = launch_cpml_adjoint<float>(a, ca, k & 1, nshots, st);
+                        e2 = launch_cpml_adjoint<float>(a, ca, k & 1, nshots, st);
                     }
-                }
-            }
+                    return e2;
+                },
+                [&](int k, int n, bool store) { return checkpoint<float>(s, a, ckl, k, n, store, ckpt_fp16, nshots, st); },
+                [&]() { return gradient_mid<float>(s, nshots, nrows, o.vjp, st); });
+            // FP64 sum over shots and replicated cells
             if (e == cudaSuccess) e = cudaMemsetAsync(s->acc, 0, nint * sizeof(double), st);
             if (e == cudaSuccess)
                 e = launch_fold_gradient<float>(g, Gs, g.fstride, nshots, static_cast<const float *>(s->vpad),
@@ -1603,57 +1910,27 @@ sim_status adjoint3d(sim_t s, int nshots, const void *wavelet, const double *src
             return e;
         }))
         return r;
-    if (sim_status r = s->cuda(launch_add_gradient<float>(s->acc, static_cast<float *>(grdev), nint, s->st),
-                               "gradient add"))
-        return r;
-    if (sim_status r = s->cuda(launch_check_finite<float>(g, a.pbuf[d.nt & 1], nshots, s->flags, s->st),
-                               "finite check"))
-        return r;
-    if (sim_status r = s->cuda(cudaMemcpyAsync(s->flags_host, s->flags, sizeof(unsigned), cudaMemcpyDeviceToHost,
-                                               s->st), "flag readback"))
-        return r;
-    if (gr_host)
-        if (sim_status r = s->cuda(cudaMemcpyAsync(grad_v, grdev, nint * sizeof(float), cudaMemcpyDeviceToHost, s->st),
-                                   "gradient download"))
-            return r;
-    if (gather_out)
-        if (sim_status r = s->cuda(cudaMemcpyAsync(gather_out, s->gath, nrows * sizeof(float), cudaMemcpyDefault,
-                                                   s->st), "gather copy"))
-            return r;
-    std::vector<double> part(kResidBlocks);
-    if (misfit_out)
-        if (sim_status r = s->cuda(cudaMemcpyAsync(part.data(), s->mpart, part.size() * sizeof(double),
-                                                   cudaMemcpyDeviceToHost, s->st), "misfit readback"))
-            return r;
-    if (misfit_out || gr_host || g_host) {
-        if (sim_status r = poll_flags(s, true)) return r;
-        if (misfit_out) {
-            double J = 0;
-            for (double v : part) J += v;
-            *misfit_out = J;
-        }
-    }
-    return SIM_OK;
+    return finish_gradient<float>(s, a, nshots, nrows, grad_v, grdev, gr_host, gather_out, g_host, misfit_out, o);
 }
 
 template <typename T>
 sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src_pos, int nrec,
                      const double *rec_pos, const void *d_obs, void *gather_out, double *misfit_out, int ckpt_fp16,
-                     void *grad_v) {
+                     void *grad_v, const AdjOpts &o) {
     const sim_desc &d = s->d;
     const Geom &g = s->g;
     if (g.ndim == 3 && d.precision != SIM_FP32) return s->fail(SIM_ERR_UNSUPPORTED, "the 3D path runs in FP32");
     if (ckpt_fp16 && d.precision != SIM_FP32) return s->fail(SIM_ERR_ARG, "FP16 checkpoints need an FP32 handle");
     if (nrec < 1) return s->fail(SIM_ERR_ARG, "the misfit needs receivers");
-    if (!d_obs || !wavelet || !grad_v) return s->fail(SIM_ERR_ARG, "d_obs, wavelet and grad_v are required");
+    if (!d_obs || !wavelet || (!grad_v && !o.grad_fp64))
+        return s->fail(SIM_ERR_ARG, "d_obs, wavelet and grad_v are required");
     if (g.ndim == 3)
         return adjoint3d(s, nshots, wavelet, src_pos, nrec, rec_pos, d_obs, gather_out, misfit_out, ckpt_fp16,
-                         grad_v);
-    if (sim_status r = ensure_adjoint(s)) return r;
+                         grad_v, o);
+    if (sim_status r = ensure_adjoint(s, ckpt_fp16)) return r;
     if (sim_status r = autotune(s, nshots)) return r;
     const size_t nt = d.nt;
     const int ms = d.max_shots;
-    const long long ncomp = (long long)g.NZ * g.NY * g.NX;
     const int ntiles = s->ntx * s->nty * s->ntz;
     const long long nint = (long long)g.nz * g.ny * g.nx;
     const size_t nrows = (size_t)nshots * nt * nrec;
@@ -1672,10 +1949,8 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
     if (sim_status r = s->cuda(cudaMemcpyAsync(s->dobs, d_obs, nrows * sizeof(T), cudaMemcpyDefault, s->st),
                                "d_obs copy"))
         return r;
-    const void *dob = s->dobs;
     const bool g_host = gather_out && !is_device_ptr(gather_out);
-    void *gdev = s->gath;
-    const bool gr_host = !is_device_ptr(grad_v);
+    const bool gr_host = !o.grad_fp64 && !is_device_ptr(grad_v);
     void *grdev = gr_host ? s->gradst : grad_v;
     if (gr_host)
         if (sim_status r = s->cuda(cudaMemcpyAsync(grdev, grad_v, nint * sizeof(T), cudaMemcpyHostToDevice, s->st),
@@ -1707,30 +1982,23 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
 
     SimIO io{};
     io.wavelet = wav;
-    io.gather = gdev;
+    io.gather = s->gath;
     io.resid = s->res;
     io.nrec = nrec;
     io.nshots = nshots;
     if (sim_status r = s->cuda(cudaMemcpyAsync(s->io, &io, sizeof io, cudaMemcpyHostToDevice, s->st), "io upload"))
         return r;
 
-    const int L = s->seg;
-    const size_t ck_state = (size_t)ms * ncomp;  // elements of one checkpointed state (all shots)
-    const int ckx = (g.NX + kTileX2 - 1) / kTileX2, ckz = (g.NZ * g.NY + kTileZ2 - 1) / kTileZ2;  // store tiles
-    const size_t ck_tiles = (size_t)ms * ckx * ckz;
-    const size_t q_tiles = (size_t)ms * ntiles;
-    auto ck_ptr = [&](int k, int which) {
-        return static_cast<char *>(s->ckpt) + ((size_t)k * 2 + which) * ck_state * (ckpt_fp16 ? 2 : sizeof(T));
-    };
-    auto ck_scale = [&](int k, int which) { return s->ckscale + ((size_t)k * 2 + which) * ck_tiles; };
-
+    const AdjPlan &P = s->plan;
+    const CkLayout ckl = ck_layout(s, ckpt_fp16);
     // 1. forward pass, keeping (p^{n-1}, p^n) at every segment start
     StepArgs<T> a = step_args<T>(s);
     a.inj_per_shot = 1;
     a.inj_kind = 0;
     a.nsnap = 0;
-    StepArgs<T> rcp = a;
-    rcp.sample = 0;
+    StepArgs<T> quiet = a;  // recompute: no sampling
+    quiet.sample = 0;
+    StepArgs<T> rcp = quiet;
     rcp.q_fp16 = ckpt_fp16;
     StepArgs<T> adj = a;
     adj.pbuf[0] = static_cast<T *>(s->ubuf);
@@ -1746,80 +2014,28 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
     adj.q_fp16 = ckpt_fp16;
     adj.G = static_cast<T *>(s->Gbuf);
     // CPML: the sweep runs the plain update of u plus the transposed CPML
-    // terms (cpml_adj.cu) it receives through cext; the forward CPML state
-    // of every segment start joins the checkpoints
+    // terms (cpml_adj.cu) it receives through cext
     const bool cpml = d.bc == SIM_BC_CPML;
     if (cpml) {
         adj.bc = SIM_BC_NONE;
         adj.cext = static_cast<const T *>(s->cext);
     }
-    const int ckcx = ckx, ckcz = ckz;
-    auto ckc_ptr = [&](int k, int j) {
-        return static_cast<char *>(s->ckcpml) + ((size_t)k * 4 + j) * ck_state * (ckpt_fp16 ? 2 : sizeof(T));
-    };
-    auto ckc_scale = [&](int k, int j) { return s->ckcpml_scale + ((size_t)k * 4 + j) * ck_tiles; };
-    // the forward CPML state entering step n: psi^{n-1} in the buffer of parity
-    // (n + 1) & 1, zeta^{n-1}; j = 0..3: psi_z, zeta_z, psi_x, zeta_x
-    auto cpml_field = [&](int n, int j) -> T * {
-        const int ax = j < 2 ? 0 : 2;
-        return static_cast<T *>(j % 2 == 0 ? s->psi[ax][(n + 1) & 1] : s->zeta[ax]);
-    };
-    auto cpml_ckpt = [&](int n, int k, bool store, cudaStream_t st) {
-        cudaError_t e = cudaSuccess;
-        for (int j = 0; j < 4 && e == cudaSuccess; j++) {
-            if (!s->psi[j < 2 ? 0 : 2][0]) continue;
-            e = store ? launch_store_state<T>(g, cpml_field(n, j), ckc_ptr(k, j), ckc_scale(k, j), ckpt_fp16, nshots,
-                                              ncomp, ckcx, ckcz, st)
-                      : launch_load_state<T>(g, cpml_field(n, j), ckc_ptr(k, j), ckc_scale(k, j), ckpt_fp16, nshots,
-                                             ncomp, ckcx, ckcz, st);
-        }
-        return e;
-    };
-    const size_t qslot_bytes = (size_t)ms * g.fstride * (ckpt_fp16 ? 2 : sizeof(T));
-    const size_t ub = (size_t)g.fstride * s->esz * nshots;
+    const size_t qstride = q_slot_bytes(s, ckpt_fp16), q_tiles = (size_t)ms * ntiles;
     // graph key: everything the captured launches depend on beyond handle buffers
     const long long gkey = ((long long)nshots << 40) ^ ((long long)nrec << 12) ^ ((long long)s->tile_z << 4) ^
-                           ((long long)ckpt_fp16 << 3) ^ 5;
+                           ((long long)ckpt_fp16 << 3) ^ ((long long)o.vjp << 9) ^ 5;
     if (sim_status r = run_graph(s, gkey, [&](cudaStream_t st) {
             cudaError_t e = reset_state_on(s, nshots, st);
-            for (int n = 0; n < d.nt && e == cudaSuccess; n++) {
-                if (n % L == 0) {
-                    const int k = n / L;
-                    e = launch_store_state<T>(g, a.pbuf[n & 1], ck_ptr(k, 1), ck_scale(k, 1), ckpt_fp16, nshots,
-                                              ncomp, ckx, ckz, st);
-                    if (e == cudaSuccess)
-                        e = launch_store_state<T>(g, a.pbuf[(n + 1) & 1], ck_ptr(k, 0), ck_scale(k, 0), ckpt_fp16,
-                                                  nshots, ncomp, ckx, ckz, st);
-                    if (e == cudaSuccess && cpml) e = cpml_ckpt(n, k, true, st);
-                }
-                if (e == cudaSuccess) e = launch_step<T>(s, a, n, nshots, kModeForward, st);
-            }
-            // 2. residual and misfit
-            if (e == cudaSuccess)
-                e = launch_residual<T>(static_cast<const T *>(gdev), static_cast<const T *>(dob),
-                                       static_cast<T *>(s->res), (long long)nrows, s->mpart, kResidBlocks, st);
-            // 3. segments in reverse: restore, recompute while recording Q', sweep the adjoint back
-            if (e == cudaSuccess) e = cudaMemsetAsync(s->ubuf, 0, ub, st);
-            if (e == cudaSuccess)
-                e = cudaMemsetAsync(static_cast<char *>(s->ubuf) + (size_t)g.fstride * s->esz * ms, 0, ub, st);
-            if (e == cudaSuccess) e = cudaMemsetAsync(s->Gbuf, 0, (size_t)nshots * g.fstride * s->esz, st);
-            if (cpml) e = reset_cpml_adjoint(s, nshots, st);
-            for (int sgi = s->nseg - 1; sgi >= 0 && e == cudaSuccess; sgi--) {
-                const int n0 = sgi * L, n1 = std::min(n0 + L, d.nt);
-                e = launch_load_state<T>(g, a.pbuf[n0 & 1], ck_ptr(sgi, 1), ck_scale(sgi, 1), ckpt_fp16, nshots,
-                                         ncomp, ckx, ckz, st);
-                if (e == cudaSuccess)
-                    e = launch_load_state<T>(g, a.pbuf[(n0 + 1) & 1], ck_ptr(sgi, 0), ck_scale(sgi, 0), ckpt_fp16,
-                                             nshots, ncomp, ckx, ckz, st);
-                if (e == cudaSuccess && cpml) e = cpml_ckpt(n0, sgi, false, st);
-                for (int n = n0; n < n1 && e == cudaSuccess; n++) {
-                    void *slot = static_cast<char *>(s->qbuf) + (size_t)(n - n0) * qslot_bytes;
-                    float *scl = s->qscale + (size_t)(n - n0) * q_tiles;
-                    e = launch_step<T>(s, rcp, n, nshots, kModeRecord, st, slot, scl);
-                }
-                for (int k = n1; k >= n0 + 1 && e == cudaSuccess; k--) {
-                    void *slot = static_cast<char *>(s->qbuf) + (size_t)(k - 1 - n0) * qslot_bytes;
-                    float *scl = s->qscale + (size_t)(k - 1 - n0) * q_tiles;
+            if (e != cudaSuccess) return e;
+            auto slot_of = [&](int i) { return static_cast<void *>(static_cast<char *>(s->qbuf) + (size_t)i * qstride); };
+            auto scale_of = [&](int i) { return s->qscale + (size_t)i * (q_scale_bytes(s) / sizeof(float)); };
+            (void)q_tiles;
+            e = emit_gradient(
+                P, d.nt, [&](int n) { return launch_step<T>(s, a, n, nshots, kModeForward, st); },
+                [&](int n) { return launch_step<T>(s, quiet, n, nshots, kModeForward, st); },
+                [&](int n, int i) { return launch_step<T>(s, rcp, n, nshots, kModeRecord, st, slot_of(i), scale_of(i)); },
+                [&](int k, int i) {
+                    cudaError_t e2 = cudaSuccess;
                     if (cpml && k <= d.nt - 1) {  // nu^k, mu^k from u^{k+1}, then their term in u^k
                         CpmlAdjArgs<T> ca{};
                         ca.u = adj.pbuf[(d.nt - k) & 1];
@@ -1829,12 +2045,15 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
                             ca.mu[ax] = static_cast<T *>(s->cmu[ax]);
                         }
                         ca.ext = static_cast<T *>(s->cext);
-                        e = launch_cpml_adjoint<T>(a, ca, k & 1, nshots, st);
+                        e2 = launch_cpml_adjoint<T>(a, ca, k & 1, nshots, st);
                     }
-                    if (e == cudaSuccess) e = launch_step<T>(s, adj, d.nt - k, nshots, kModeAdjoint, st, slot, scl);
-                }
-            }
-            // 4. gradient: FP64 sum over shots and replicated cells
+                    if (e2 == cudaSuccess)
+                        e2 = launch_step<T>(s, adj, d.nt - k, nshots, kModeAdjoint, st, slot_of(i), scale_of(i));
+                    return e2;
+                },
+                [&](int k, int n, bool store) { return checkpoint<T>(s, a, ckl, k, n, store, ckpt_fp16, nshots, st); },
+                [&]() { return gradient_mid<T>(s, nshots, nrows, o.vjp, st); });
+            // FP64 sum over shots and replicated cells
             if (e == cudaSuccess) e = cudaMemsetAsync(s->acc, 0, nint * sizeof(double), st);
             if (e == cudaSuccess)
                 e = launch_fold_gradient<T>(g, static_cast<const T *>(s->Gbuf), g.fstride, nshots,
@@ -1842,36 +2061,7 @@ sim_status adjoint_t(sim_t s, int nshots, const void *wavelet, const double *src
             return e;
         }))
         return r;
-    if (sim_status r = s->cuda(launch_add_gradient<T>(s->acc, static_cast<T *>(grdev), nint, s->st), "gradient add"))
-        return r;
-    if (sim_status r = s->cuda(launch_check_finite<T>(g, a.pbuf[d.nt & 1], nshots, s->flags, s->st), "finite check"))
-        return r;
-    if (sim_status r = s->cuda(cudaMemcpyAsync(s->flags_host, s->flags, sizeof(unsigned), cudaMemcpyDeviceToHost,
-                                               s->st), "flag readback"))
-        return r;
-    if (gr_host)
-        if (sim_status r = s->cuda(cudaMemcpyAsync(grad_v, grdev, nint * sizeof(T), cudaMemcpyDeviceToHost, s->st),
-                                   "gradient download"))
-            return r;
-    if (gather_out)
-        if (sim_status r = s->cuda(cudaMemcpyAsync(gather_out, gdev, nrows * sizeof(T), cudaMemcpyDefault, s->st),
-                                   "gather copy"))
-            return r;
-    std::vector<double> part(kResidBlocks);
-    if (misfit_out) {
-        if (sim_status r = s->cuda(cudaMemcpyAsync(part.data(), s->mpart, part.size() * sizeof(double),
-                                                   cudaMemcpyDeviceToHost, s->st), "misfit readback"))
-            return r;
-    }
-    if (misfit_out || gr_host || g_host) {
-        if (sim_status r = poll_flags(s, true)) return r;
-        if (misfit_out) {
-            double J = 0;
-            for (double v : part) J += v;
-            *misfit_out = J;
-        }
-    }
-    return SIM_OK;
+    return finish_gradient<T>(s, a, nshots, nrows, grad_v, grdev, gr_host, gather_out, g_host, misfit_out, o);
 }
 
 
@@ -2200,6 +2390,67 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
 
 }  // namespace
 
+// Gradient mode of the batch: for every item, the adjoint-state gradient of
+// its shots on its handle (all shots of an item in one call, FP64 fold over
+// its shots) added to the item's FP64 accumulator, and its misfit. Items run
+// one after another on their handles' streams, ordered after the batch
+// stream's earlier work and before its later work.
+sim_status batch_gradient(int nitems, const sim_batch_item *items, int ckpt_fp16, cudaStream_t bst) {
+    if (nitems < 1 || !items) return thread_fail(SIM_ERR_ARG, "empty batch");
+    for (int i = 0; i < nitems; i++) {
+        const sim_batch_item &it = items[i];
+        sim_t s = it.sim;
+        if (!s || !s->model_set) return thread_fail(SIM_ERR_STATE, "batch item %d: no handle or no model", i);
+        if (s->sticky) return s->sticky;
+        if (s->dev != items[0].sim->dev) return thread_fail(SIM_ERR_ARG, "batch item %d: another device", i);
+        if (it.nshots < 1 || it.nshots > s->d.max_shots)
+            return thread_fail(SIM_ERR_ARG, "batch item %d: nshots outside [1, max_shots]", i);
+        if (it.nrec < 1 || it.nrec > s->d.max_rec || !it.rec_pos)
+            return thread_fail(SIM_ERR_ARG, "batch item %d: the gradient needs receivers", i);
+        if (!it.wavelet || !it.src_pos || !it.d_obs)
+            return thread_fail(SIM_ERR_ARG, "batch item %d: wavelet, sources and d_obs are required", i);
+        if (!it.grad_sum_fp64 || !is_device_ptr(it.grad_sum_fp64))
+            return thread_fail(SIM_ERR_ARG, "batch item %d: grad_sum_fp64 must be device memory", i);
+        for (int j = 0; j < i; j++)
+            if (items[j].sim == s) return thread_fail(SIM_ERR_ARG, "batch items %d and %d share a handle", j, i);
+    }
+    cudaSetDevice(items[0].sim->dev);
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return thread_fail(SIM_ERR_CUDA, "event creation failed");
+    }
+    sim_status rc = SIM_OK;
+    for (int i = 0; i < nitems && rc == SIM_OK; i++) {
+        const sim_batch_item &it = items[i];
+        sim_t s = it.sim;
+        if (cudaEventRecord(ev, bst) != cudaSuccess || cudaStreamWaitEvent(s->st, ev, 0) != cudaSuccess) {
+            cudaGetLastError();
+            rc = thread_fail(SIM_ERR_CUDA, "batch ordering failed");
+            break;
+        }
+        AdjOpts o;
+        o.grad_fp64 = it.grad_sum_fp64;
+        double J = 0;
+        rc = s->d.precision == SIM_FP64
+                 ? adjoint_t<double>(s, it.nshots, it.wavelet, it.src_pos, it.nrec, it.rec_pos, it.d_obs, it.gather,
+                                     it.misfit ? &J : nullptr, ckpt_fp16, nullptr, o)
+                 : adjoint_t<float>(s, it.nshots, it.wavelet, it.src_pos, it.nrec, it.rec_pos, it.d_obs, it.gather,
+                                    it.misfit ? &J : nullptr, ckpt_fp16, nullptr, o);
+        if (rc != SIM_OK) {
+            t_err = s->err;
+            break;
+        }
+        if (it.misfit) *it.misfit = J;
+        if (cudaEventRecord(ev, s->st) != cudaSuccess || cudaStreamWaitEvent(bst, ev, 0) != cudaSuccess) {
+            cudaGetLastError();
+            rc = thread_fail(SIM_ERR_CUDA, "batch ordering failed");
+        }
+    }
+    cudaEventDestroy(ev);
+    return rc;
+}
+
 // ============================================================== C ABI
 
 extern "C" {
@@ -2374,15 +2625,41 @@ sim_status sim_adjoint(sim_t s, int nshots, const void *wavelet, const double *s
     if (nrec < 0 || nrec > s->d.max_rec) return s->fail(SIM_ERR_ARG, "nrec = %d outside [0, %d]", nrec, s->d.max_rec);
     if (!src_pos || !rec_pos) return s->fail(SIM_ERR_ARG, "positions are required");
     cudaSetDevice(s->dev);
+    const AdjOpts o;
     return s->d.precision == SIM_FP64
                ? adjoint_t<double>(s, nshots, wavelet, src_pos, nrec, rec_pos, d_obs, gather_out, misfit_out,
-                                   ckpt_fp16, grad_v)
+                                   ckpt_fp16, grad_v, o)
                : adjoint_t<float>(s, nshots, wavelet, src_pos, nrec, rec_pos, d_obs, gather_out, misfit_out,
-                                  ckpt_fp16, grad_v);
+                                  ckpt_fp16, grad_v, o);
+}
+
+sim_status sim_adjoint_vjp(sim_t s, int nshots, const void *wavelet, const double *src_pos, int nrec,
+                           const double *rec_pos, const void *cot, void *gather_out, int ckpt_fp16, void *grad_v) {
+    if (!s) return thread_fail(SIM_ERR_ARG, "NULL handle");
+    if (sim_status r = poll_flags(s, false)) return r;
+    if (!s->model_set) return s->fail(SIM_ERR_STATE, "no velocity model set");
+    if (nshots < 1 || nshots > s->d.max_shots)
+        return s->fail(SIM_ERR_ARG, "nshots = %d outside [1, %d]", nshots, s->d.max_shots);
+    if (nrec < 0 || nrec > s->d.max_rec) return s->fail(SIM_ERR_ARG, "nrec = %d outside [0, %d]", nrec, s->d.max_rec);
+    if (!src_pos || !rec_pos) return s->fail(SIM_ERR_ARG, "positions are required");
+    cudaSetDevice(s->dev);
+    AdjOpts o;
+    o.vjp = true;
+    return s->d.precision == SIM_FP64
+               ? adjoint_t<double>(s, nshots, wavelet, src_pos, nrec, rec_pos, cot, gather_out, nullptr, ckpt_fp16,
+                                   grad_v, o)
+               : adjoint_t<float>(s, nshots, wavelet, src_pos, nrec, rec_pos, cot, gather_out, nullptr, ckpt_fp16,
+                                  grad_v, o);
 }
 
 sim_status sim_batch(int nitems, const sim_batch_item *items, void *cuda_stream) {
     return batch_impl(nitems, items, static_cast<cudaStream_t>(cuda_stream));
+}
+
+sim_status sim_batch_ex(int nitems, const sim_batch_item *items, int mode, int ckpt_fp16, void *cuda_stream) {
+    if (mode == 0) return batch_impl(nitems, items, static_cast<cudaStream_t>(cuda_stream));
+    if (mode == 1) return batch_gradient(nitems, items, ckpt_fp16, static_cast<cudaStream_t>(cuda_stream));
+    return thread_fail(SIM_ERR_ARG, "batch mode %d is neither 0 (forward) nor 1 (gradient)", mode);
 }
 
 sim_status sim_sync(sim_t s) {
@@ -2402,6 +2679,14 @@ sim_status sim_get_info(sim_t s, sim_info *out) {
     out->vmax = s->vmax;
     out->courant = s->vmax * s->d.dt / s->d.h;
     out->device_bytes = s->bytes;
+    if (s->adj_ready) {
+        out->adj_levels = s->plan.levels;
+        out->adj_slots = s->plan.L;
+        out->adj_top = s->plan.n1;
+        out->adj_sub = s->plan.n2;
+        out->adj_inner = s->plan.m;
+        out->adj_bytes = s->adj_bytes;
+    }
     return SIM_OK;
 }
 
@@ -2420,6 +2705,7 @@ void sim_destroy(sim_t s) {
     if (s->ev_in) cudaEventDestroy(s->ev_in);
     if (s->ev_out) cudaEventDestroy(s->ev_out);
     for (void *p : s->allocs) cudaFree(p);
+    for (void *p : s->adj_allocs) cudaFree(p);
     if (s->flags_host) cudaFreeHost(s->flags_host);
     cudaGetLastError();
     delete s;

@@ -295,6 +295,26 @@ cudaError_t launch_store_state(const Geom &g, const T *field, void *dst, float *
 template <typename T>
 cudaError_t launch_load_state(const Geom &g, T *field, const void *src, const float *scale, int fp16, int nshots,
                               long long shot_stride, int ntx, int ntz, cudaStream_t st);
+// Checkpoint of the CPML memory of one axis: only the boxes of its strips
+// (the memory is zero elsewhere), compact [shot][rows][x] with, in FP16, a
+// power-of-two scale per (shot, box row). row0 / elem0 are prefix sums over
+// the boxes (row0[n] rows and elem0[n] elements per shot).
+struct CkBox {
+    int z0, z1, y0, y1, x0, x1;
+};
+constexpr int kMaxCkBoxes = 2;
+struct CkBoxes {
+    int n;
+    CkBox b[kMaxCkBoxes];
+    long long row0[kMaxCkBoxes + 1];
+    long long elem0[kMaxCkBoxes + 1];
+};
+template <typename T>
+cudaError_t launch_store_boxes(const Geom &g, const CkBoxes &b, const T *field, void *dst, float *scale, int fp16,
+                               int nshots, cudaStream_t st);
+template <typename T>
+cudaError_t launch_load_boxes(const Geom &g, const CkBoxes &b, T *field, const void *src, const float *scale,
+                              int fp16, int nshots, cudaStream_t st);
 // res = g - d (all shots), per-block partial sums of res^2 / 2 into part.
 template <typename T>
 cudaError_t launch_residual(const T *g, const T *d, T *res, long long n, double *part, int nblocks, cudaStream_t st);

@@ -57,10 +57,16 @@ def test_c2_full_length_gathers_and_snapshots(pkg):
     assert sn.shape == (500, 619, 1000)
     ref = oracle.forward(c, c["vel"].astype(np.float64), c["wavelet"].astype(np.float64), src=c["src"][0],
                          rec=c["rec"], snaps=True)
+    # snapshots whose reference is all zero (before the wave leaves the
+    # source cell's neighbourhood: p^0 = 0) must be exactly zero
+    zero = [j for j in range(500) if not np.any(ref["snaps"][j])]
+    for j in zero:
+        assert not np.any(sn[j]), j
     curve = []
     for n in range(1000, 8001, 1000):
         k = min(500, n // 10)
-        es = max(rel(sn[j], ref["snaps"][j]) for j in range(max(0, k - 100), k)) if n <= 5000 else None
+        js = [j for j in range(max(0, k - 100), k) if j not in zero]
+        es = max(rel(sn[j], ref["snaps"][j]) for j in js) if n <= 5000 else None
         curve.append((n, rel(g[:n], ref["gather"][:n]), es))
     print("C2 relative L2 vs steps (gather rows < n, worst snapshot of the last 100 before n):", curve)
     for n, eg, es in curve:
