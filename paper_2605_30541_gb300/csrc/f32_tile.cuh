@@ -26,8 +26,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 // second difference of the 12-float window v[0..11] at v[4 + k]
 __device__ __forceinline__ float d2w(const float *v, int k) {
-    return float(kC0) * v[4 + k] + float(kC1) * (v[5 + k] + v[3 + k]) + float(kC2) * (v[6 + k] + v[2 + k]) +
-           float(kC3) * (v[7 + k] + v[1 + k]) + float(kC4) * (v[8 + k] + v[k]);
+    return d2c<float>(v[4 + k], v[3 + k], v[5 + k], v[2 + k], v[6 + k], v[1 + k], v[7 + k], v[k], v[8 + k]);
 }
 // first difference of the 12-float window at v[4 + k]
 __device__ __forceinline__ float d1w(const float *v, int k) {

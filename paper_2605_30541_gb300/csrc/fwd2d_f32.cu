@@ -56,8 +56,7 @@ __device__ __forceinline__ float bmax(float v, float *red) {
 
 // second difference of the 12-float window v[0..11] at v[4 + k]
 __device__ __forceinline__ float d2w(const float *v, int k) {
-    return float(kC0) * v[4 + k] + float(kC1) * (v[5 + k] + v[3 + k]) + float(kC2) * (v[6 + k] + v[2 + k]) +
-           float(kC3) * (v[7 + k] + v[1 + k]) + float(kC4) * (v[8 + k] + v[k]);
+    return d2c<float>(v[4 + k], v[3 + k], v[5 + k], v[2 + k], v[6 + k], v[1 + k], v[7 + k], v[k], v[8 + k]);
 }
 // first difference of the 12-float window at v[4 + k]
 __device__ __forceinline__ float d1w(const float *v, int k) {
@@ -290,8 +289,7 @@ __device__ __forceinline__ void tile_step(const StepArgs<float> &A, const StepTi
                         cz[m] = col[(m - 4) * SW + k];
                         pz[m] = pzc[(m - 4) * TX + k];
                     }
-                    const float d2 = float(kC0) * cz[4] + float(kC1) * (cz[5] + cz[3]) + float(kC2) * (cz[6] + cz[2]) +
-                                     float(kC3) * (cz[7] + cz[1]) + float(kC4) * (cz[8] + cz[0]);
+                    const float d2 = d2c<float>(cz[4], cz[3], cz[5], cz[2], cz[6], cz[1], cz[7], cz[0], cz[8]);
                     const float dps = float(kD1) * (pz[5] - pz[3]) + float(kD2) * (pz[6] - pz[2]) +
                                       float(kD3) * (pz[7] - pz[1]) + float(kD4) * (pz[8] - pz[0]);
                     zo[k] = bz * lane_of(z4, k) + az * (d2 + dps);
@@ -364,10 +362,8 @@ __device__ __forceinline__ void tile_step(const StepArgs<float> &A, const StepTi
         for (int k = 0; k < 4; k++) {
             const float p = v[4 + k];
             const float d2x = d2w(v, k);
-            const float d2z = float(kC0) * p + float(kC1) * (lane_of(zw[j + 5], k) + lane_of(zw[j + 3], k)) +
-                              float(kC2) * (lane_of(zw[j + 6], k) + lane_of(zw[j + 2], k)) +
-                              float(kC3) * (lane_of(zw[j + 7], k) + lane_of(zw[j + 1], k)) +
-                              float(kC4) * (lane_of(zw[j + 8], k) + lane_of(zw[j], k));
+            const float d2z = d2c<float>(p, lane_of(zw[j + 3], k), lane_of(zw[j + 5], k), lane_of(zw[j + 2], k), lane_of(zw[j + 6], k),
+                                         lane_of(zw[j + 1], k), lane_of(zw[j + 7], k), lane_of(zw[j], k), lane_of(zw[j + 8], k));
             float rhs = d2z + d2x;
             if (cpx || cpz) rhs += lane_of(cadd[j], k);
             if (MODE == kModeAdjoint && A.cext) rhs += lane_of(ext4, k);

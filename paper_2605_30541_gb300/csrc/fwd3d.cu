@@ -16,6 +16,8 @@
 // and snapshot output.
 #include <cfloat>
 
+#include <cudaTypedefs.h>
+
 #include "sim_internal.h"
 #include "stencil.cuh"
 
@@ -158,17 +160,12 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d(const StepArgs<float> A, cons
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const float p = v[4 + k];
-                const float d2x = float(kC0) * p + float(kC1) * (v[5 + k] + v[3 + k]) +
-                                  float(kC2) * (v[6 + k] + v[2 + k]) + float(kC3) * (v[7 + k] + v[1 + k]) +
-                                  float(kC4) * (v[8 + k] + v[k]);
-                const float d2y = float(kC0) * p + float(kC1) * (lane4(yv[5], k) + lane4(yv[3], k)) +
-                                  float(kC2) * (lane4(yv[6], k) + lane4(yv[2], k)) +
-                                  float(kC3) * (lane4(yv[7], k) + lane4(yv[1], k)) +
-                                  float(kC4) * (lane4(yv[8], k) + lane4(yv[0], k));
-                const float d2z = float(kC0) * p + float(kC1) * (lane4(q[5][r], k) + lane4(q[3][r], k)) +
-                                  float(kC2) * (lane4(q[6][r], k) + lane4(q[2][r], k)) +
-                                  float(kC3) * (lane4(q[7][r], k) + lane4(q[1][r], k)) +
-                                  float(kC4) * (lane4(q[8][r], k) + lane4(q[0][r], k));
+                const float d2x = d2c<float>(p, v[3 + k], v[5 + k], v[2 + k], v[6 + k], v[1 + k], v[7 + k], v[k], v[8 + k]);
+                const float d2y = d2c<float>(p, lane4(yv[3], k), lane4(yv[5], k), lane4(yv[2], k), lane4(yv[6], k),
+                                                lane4(yv[1], k), lane4(yv[7], k), lane4(yv[0], k), lane4(yv[8], k));
+                const float d2z = d2c<float>(p, lane4(q[3][r], k), lane4(q[5][r], k), lane4(q[2][r], k),
+                                                lane4(q[6][r], k), lane4(q[1][r], k), lane4(q[7][r], k),
+                                                lane4(q[0][r], k), lane4(q[8][r], k));
                 const float rhs = d2x + d2y + d2z;
                 const float chv = lane4(ch4, k), pp = lane4(pp4, k);
                 float out, es = 0.f;
@@ -207,6 +204,228 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d(const StepArgs<float> A, cons
         __syncthreads();  // this slot is restaged at the next plane
     }
     cp_wait<0>();  // no copy into shared memory outlives the block
+}
+
+// ---------------------------------------------------------------- z-march with TMA
+//
+// The same update as k_step3d, with the planes staged by the tensor memory
+// accelerator: one thread issues, per plane, three bulk tensor copies (p^n
+// with its radius-4 x/y halo, 136 x 16 cells; p^{n-1} and c of the tile's own
+// 128 x 8 cells) into a ring slot and arms the slot's mbarrier with their
+// byte count; every thread waits on the barrier (bounded) instead of issuing
+// its own 16-byte copies. The z loop is unrolled by the 9 planes of the
+// register queue, so the queue rotates by renaming registers, not by moving
+// them. A wait that gives up sets kFlagTimeout; all threads then leave
+// together after the copies already issued have landed (also bounded).
+constexpr int NST = 6;                                  // ring slots
+constexpr int SLOT_T = 16 * SW3 * 4 + 2 * 8 * TX * 4;   // bytes per slot: 8704 + 8192
+constexpr int HALO_T = 16 * SW3 * 4, OWN_T = 8 * TX * 4;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned cnt) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(cnt) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned long long *b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned long long *b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity, long long limit) {
+    for (long long i = 0; i < limit; i++)
+        if (mbar_try(b, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load4(void *dst, const CUtensorMap *m, int x, int y, int z, int w,
+                                          unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(m)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load3(void *dst, const CUtensorMap *m, int x, int y, int z,
+                                          unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(m)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, const __grid_constant__ Tma3 M,
+                                                       const int n, const int zchunk, const int ms, float *qs,
+                                                       float *Gs, const long long spin) {
+    constexpr int TY = NW, NR = TY + 8;
+    extern __shared__ __align__(128) unsigned char sm_t[];
+    unsigned char *const ring = sm_t;
+    unsigned long long *const full = reinterpret_cast<unsigned long long *>(sm_t + NST * SLOT_T);
+
+    const Geom &g = A.g;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int nchunk = (g.NZ + zchunk - 1) / zchunk;
+    const int shot = blockIdx.z / nchunk, zb = (blockIdx.z % nchunk) * zchunk;
+    const int ze = min(zb + zchunk, g.NZ);
+    const long long PP = (long long)g.PY * g.P;
+    const long long sh = (long long)shot * g.fstride;
+    const float *pc = A.pbuf[n & 1] + sh;
+    float *pn = A.pbuf[(n + 1) & 1] + sh;
+    const int gx0 = x0 + 4 * lane;
+    const bool xedge = x0 + TX > g.NX;
+    const bool spg = A.bc == SIM_BC_SPONGE &&
+                     ((g.nbx0 > 0 && x0 < g.nbx0) || (g.nbx1 > 0 && x0 + TX > g.NX - g.nbx1) ||
+                      (g.nby0 > 0 && y0 < g.nby0) || (g.nby1 > 0 && y0 + TY > g.NY - g.nby1) || g.nbz0 > 0 ||
+                      g.nbz1 > 0);
+    float4 Ex4 = make_float4(0, 0, 0, 0);
+    float Ey = 0.f;
+    if (spg) {
+        Ex4 = __ldg(reinterpret_cast<const float4 *>(A.E[2] + gx0));
+        Ey = __ldg(A.E[1] + y0 + w);
+    }
+    const long long own0 = cell_off(g, 0, y0 + w, gx0);
+    // tensor coordinates of the padded layout: (x, y, z) + kGhost; w = buffer parity * ms + shot
+    const int tx = x0 + kGhost, ty = y0 + kGhost;
+    const int wcur = (n & 1) * ms + shot, wprev = ((n + 1) & 1) * ms + shot;
+    if (tid == 0) {
+        for (int k = 0; k < NST; k++) mbar_init(full + k, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+
+    cudaGridDependencySynchronize();
+
+    int zlast = zb - 1;        // last plane staged (thread 0)
+    auto stage = [&](int z) {  // thread 0 only
+        zlast = z;
+        const int k = (z - zb) % NST;
+        unsigned char *dst = ring + k * SLOT_T;
+        const bool own = z < ze;
+        mbar_expect(full + k, HALO_T + (own ? 2 * OWN_T : 0));
+        tma_load4(dst, &M.ph, tx - 4, ty - 4, z + kGhost, wcur, full + k);
+        if (own) {
+            tma_load4(dst + HALO_T, &M.po, tx, ty, z + kGhost, wprev, full + k);
+            tma_load3(dst + HALO_T + OWN_T, &M.c, tx, ty, z + kGhost, full + k);
+        }
+    };
+    if (tid == 0)
+        for (int k = 0; k < NST - 1; k++) stage(zb + k);
+
+    // register queue of this thread's cells: plane z + m lives in q[(j + m + 4) % 9]
+    // at unrolled step j of a block of 9 planes
+    float4 q[9];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const int z = zb - 4 + k;
+        float4 v;
+        if (z < 0) {
+            if (!g.fs) {
+                v = make_float4(0, 0, 0, 0);
+            } else {
+                const float4 u = *reinterpret_cast<const float4 *>(pc + own0 + (long long)(-z) * PP);
+                v = make_float4(-u.x, -u.y, -u.z, -u.w);
+            }
+        } else {
+            v = *reinterpret_cast<const float4 *>(pc + own0 + (long long)z * PP);
+        }
+        q[k] = v;
+    }
+
+    bool bad = false;
+    for (int zz = zb; zz < ze && !bad; zz += 9) {
+#pragma unroll
+        for (int j = 0; j < 9; j++) {
+            const int z = zz + j;
+            if (z >= ze || bad) break;
+            if (tid == 0) stage(z + NST - 1);
+            const int kz = (z - zb) % NST, k4 = (z + 4 - zb) % NST;
+            bool ok = mbar_wait(full + kz, ((z - zb) / NST) & 1, spin);
+            ok = ok && mbar_wait(full + k4, ((z + 4 - zb) / NST) & 1, spin);
+            if (ok) {
+                const float *cur = reinterpret_cast<const float *>(ring + kz * SLOT_T);
+                const float *ahead = reinterpret_cast<const float *>(ring + k4 * SLOT_T);
+                q[(j + 8) % 9] = *reinterpret_cast<const float4 *>(ahead + (w + 4) * SW3 + 4 + 4 * lane);
+                const float ez = spg ? __ldg(A.E[0] + z) : 0.f;
+                const int gy = y0 + w;
+                const float *row = cur + (w + 4) * SW3 + 4 + 4 * lane;
+                const float4 L = *reinterpret_cast<const float4 *>(row - 4), C = *reinterpret_cast<const float4 *>(row),
+                             R = *reinterpret_cast<const float4 *>(row + 4);
+                const float v[12] = {L.x, L.y, L.z, L.w, C.x, C.y, C.z, C.w, R.x, R.y, R.z, R.w};
+                float4 yv[9];
+#pragma unroll
+                for (int m = 0; m < 9; m++) yv[m] = *reinterpret_cast<const float4 *>(row + (m - 4) * SW3);
+                const float4 pp4 = *reinterpret_cast<const float4 *>(cur + NR * SW3 + w * TX + 4 * lane);
+                const float4 ch4 = *reinterpret_cast<const float4 *>(cur + NR * SW3 + TY * TX + w * TX + 4 * lane);
+                float res[4], qk[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float p = v[4 + k];
+                    const float d2x = d2c<float>(p, v[3 + k], v[5 + k], v[2 + k], v[6 + k], v[1 + k], v[7 + k], v[k], v[8 + k]);
+                    const float d2y = d2c<float>(p, lane4(yv[3], k), lane4(yv[5], k), lane4(yv[2], k), lane4(yv[6], k),
+                                                lane4(yv[1], k), lane4(yv[7], k), lane4(yv[0], k), lane4(yv[8], k));
+                    const float d2z = d2c<float>(p, lane4(q[(j + 3) % 9], k), lane4(q[(j + 5) % 9], k),
+                                                    lane4(q[(j + 2) % 9], k), lane4(q[(j + 6) % 9], k),
+                                                    lane4(q[(j + 1) % 9], k), lane4(q[(j + 7) % 9], k),
+                                                    lane4(q[j % 9], k), lane4(q[(j + 8) % 9], k));
+                    const float rhs = d2x + d2y + d2z;
+                    const float chv = lane4(ch4, k), pp = lane4(pp4, k);
+                    float out, es = 0.f;
+                    if (spg) {
+                        es = ez + Ey + lane4(Ex4, k);
+                        const float a = chv * es;
+                        out = (2.f * p - (1.f - a) * pp + chv * rhs) / (1.f + a);
+                    } else {
+                        out = 2.f * p - pp + chv * rhs;
+                    }
+                    res[k] = out;
+                    qk[k] = es * (out - pp) - rhs;
+                }
+                if (xedge) {
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        if (gx0 + k >= g.NX) res[k] = 0.f;
+                }
+                if (g.fs && z == 0) res[0] = res[1] = res[2] = res[3] = 0.f;
+                if (gy < g.NY) {
+                    const long long o = own0 + (long long)z * PP;
+                    *reinterpret_cast<float4 *>(pn + o) = make_float4(res[0], res[1], res[2], res[3]);
+                    if (MODE == kModeRecord)
+                        *reinterpret_cast<float4 *>(qs + sh + o) = make_float4(qk[0], qk[1], qk[2], qk[3]);
+                    if (MODE == kModeAdjoint) {
+                        const float4 q4 = *reinterpret_cast<const float4 *>(qs + sh + o);
+                        float4 g4 = *reinterpret_cast<const float4 *>(Gs + sh + o);
+                        g4.x += res[0] * q4.x;
+                        g4.y += res[1] * q4.y;
+                        g4.z += res[2] * q4.z;
+                        g4.w += res[3] * q4.w;
+                        *reinterpret_cast<float4 *>(Gs + sh + o) = g4;
+                    }
+                }
+            }
+            // every thread is done with slot kz before it is restaged; a wait
+            // that gave up anywhere ends the march for the whole block
+            bad = __syncthreads_or(!ok) != 0;
+        }
+    }
+    // the last NST planes staged (ahead of the march) may still be in
+    // flight: wait for each (a completed phase returns at once) so no copy
+    // outlives the block
+    if (tid == 0) {
+        if (bad) atomicOr(A.flags, kFlagTimeout);
+        for (int z = max(zb, zlast - NST + 1); z <= zlast; z++) {
+            const int k = (z - zb) % NST;
+            if (!mbar_wait(full + k, ((z - zb) / NST) & 1, spin)) atomicOr(A.flags, kFlagTimeout);
+        }
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------- CPML (3D)
@@ -273,23 +492,16 @@ __device__ __forceinline__ float4 d2_4(const float *f, long long o, long long s)
         const float v[12] = {L.x, L.y, L.z, L.w, C.x, C.y, C.z, C.w, R.x, R.y, R.z, R.w};
 #pragma unroll
         for (int k = 0; k < 4; k++)
-            r[k] = float(kC0) * v[4 + k] + float(kC1) * (v[5 + k] + v[3 + k]) + float(kC2) * (v[6 + k] + v[2 + k]) +
-                   float(kC3) * (v[7 + k] + v[1 + k]) + float(kC4) * (v[8 + k] + v[k]);
+            r[k] = d2c<float>(v[4 + k], v[3 + k], v[5 + k], v[2 + k], v[6 + k], v[1 + k], v[7 + k], v[k], v[8 + k]);
     } else {
         const float4 c = ld4g(f + o);
-        r[0] = float(kC0) * c.x; r[1] = float(kC0) * c.y; r[2] = float(kC0) * c.z; r[3] = float(kC0) * c.w;
-        float4 a = ld4g(f + o + s), b = ld4g(f + o - s);
-        r[0] += float(kC1) * (a.x + b.x); r[1] += float(kC1) * (a.y + b.y);
-        r[2] += float(kC1) * (a.z + b.z); r[3] += float(kC1) * (a.w + b.w);
-        a = ld4g(f + o + 2 * s), b = ld4g(f + o - 2 * s);
-        r[0] += float(kC2) * (a.x + b.x); r[1] += float(kC2) * (a.y + b.y);
-        r[2] += float(kC2) * (a.z + b.z); r[3] += float(kC2) * (a.w + b.w);
-        a = ld4g(f + o + 3 * s), b = ld4g(f + o - 3 * s);
-        r[0] += float(kC3) * (a.x + b.x); r[1] += float(kC3) * (a.y + b.y);
-        r[2] += float(kC3) * (a.z + b.z); r[3] += float(kC3) * (a.w + b.w);
-        a = ld4g(f + o + 4 * s), b = ld4g(f + o - 4 * s);
-        r[0] += float(kC4) * (a.x + b.x); r[1] += float(kC4) * (a.y + b.y);
-        r[2] += float(kC4) * (a.z + b.z); r[3] += float(kC4) * (a.w + b.w);
+        const float4 m1 = ld4g(f + o - s), p1 = ld4g(f + o + s), m2 = ld4g(f + o - 2 * s), p2 = ld4g(f + o + 2 * s);
+        const float4 m3 = ld4g(f + o - 3 * s), p3 = ld4g(f + o + 3 * s), m4 = ld4g(f + o - 4 * s),
+                     p4 = ld4g(f + o + 4 * s);
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            r[k] = d2c<float>(lane4(c, k), lane4(m1, k), lane4(p1, k), lane4(m2, k), lane4(p2, k), lane4(m3, k),
+                              lane4(p3, k), lane4(m4, k), lane4(p4, k));
     }
     return make_float4(r[0], r[1], r[2], r[3]);
 }
@@ -354,8 +566,7 @@ __global__ void k_cpml_add3d(const StepArgs<float> A, const int n, const int ax,
                     const int zz = z + m;
                     c[m + 4] = zz < 0 ? -p[cell_off(g, -zz, y, x + k)] : p[cell_off(g, zz, y, x + k)];
                 }
-                r[k] = float(kC0) * c[4] + float(kC1) * (c[5] + c[3]) + float(kC2) * (c[6] + c[2]) +
-                       float(kC3) * (c[7] + c[1]) + float(kC4) * (c[8] + c[0]);
+                r[k] = d2c<float>(c[4], c[3], c[5], c[2], c[6], c[1], c[7], c[0], c[8]);
             }
             d2 = make_float4(r[0], r[1], r[2], r[3]);
         } else {
@@ -493,10 +704,9 @@ __global__ void __launch_bounds__(128) k_cpml_col3d(const StepArgs<float> A, con
             float zt[4], add[4];
 #pragma unroll
             for (int c = 0; c < 4; c++) {
-                const float d2 = float(kC0) * comp4(P[4], c) + float(kC1) * (comp4(P[5], c) + comp4(P[3], c)) +
-                                 float(kC2) * (comp4(P[6], c) + comp4(P[2], c)) +
-                                 float(kC3) * (comp4(P[7], c) + comp4(P[1], c)) +
-                                 float(kC4) * (comp4(P[8], c) + comp4(P[0], c));
+                const float d2 = d2c<float>(comp4(P[4], c), comp4(P[3], c), comp4(P[5], c), comp4(P[2], c),
+                                            comp4(P[6], c), comp4(P[1], c), comp4(P[7], c), comp4(P[0], c),
+                                            comp4(P[8], c));
                 const float dps = float(kD1) * (comp4(S[5], c) - comp4(S[3], c)) +
                                   float(kD2) * (comp4(S[6], c) - comp4(S[2], c)) +
                                   float(kD3) * (comp4(S[7], c) - comp4(S[1], c)) +
@@ -601,8 +811,7 @@ __global__ void __launch_bounds__(128) k_cpml_row3d(const StepArgs<float> A, con
     float zt[4], add[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        const float d2 = float(kC0) * v[4 + k] + float(kC1) * (v[5 + k] + v[3 + k]) + float(kC2) * (v[6 + k] + v[2 + k]) +
-                         float(kC3) * (v[7 + k] + v[1 + k]) + float(kC4) * (v[8 + k] + v[k]);
+        const float d2 = d2c<float>(v[4 + k], v[3 + k], v[5 + k], v[2 + k], v[6 + k], v[1 + k], v[7 + k], v[k], v[8 + k]);
         const float dps = float(kD1) * (w[5 + k] - w[3 + k]) + float(kD2) * (w[6 + k] - w[2 + k]) +
                           float(kD3) * (w[7 + k] - w[1 + k]) + float(kD4) * (w[8 + k] - w[k]);
         zt[k] = comp4(b4, k) * comp4(zo, k) + comp4(a4, k) * (d2 + dps);
@@ -731,9 +940,49 @@ size_t smem3d() {
 
 }  // namespace
 
+constexpr size_t kSmemTma = (size_t)NST * SLOT_T + NST * sizeof(unsigned long long);
+
+// Tensor maps of one launch (host): the pressure buffers pbuf[0] (both
+// parities of max_shots shots, fstride apart) and c, in the padded layout.
+cudaError_t make_maps(const StepArgs<float> &a, Tma3 &m) {
+    static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+    if (!enc) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return cudaErrorNotSupported;
+        enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const Geom &g = a.g;
+    const long long ms = (a.pbuf[1] - a.pbuf[0]) / g.fstride;
+    const long long planes = g.fstride / ((long long)g.PY * g.P);
+    const cuuint64_t dims[4] = {(cuuint64_t)g.P, (cuuint64_t)g.PY, (cuuint64_t)planes, (cuuint64_t)(2 * ms)};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.P * 4, (cuuint64_t)g.PY * g.P * 4, (cuuint64_t)g.fstride * 4};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    const cuuint32_t bh[4] = {TX + 8, 16, 1, 1}, bo[4] = {TX, 8, 1, 1};
+    CUresult r = enc(&m.ph, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.pbuf[0], dims, strides, bh, one,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r == CUDA_SUCCESS)
+        r = enc(&m.po, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.pbuf[0], dims, strides, bo, one,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r == CUDA_SUCCESS)
+        r = enc(&m.c, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(a.ch), dims, strides, bo, one,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t configure_step3d() {
-    cudaError_t e = cudaFuncSetAttribute(k_step3d<1, kModeForward>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem3d<1>());
+    cudaError_t e = cudaSuccess;
+    for (auto k : {k_step3d_tma<kModeForward>, k_step3d_tma<kModeRecord>, k_step3d_tma<kModeAdjoint>})
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTma);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step3d<1, kModeForward>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem3d<1>());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_step3d<1, kModeRecord>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem3d<1>());
@@ -750,11 +999,11 @@ cudaError_t launch_step3d_mode(cudaLaunchConfig_t &cfg, const StepArgs<float> &a
     return cudaLaunchKernelEx(&cfg, k_step3d<RY, MODE>, a, n, zchunk, qs, Gs);
 }
 
-cudaError_t launch_step3d(const StepArgs<float> &a, int n, int ry, int zchunk, int nshots, cudaStream_t st,
+cudaError_t launch_step3d(const StepArgs<float> &a, int n, int variant, int zchunk, int nshots, cudaStream_t st,
                           bool pdl, int mode, float *qs, float *Gs) {
     const int nchunk = (a.g.NZ + zchunk - 1) / zchunk;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(a.ntx, (a.g.NY + NW * ry - 1) / (NW * ry), nchunk * nshots);
+    cfg.gridDim = dim3(a.ntx, (a.g.NY + NW - 1) / NW, nchunk * nshots);
     cfg.blockDim = dim3(NTH);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -762,7 +1011,17 @@ cudaError_t launch_step3d(const StepArgs<float> &a, int n, int ry, int zchunk, i
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    if (ry != 1) return cudaErrorInvalidValue;
+    if (variant == kZMarchTma) {
+        Tma3 m;
+        if (cudaError_t e = make_maps(a, m)) return e;
+        cfg.dynamicSmemBytes = kSmemTma;
+        const int ms = (int)((a.pbuf[1] - a.pbuf[0]) / a.g.fstride);
+        const long long spin = 1LL << 22;
+        if (mode == kModeRecord) return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeRecord>, a, m, n, zchunk, ms, qs, Gs, spin);
+        if (mode == kModeAdjoint) return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeAdjoint>, a, m, n, zchunk, ms, qs, Gs, spin);
+        return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeForward>, a, m, n, zchunk, ms, qs, Gs, spin);
+    }
+    if (variant != kZMarchAsync) return cudaErrorInvalidValue;
     if (mode == kModeRecord) return launch_step3d_mode<1, kModeRecord>(cfg, a, n, zchunk, qs, Gs);
     if (mode == kModeAdjoint) return launch_step3d_mode<1, kModeAdjoint>(cfg, a, n, zchunk, qs, Gs);
     return launch_step3d_mode<1, kModeForward>(cfg, a, n, zchunk, qs, Gs);

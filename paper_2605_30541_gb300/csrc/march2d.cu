@@ -86,9 +86,8 @@ __device__ __forceinline__ float4 psi_z_row(const float4 &m4, const float4 &m3, 
 
 // z-part of the Laplacian (without 1/h^2) at cell k of the window row w[4]
 __device__ __forceinline__ float d2z_at(const float4 *w, int k) {
-    return float(kC0) * lane_of(w[4], k) + float(kC1) * (lane_of(w[5], k) + lane_of(w[3], k)) +
-           float(kC2) * (lane_of(w[6], k) + lane_of(w[2], k)) + float(kC3) * (lane_of(w[7], k) + lane_of(w[1], k)) +
-           float(kC4) * (lane_of(w[8], k) + lane_of(w[0], k));
+    return d2c<float>(lane_of(w[4], k), lane_of(w[3], k), lane_of(w[5], k), lane_of(w[2], k), lane_of(w[6], k),
+                      lane_of(w[1], k), lane_of(w[7], k), lane_of(w[0], k), lane_of(w[8], k));
 }
 
 // ---------------------------------------------------------------- per-row I/O

@@ -438,10 +438,8 @@ __global__ void __launch_bounds__(NTR, 1) k_resident2d(const StepArgs<float> A, 
             for (int k = 0; k < 4; k++) {
                 const float p = v[4 + k];
                 const float d2x = d2w(v, k);
-                const float d2z = float(kC0) * p + float(kC1) * (lane_of(zw[j + 5], k) + lane_of(zw[j + 3], k)) +
-                                  float(kC2) * (lane_of(zw[j + 6], k) + lane_of(zw[j + 2], k)) +
-                                  float(kC3) * (lane_of(zw[j + 7], k) + lane_of(zw[j + 1], k)) +
-                                  float(kC4) * (lane_of(zw[j + 8], k) + lane_of(zw[j], k));
+                const float d2z = d2c<float>(p, lane_of(zw[j + 3], k), lane_of(zw[j + 5], k), lane_of(zw[j + 2], k), lane_of(zw[j + 6], k),
+                                         lane_of(zw[j + 1], k), lane_of(zw[j + 7], k), lane_of(zw[j], k), lane_of(zw[j + 8], k));
                 float rhs = d2z + d2x;
                 if (cpx) rhs += lane_of(ax4, k);
                 zo[k] = 0.f;

@@ -281,7 +281,9 @@ struct sim_s {
     int march_nwarps = 0, march_nitems = 0;
     unsigned *mctr = nullptr;              // row march: per-step item counters
     int last_path = 0, last_rows = 0;      // see sim_info
-    int zchunk = 0;                        // z-march chunk of the 3D kernel
+    int zchunk = 0;                        // z-march chunk of the 3D kernel (planes per CTA)
+    int zvariant = kZMarchTma;             // z-march staging (cp.async or TMA), see autotune3d
+    int tuned3d = 0;                       // shot count the 3D launch shape was tuned for
     // adjoint-state buffers, allocated by the first sim_adjoint call (on
     // their own list: a call that needs a larger plan frees and re-plans them)
     bool adj_ready = false;
@@ -856,6 +858,70 @@ int zchunk_for(const sim_s *s, int nshots) {
     return (g.NZ + chunks - 1) / chunks;
 }
 
+// 3D launch shape: the z-march variant (per-thread cp.async or TMA staging)
+// and the planes per CTA (z chunk: fewer, longer columns re-read less halo;
+// more, shorter ones fill the GPU). The first forward or gradient call for a
+// shot count times a few steps of each candidate on this GPU with CUDA
+// events (on zeroed fields, before the run resets them) and keeps the
+// fastest. GSIM_ZMARCH=async|tma fixes the variant, GSIM_ZCHUNK the chunk;
+// GSIM_AUTOTUNE=0 takes the TMA variant with the default chunk untimed.
+sim_status autotune3d(sim_t s, int nshots) {
+    if (s->tuned3d == nshots) return SIM_OK;
+    s->tuned3d = nshots;
+    const int base = zchunk_for(s, nshots), NZ = s->g.NZ;
+    std::vector<int> variants = {kZMarchTma, kZMarchAsync};
+    if (const char *f = getenv("GSIM_ZMARCH")) {
+        if (!strcmp(f, "async")) variants = {kZMarchAsync};
+        if (!strcmp(f, "tma")) variants = {kZMarchTma};
+    }
+    s->zvariant = variants[0];
+    s->zchunk = base;
+    const char *at = getenv("GSIM_AUTOTUNE");
+    if (at && at[0] == '0') return SIM_OK;
+    std::vector<int> chunks = {base};
+    for (int c : {NZ, (NZ + 1) / 2, (NZ + 3) / 4, (NZ + 7) / 8})
+        if (c >= 16 && std::find(chunks.begin(), chunks.end(), c) == chunks.end()) chunks.push_back(c);
+    if (const char *f = getenv("GSIM_ZCHUNK")) {  // a fixed chunk (tests)
+        chunks = {std::max(1, std::min(NZ, atoi(f)))};
+        s->zchunk = chunks[0];
+    }
+    if (variants.size() == 1 && chunks.size() == 1) return SIM_OK;
+    if (sim_status r = reset_state(s, nshots)) return r;
+    StepArgs<float> a = step_args<float>(s);
+    cudaEvent_t e0, e1;
+    if (sim_status r = s->cuda(cudaEventCreate(&e0), "tune event")) return r;
+    if (sim_status r = s->cuda(cudaEventCreate(&e1), "tune event")) {
+        cudaEventDestroy(e0);
+        return r;
+    }
+    float best = 1e30f;
+    cudaError_t e = cudaSuccess;
+    for (int v : variants)
+        for (int zc : chunks) {
+            const int warm = 1, timed = 3;
+            for (int n = 0; n < warm + timed && e == cudaSuccess; n++) {
+                if (n == warm) e = cudaEventRecord(e0, s->st);
+                if (e == cudaSuccess) e = launch_step3d(a, n, v, zc, nshots, s->st, false);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s->st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) break;
+            if (getenv("GSIM_TUNE_LOG"))
+                fprintf(stderr, "[gsim autotune] 3D %dx%dx%d shots %d %s chunk %d: %.1f us/step\n", s->g.NZ, s->g.NY,
+                        s->g.NX, nshots, v == kZMarchTma ? "tma" : "async", zc, 1e3 * ms / timed);
+            if (ms < best) {
+                best = ms;
+                s->zvariant = v;
+                s->zchunk = zc;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return s->cuda(e, "3D autotune");
+}
+
 // 3D points: the 8 trilinear corners of each point as field offsets.
 sim_status points3d(sim_t s, int npts, const double *pos, std::vector<Pt3> &out, bool drop_surface,
                     const char *what) {
@@ -912,12 +978,12 @@ sim_status forward3d(sim_t s, int nshots, const void *wav, const double *src_pos
     io.snap_fp16 = d.snap_fp16;
     if (sim_status r = s->cuda(cudaMemcpyAsync(s->io, &io, sizeof io, cudaMemcpyHostToDevice, s->st), "io upload"))
         return r;
+    if (sim_status r = autotune3d(s, nshots)) return r;
     if (sim_status r = reset_state(s, nshots)) return r;
     StepArgs<float> a = step_args<float>(s);
     a.inj_per_shot = 1;
     a.inj_kind = 0;
     a.sample = nrec > 0 && gdev != nullptr;
-    s->zchunk = zchunk_for(s, nshots);
     const bool cpml = d.bc == SIM_BC_CPML;
     const int on[3] = {s->psi[0][0] != nullptr, s->psi[1][0] != nullptr, s->psi[2][0] != nullptr};
     const bool has_src = !src.empty(), has_snap = io.snaps != nullptr;
@@ -930,7 +996,7 @@ sim_status forward3d(sim_t s, int nshots, const void *wav, const double *src_pos
             if (e == cudaSuccess && a.sample) e = launch_sample3d(a, t, r3, nrec, nshots, st);
             for (int ax = 0; ax < 3 && cpml && e == cudaSuccess; ax++)
                 if (on[ax]) e = launch_cpml3d(a, n, ax, 0, nshots, st);
-            if (e == cudaSuccess) e = launch_step3d(a, n, 1, s->zchunk, nshots, st, false);
+            if (e == cudaSuccess) e = launch_step3d(a, n, s->zvariant, s->zchunk, nshots, st, false);
             for (int ax = 0; ax < 3 && cpml && e == cudaSuccess; ax++)
                 if (on[ax]) e = launch_cpml3d(a, n, ax, 1, nshots, st);
             if (e == cudaSuccess && has_src) e = launch_inject3d(a, t, s3, nshots, st);
@@ -1834,8 +1900,9 @@ sim_status adjoint3d(sim_t s, int nshots, const void *wavelet, const double *src
     if (sim_status r = s->cuda(cudaMemcpyAsync(s->io, &io, sizeof io, cudaMemcpyHostToDevice, s->st), "io upload"))
         return r;
 
+    if (sim_status r = autotune3d(s, nshots)) return r;
     const AdjPlan &P = s->plan;
-    const int zc = zchunk_for(s, nshots);
+    const int zc = s->zchunk, zv = s->zvariant;
     const CkLayout ckl = ck_layout(s, ckpt_fp16);
     StepArgs<float> a = step_args<float>(s);
     a.sample = 1;
@@ -1868,7 +1935,7 @@ sim_status adjoint3d(sim_t s, int nshots, const void *wavelet, const double *src
                 if (sample) e2 = launch_sample3d(A, step_time(s, A, n, kModeForward, nullptr, nullptr), r3, nrec,
                                                  nshots, st);
                 if (e2 == cudaSuccess && cpml) e2 = cpml_pass(n, 0, nullptr, st);
-                if (e2 == cudaSuccess) e2 = launch_step3d(A, n, 1, zc, nshots, st, true, mode, slot, nullptr);
+                if (e2 == cudaSuccess) e2 = launch_step3d(A, n, zv, zc, nshots, st, true, mode, slot, nullptr);
                 if (e2 == cudaSuccess && cpml) e2 = cpml_pass(n, 1, slot, st);
                 if (e2 == cudaSuccess)
                     e2 = launch_inj3d(A, n, n, s->src3g, nsg, s->src3e, 0, nshots, mode, slot, nullptr, st);
@@ -1882,7 +1949,7 @@ sim_status adjoint3d(sim_t s, int nshots, const void *wavelet, const double *src
                 [&](int k, int i) {
                     float *slot = slot_of(i);
                     const int n = d.nt - k;
-                    cudaError_t e2 = launch_step3d(adj, n, 1, zc, nshots, st, true, kModeAdjoint, slot, Gs);
+                    cudaError_t e2 = launch_step3d(adj, n, zv, zc, nshots, st, true, kModeAdjoint, slot, Gs);
                     if (e2 == cudaSuccess)
                         e2 = launch_inj3d(adj, n, k, s->res3g, nrg, s->res3e, 1, nshots, kModeAdjoint, slot, Gs, st);
                     if (e2 == cudaSuccess && cpml && k <= d.nt - 1) {  // nu^k, mu^k from u^{k+1}; c [.] into u^k

@@ -2,6 +2,7 @@
 // the launch entry points each translation unit provides. Host code is C++17.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -223,8 +224,18 @@ cudaError_t launch_march2d(const MarchArgs &m, bool cpml, const StepTime &t, cud
 
 // 3D launchers (fwd3d.cu). Per step: snapshot, sample, CPML psi, z-march
 // update, CPML zeta + addend, source injection.
+// z-march variants: kZMarchAsync stages each plane by per-thread 16-byte
+// cp.async copies; kZMarchTma by three bulk tensor copies (TMA) per plane
+// issued by one thread, completion on mbarriers. Both take z chunks of
+// `zchunk` planes per CTA.
+enum { kZMarchAsync = 1, kZMarchTma = 2 };
+struct Tma3 {
+    CUtensorMap ph;  // p (both parities, all shots): 136 x 16 x 1 boxes, the plane with its x / y halo
+    CUtensorMap po;  // the same buffers: 128 x 8 x 1 boxes, a tile's own cells
+    CUtensorMap c;   // c = (v dt / h)^2: 128 x 8 x 1 boxes
+};
 cudaError_t configure_step3d();
-cudaError_t launch_step3d(const StepArgs<float> &a, int n, int ry, int zchunk, int nshots, cudaStream_t st,
+cudaError_t launch_step3d(const StepArgs<float> &a, int n, int variant, int zchunk, int nshots, cudaStream_t st,
                           bool pdl, int mode = kModeForward, float *qs = nullptr, float *Gs = nullptr);
 // 3D point injection grouped by target cell (the adjoint path): group =
 // cell offset within a field, entry range, shot (-1: the same for every

@@ -14,11 +14,33 @@ constexpr double kC0 = -205.0 / 72.0, kC1 = 8.0 / 5.0, kC2 = -1.0 / 5.0, kC3 = 8
 // Central first-derivative weights of order 8, without the 1/h (CPML memory terms).
 constexpr double kD1 = 4.0 / 5.0, kD2 = -1.0 / 5.0, kD3 = 4.0 / 105.0, kD4 = -1.0 / 280.0;
 
-// sum_m w_m (p[m s] + p[-m s]) + w_0 p[0]
+// Centre weight of the outer pairs: w_0 = -2 (w_1 + w_2 + w_3 + w_4), so
+// sum_m w_m (p_m + p_-m) + w_0 p_0 = sum_{m=1,2} w_m ((p_m - p_0) + (p_-m - p_0))
+//                                   + sum_{m=3,4} w_m (p_m + p_-m) + kC34 p_0.
+constexpr double kC34 = -2.0 * (kC3 + kC4);
+
+// Second difference along one axis (without 1/h^2) from the nine values
+// c = p_0 and m_k = p_-k, p_k = p_+k. The two inner pairs, whose weights are
+// large, enter as differences from the centre: for a smooth field those are
+// exact in floating point and small, so the result carries no rounding error
+// of the size of w_0 p_0 (the plain form cancels terms 2.85 |p_0| large; over
+// thousands of FP32 steps that error accumulates into the wavefield). Summed
+// from the smallest term up; every kernel uses this one expression, so all
+// paths give the same bits.
+template <typename T>
+__device__ __forceinline__ T d2c(T c, T m1, T p1, T m2, T p2, T m3, T p3, T m4, T p4) {
+    T r = T(kC34) * c;
+    r += T(kC4) * (p4 + m4);
+    r += T(kC3) * (p3 + m3);
+    r += T(kC2) * ((p2 - c) + (m2 - c));
+    r += T(kC1) * ((p1 - c) + (m1 - c));
+    return r;
+}
+
+// the second difference at p[0] along stride s
 template <typename T>
 __device__ __forceinline__ T d2_col(const T *p, int s) {
-    return T(kC0) * p[0] + T(kC1) * (p[s] + p[-s]) + T(kC2) * (p[2 * s] + p[-2 * s]) +
-           T(kC3) * (p[3 * s] + p[-3 * s]) + T(kC4) * (p[4 * s] + p[-4 * s]);
+    return d2c<T>(p[0], p[-s], p[s], p[-2 * s], p[2 * s], p[-3 * s], p[3 * s], p[-4 * s], p[4 * s]);
 }
 
 // sum_m d_m (p[m s] - p[-m s])
