@@ -2165,7 +2165,15 @@ cudaError_t grow(void **p, size_t *cap, size_t need) {
     return e;
 }
 
-sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst) {
+// Batch schedules: the row march (one launch per step over every member),
+// the stepped tile kernel (one launch per step) and the persistent dataflow
+// kernel (one launch for all steps).
+enum { kBatchMarch = 0, kBatchStepped = 1, kBatchPersistent = 2 };
+
+// One batch run with a given schedule and list tile height. probe > 0: run
+// only that many steps, launched directly (the autotuner's timing probe; no
+// graph, no output copies).
+sim_status batch_run(int nitems, const sim_batch_item *items, cudaStream_t bst, int sched, int tz_in, int probe) {
     if (nitems < 1 || !items) return thread_fail(SIM_ERR_ARG, "empty batch");
     sim_t s0 = items[0].sim;
     if (!s0) return thread_fail(SIM_ERR_ARG, "batch item 0 has no handle");
@@ -2187,20 +2195,11 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
     }
     cudaSetDevice(s0->dev);
     const int nt = s0->d.nt;
-    // Three schedules: "march" (default) launches step n of every member as
-    // one row-march launch, nt launches replayed as a graph (streams the batch
-    // through HBM); "stepped" (GSIM_BATCH=stepped) does the same with the
-    // tiled step kernel; "persistent" (GSIM_BATCH=persistent) runs the
-    // dataflow kernel k_batch2d, one launch for all steps.
-    const char *bm = getenv("GSIM_BATCH");
-    const bool persistent = bm && strcmp(bm, "persistent") == 0;
-    const bool march = !persistent && !(bm && strcmp(bm, "stepped") == 0);
+    const int nsteps = probe > 0 ? std::min(probe, nt) : nt;
+    const bool persistent = sched == kBatchPersistent;
+    const bool march = sched == kBatchMarch;
     const bool stepped = !persistent;
-    int tz = persistent || march ? 16 : 32;
-    if (const char *f = getenv("GSIM_TILE_Z")) {
-        const int v = atoi(f);
-        if (v == 8 || v == 16 || v == 32) tz = v;
-    }
+    const int tz = tz_in;
     bool any_cpml = false;
     std::vector<StepArgs<float>> slices(nitems);
     std::vector<void *> gdev(nitems, nullptr);
@@ -2391,7 +2390,7 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
         if (march) {
             cudaError_t r = cudaMemsetAsync(ctx->flags, 0, sizeof(unsigned), st);
             if (r == cudaSuccess && mb.ctr) r = cudaMemsetAsync(mb.ctr, 0, 2 * sizeof(unsigned), st);
-            for (int n = 0; n < nt && r == cudaSuccess; n++) {
+            for (int n = 0; n < nsteps && r == cudaSuccess; n++) {
                 StepTime t{};
                 t.n = n;
                 t.snap_k = t.max_k = -1;
@@ -2402,7 +2401,7 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
         }
         if (stepped) {
             cudaError_t r = cudaMemsetAsync(ctx->flags, 0, sizeof(unsigned), st);
-            for (int n = 0; n < nt && r == cudaSuccess; n++)
+            for (int n = 0; n < nsteps && r == cudaSuccess; n++)
                 r = launch_multi2d(b, tz, any_cpml, (int)done_total, n, st, st != nullptr);
             return r;
         }
@@ -2412,6 +2411,10 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
         if (r == cudaSuccess) r = launch_batch2d(b, tz, any_cpml, grid, st);
         return r;
     };
+    if (probe > 0) {  // timing probe: launch directly, leave outputs alone
+        if ((e = body(bst))) return fail(e, "launch");
+        return SIM_OK;
+    }
     if (bst == nullptr) {  // the legacy stream cannot be captured: launch directly
         if ((e = body(bst))) return fail(e, "launch");
     } else {
@@ -2453,6 +2456,85 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
     for (int i = 0; i < nitems; i++)
         if (sim_status r = poll_flags(items[i].sim, wait)) return r;
     return SIM_OK;
+}
+
+// Batch autotuner: the schedule (row march, or the stepped kernel with list
+// tiles of 8, 16 or 32 rows) of a batch shape (every item's grid, boundary,
+// shot count, receivers; nt) is picked on its first call by timing a short
+// probe of each candidate with CUDA events on the batch stream, and cached
+// for the process. The persistent kernel (slower wherever measured: every
+// item pays a counter, an acquire wait and a release) runs only when forced:
+// GSIM_BATCH=march|stepped|persistent fixes the schedule, GSIM_TILE_Z the
+// tile height, GSIM_AUTOTUNE=0 takes the row march untimed.
+std::mutex g_btune_mu;
+std::map<std::vector<long long>, std::pair<int, int>> g_btune;
+
+sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst) {
+    if (nitems < 1 || !items || !items[0].sim) return batch_run(nitems, items, bst, kBatchMarch, 16, 0);
+    int sched = -1, tz = 0;
+    if (const char *bm = getenv("GSIM_BATCH")) {
+        if (!strcmp(bm, "persistent")) sched = kBatchPersistent;
+        else if (!strcmp(bm, "stepped")) sched = kBatchStepped;
+        else if (!strcmp(bm, "march")) sched = kBatchMarch;
+    }
+    if (const char *f = getenv("GSIM_TILE_Z")) {
+        const int v = atoi(f);
+        if (v == 8 || v == 16 || v == 32) tz = v;
+    }
+    const char *at = getenv("GSIM_AUTOTUNE");
+    const bool untimed = at && at[0] == '0';
+    if (sched >= 0 || untimed) {
+        if (sched < 0) sched = kBatchMarch;
+        return batch_run(nitems, items, bst, sched, tz ? tz : (sched == kBatchStepped ? 32 : 16), 0);
+    }
+    std::vector<long long> key = {items[0].sim->dev, items[0].sim->d.nt, tz};
+    for (int i = 0; i < nitems; i++) {
+        const sim_s *s = items[i].sim;
+        if (!s) return batch_run(nitems, items, bst, kBatchMarch, 16, 0);  // reports the bad item
+        key.insert(key.end(), {(long long)s->g.NZ, (long long)s->g.NX, (long long)s->d.bc, (long long)s->d.free_surface,
+                               (long long)items[i].nshots, (long long)(items[i].nrec > 0 && items[i].gather)});
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_btune_mu);
+        auto it = g_btune.find(key);
+        if (it != g_btune.end()) return batch_run(nitems, items, bst, it->second.first, it->second.second, 0);
+    }
+    std::vector<std::pair<int, int>> cand;
+    if (tz) cand = {{kBatchMarch, tz}, {kBatchStepped, tz}};
+    else cand = {{kBatchMarch, 16}, {kBatchStepped, 8}, {kBatchStepped, 16}, {kBatchStepped, 32}};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return thread_fail(SIM_ERR_CUDA, "batch autotune: event creation failed");
+    }
+    float best = 1e30f;
+    std::pair<int, int> pick = cand[0];
+    sim_status rc = SIM_OK;
+    for (const auto &c : cand) {
+        const int steps = 6;
+        if ((rc = batch_run(nitems, items, bst, c.first, c.second, 2))) break;  // warm-up (and first-use set-up)
+        cudaEventRecord(e0, bst);
+        if ((rc = batch_run(nitems, items, bst, c.first, c.second, steps))) break;
+        cudaEventRecord(e1, bst);
+        float ms = 0;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            cudaGetLastError();
+            rc = thread_fail(SIM_ERR_CUDA, "batch autotune timing failed");
+            break;
+        }
+        if (getenv("GSIM_TUNE_LOG"))
+            fprintf(stderr, "[gsim autotune] batch of %d items: %s tile %d: %.1f us/step (probe)\n", nitems,
+                    c.first == kBatchMarch ? "march" : "stepped", c.second, 1e3 * ms / steps);
+        if (ms < best) best = ms, pick = c;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_btune_mu);
+        g_btune[key] = pick;
+    }
+    return batch_run(nitems, items, bst, pick.first, pick.second, 0);
 }
 
 }  // namespace

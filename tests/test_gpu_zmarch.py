@@ -71,7 +71,7 @@ def test_variants_and_chunks_agree_with_oracle(pkg, monkeypatch, bc, fs):
 def test_variants_give_the_same_gradient(pkg, monkeypatch):
     cfg, vel, w, src, rec = case("cpml", 0, nt=90)
     cfg.update(snap_every=0, snap_end=0)
-    v0 = np.asarray(synth.smooth(vel, 3.0), np.float32)
+    v0 = np.asarray(0.95 * synth.smooth(vel, 3.0), np.float32)  # a misfit far above the FP32 rounding of g
     d = np.stack([oracle.forward(cfg, vel.astype(np.float64), w.astype(np.float64), src=s, rec=rec)["gather"]
                   for s in src])
     ref = np.zeros(v0.shape)
