@@ -29,6 +29,7 @@ constexpr int TX = kTileXF, NW = 8, NTH = NW * 32, SW3 = TX + 8;
 __device__ __forceinline__ float lane4(const float4 &v, int k) {
     return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
+__device__ __forceinline__ float4 ld4g(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void cp16(void *smem, const void *gmem) {
     const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
@@ -206,6 +207,37 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d(const StepArgs<float> A, cons
     cp_wait<0>();  // no copy into shared memory outlives the block
 }
 
+// ---------------------------------------------------------------- x-strip CPML arithmetic
+// One float4 of x cells (v: the 12-float window of p^n around it, cells
+// v[4..7]); shared by the x-strip pass (k_cpml_row3d) and the z-march that
+// folds the x strips in, so both give the same bits.
+//   psi^n  = b psi^{n-1} + a D1 p^n
+//   zeta^n = b zeta^{n-1} + a (D2 p^n + D1 psi^n),   addend = D1 psi^n + zeta^n
+__device__ __forceinline__ float4 xcpml_psi(const float *v, const float4 old, const float4 a4, const float4 b4) {
+    float r[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        r[k] = lane4(b4, k) * lane4(old, k) +
+               lane4(a4, k) * (float(kD1) * (v[5 + k] - v[3 + k]) + float(kD2) * (v[6 + k] - v[2 + k]) +
+                               float(kD3) * (v[7 + k] - v[1 + k]) + float(kD4) * (v[8 + k] - v[k]));
+    return make_float4(r[0], r[1], r[2], r[3]);
+}
+// w: the 12-float window of psi^n; d2[k]: D2 p^n of the cells
+__device__ __forceinline__ void xcpml_zeta(const float *w, const float *d2, const float4 zo, const float4 a4,
+                                           const float4 b4, float *zt, float *add) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const float dps = float(kD1) * (w[5 + k] - w[3 + k]) + float(kD2) * (w[6 + k] - w[2 + k]) +
+                          float(kD3) * (w[7 + k] - w[1 + k]) + float(kD4) * (w[8 + k] - w[k]);
+        zt[k] = lane4(b4, k) * lane4(zo, k) + lane4(a4, k) * (d2[k] + dps);
+        add[k] = dps + zt[k];
+    }
+}
+// the float4 starting at cell x holds x-strip cells
+__device__ __forceinline__ bool xstrip4(const Geom &g, int x) {
+    return x + 3 >= 0 && x < g.NX && ((g.nbx0 > 0 && x < g.nbx0) || (g.nbx1 > 0 && x + 3 >= g.NX - g.nbx1));
+}
+
 // ---------------------------------------------------------------- z-march with TMA
 //
 // The same update as k_step3d, with the planes staged by the tensor memory
@@ -260,10 +292,26 @@ __device__ __forceinline__ void tma_load3(void *dst, const CUtensorMap *m, int x
         : "memory");
 }
 
+// x strips folded into the march: the float4s overlapping [0, lqb) and
+// [rqa, NX) take the x-CPML addend (their psi / zeta where they hold strip
+// cells); both ranges lie inside the first / last x tile.
+struct XFuse {
+    int on, lqb, rqa, pad;
+};
+
+__device__ __forceinline__ float4 shfl4w(const float4 v, bool up) {
+    float4 r;
+    r.x = up ? __shfl_up_sync(0xffffffffu, v.x, 1) : __shfl_down_sync(0xffffffffu, v.x, 1);
+    r.y = up ? __shfl_up_sync(0xffffffffu, v.y, 1) : __shfl_down_sync(0xffffffffu, v.y, 1);
+    r.z = up ? __shfl_up_sync(0xffffffffu, v.z, 1) : __shfl_down_sync(0xffffffffu, v.z, 1);
+    r.w = up ? __shfl_up_sync(0xffffffffu, v.w, 1) : __shfl_down_sync(0xffffffffu, v.w, 1);
+    return r;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, const __grid_constant__ Tma3 M,
-                                                       const int n, const int zchunk, const int ms, float *qs,
-                                                       float *Gs, const long long spin) {
+                                                       const int n, const int zchunk, const int ms, const XFuse X,
+                                                       float *qs, float *Gs, const long long spin) {
     constexpr int TY = NW, NR = TY + 8;
     extern __shared__ __align__(128) unsigned char sm_t[];
     unsigned char *const ring = sm_t;
@@ -292,6 +340,8 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
         Ey = __ldg(A.E[1] + y0 + w);
     }
     const long long own0 = cell_off(g, 0, y0 + w, gx0);
+    // this tile holds x-strip cells whose CPML the march takes (block-uniform)
+    const bool xtile = MODE != kModeAdjoint && X.on && (x0 < X.lqb || x0 + TX > X.rqa);
     // tensor coordinates of the padded layout: (x, y, z) + kGhost; w = buffer parity * ms + shot
     const int tx = x0 + kGhost, ty = y0 + kGhost;
     const int wcur = (n & 1) * ms + shot, wprev = ((n + 1) & 1) * ms + shot;
@@ -349,6 +399,7 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
             const int kz = (z - zb) % NST, k4 = (z + 4 - zb) % NST;
             bool ok = mbar_wait(full + kz, ((z - zb) / NST) & 1, spin);
             ok = ok && mbar_wait(full + k4, ((z + 4 - zb) / NST) & 1, spin);
+            ok = __all_sync(0xffffffffu, ok);  // the warp computes (and shuffles) together or not at all
             if (ok) {
                 const float *cur = reinterpret_cast<const float *>(ring + kz * SLOT_T);
                 const float *ahead = reinterpret_cast<const float *>(ring + k4 * SLOT_T);
@@ -364,11 +415,12 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
                 for (int m = 0; m < 9; m++) yv[m] = *reinterpret_cast<const float4 *>(row + (m - 4) * SW3);
                 const float4 pp4 = *reinterpret_cast<const float4 *>(cur + NR * SW3 + w * TX + 4 * lane);
                 const float4 ch4 = *reinterpret_cast<const float4 *>(cur + NR * SW3 + TY * TX + w * TX + 4 * lane);
-                float res[4], qk[4];
+                float res[4], qk[4], d2xs[4];
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     const float p = v[4 + k];
                     const float d2x = d2c<float>(p, v[3 + k], v[5 + k], v[2 + k], v[6 + k], v[1 + k], v[7 + k], v[k], v[8 + k]);
+                    d2xs[k] = d2x;
                     const float d2y = d2c<float>(p, lane4(yv[3], k), lane4(yv[5], k), lane4(yv[2], k), lane4(yv[6], k),
                                                 lane4(yv[1], k), lane4(yv[7], k), lane4(yv[0], k), lane4(yv[8], k));
                     const float d2z = d2c<float>(p, lane4(q[(j + 3) % 9], k), lane4(q[(j + 5) % 9], k),
@@ -387,6 +439,39 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
                     }
                     res[k] = out;
                     qk[k] = es * (out - pp) - rhs;
+                }
+                if (xtile) {  // x-strip CPML of the row, as k_cpml_row3d computes it after the update
+                    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    const long long o = sh + own0 + (long long)z * PP;
+                    const bool strip = gy < g.NY && xstrip4(g, gx0);
+                    const bool inw = gy < g.NY && gx0 < g.NX && (gx0 < X.lqb || gx0 + 3 >= X.rqa);
+                    const bool zrow = !(g.fs && z == 0);  // the free-surface row stays zero
+                    float4 a4 = zero4, b4 = zero4, old = zero4, zo = zero4;
+                    if (strip) {
+                        a4 = ld4g(A.ca[2] + gx0);
+                        b4 = ld4g(A.cb[2] + gx0);
+                        old = ld4g(A.psi[2][0] + o);
+                        if (zrow) zo = ld4g(A.zeta[2] + o);
+                    }
+                    float4 ps = zero4;
+                    if (strip) {
+                        ps = xcpml_psi(v, old, a4, b4);
+                        *reinterpret_cast<float4 *>(A.psi[2][0] + o) = ps;
+                    }
+                    float4 sL = shfl4w(ps, true), sR = shfl4w(ps, false);
+                    if (lane == 0) sL = zero4;
+                    if (lane == 31) sR = zero4;
+                    if (inw && zrow) {
+                        const float wv[12] = {sL.x, sL.y, sL.z, sL.w, ps.x, ps.y, ps.z, ps.w, sR.x, sR.y, sR.z, sR.w};
+                        float zt[4], add[4];
+                        xcpml_zeta(wv, d2xs, zo, a4, b4, zt, add);
+                        if (strip) *reinterpret_cast<float4 *>(A.zeta[2] + o) = make_float4(zt[0], zt[1], zt[2], zt[3]);
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            res[k] += lane4(ch4, k) * add[k];
+                            qk[k] -= add[k];
+                        }
+                    }
                 }
                 if (xedge) {
 #pragma unroll
@@ -455,7 +540,6 @@ __device__ __forceinline__ bool box_item(const Box &b, long long i, int &z, int 
 __device__ __forceinline__ long long box_items(const Box &b) {
     return (long long)(b.z1 - b.z0) * (b.y1 - b.y0) * ((b.x1 - b.x0) >> 2);
 }
-__device__ __forceinline__ float4 ld4g(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 
 // D1 of the float4 at o along axis stride s (s > 1), or along x from a
 // 12-float window (s == 1)
@@ -771,7 +855,7 @@ __global__ void __launch_bounds__(128) k_cpml_row3d(const StepArgs<float> A, con
     const long long o = (long long)blockIdx.y * g.fstride + cell_off(g, z, y, 0) + xj;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     const int NX = g.NX, nbx0 = g.nbx0, nbx1 = g.nbx1;
-    const bool strip = xj + 3 >= 0 && xj < NX && ((nbx0 > 0 && xj < nbx0) || (nbx1 > 0 && xj + 3 >= NX - nbx1));
+    const bool strip = xstrip4(g, xj);
     const bool pl = live && j < nq + 4, sl = live && j >= 1 && j < nq + 3, ql = live && j >= 2 && j < nq + 2;
 
     // every load of the lane first (one DRAM round trip), then the arithmetic
@@ -796,27 +880,17 @@ __global__ void __launch_bounds__(128) k_cpml_row3d(const StepArgs<float> A, con
     // psi^n of the lane's cells
     float4 ps = zero;
     if (ss) {
-        float r[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-            r[k] = comp4(b4, k) * comp4(old, k) +
-                   comp4(a4, k) * (float(kD1) * (v[5 + k] - v[3 + k]) + float(kD2) * (v[6 + k] - v[2 + k]) +
-                                   float(kD3) * (v[7 + k] - v[1 + k]) + float(kD4) * (v[8 + k] - v[k]));
-        ps = make_float4(r[0], r[1], r[2], r[3]);
+        ps = xcpml_psi(v, old, a4, b4);
         *reinterpret_cast<float4 *>(psi) = ps;
     }
     const float4 sL = shfl4(ps, 1, true), sR = shfl4(ps, 1, false);
     if (!qs) return;
     const float w[12] = {sL.x, sL.y, sL.z, sL.w, ps.x, ps.y, ps.z, ps.w, sR.x, sR.y, sR.z, sR.w};
-    float zt[4], add[4];
+    float d2[4], zt[4], add[4];
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const float d2 = d2c<float>(v[4 + k], v[3 + k], v[5 + k], v[2 + k], v[6 + k], v[1 + k], v[7 + k], v[k], v[8 + k]);
-        const float dps = float(kD1) * (w[5 + k] - w[3 + k]) + float(kD2) * (w[6 + k] - w[2 + k]) +
-                          float(kD3) * (w[7 + k] - w[1 + k]) + float(kD4) * (w[8 + k] - w[k]);
-        zt[k] = comp4(b4, k) * comp4(zo, k) + comp4(a4, k) * (d2 + dps);
-        add[k] = dps + zt[k];
-    }
+    for (int k = 0; k < 4; k++)
+        d2[k] = d2c<float>(v[4 + k], v[3 + k], v[5 + k], v[2 + k], v[6 + k], v[1 + k], v[7 + k], v[k], v[8 + k]);
+    xcpml_zeta(w, d2, zo, a4, b4, zt, add);
     if (strip) *reinterpret_cast<float4 *>(zeta) = make_float4(zt[0], zt[1], zt[2], zt[3]);
     pv.x += c4.x * add[0];
     pv.y += c4.y * add[1];
@@ -942,6 +1016,42 @@ size_t smem3d() {
 
 constexpr size_t kSmemTma = (size_t)NST * SLOT_T + NST * sizeof(unsigned long long);
 
+// Which x-strip pass a CPML step uses: the one-pass kernel k_cpml_row3d when
+// each widened strip spans at most 12 float4s and the two ends are apart;
+// with the TMA march (forward and record modes) the march takes it over when,
+// moreover, each widened strip lies inside the first / last x tile.
+bool x_row_pass(const Geom &g, XEnds *E) {
+    const int NX = g.NX;
+    int qa[2], qb[2], m = 0;  // widened strips [qa, qb)
+    if (g.nbx0 > 0) qa[m] = 0, qb[m++] = std::min(NX, g.nbx0 + 4);
+    if (g.nbx1 > 0) qa[m] = std::max(0, NX - g.nbx1 - 4), qb[m++] = NX;
+    bool ok = m > 0 && (m < 2 || qa[1] - qb[0] >= 16);  // ends apart: no cell's psi formed twice
+    XEnds e{};
+    for (int k = 0; k < m && ok; k++) {
+        const int q4 = qa[k] & ~3, nq = (qb[k] - q4 + 3) >> 2;
+        e.xa[k] = q4 - 8;
+        e.nq[k] = nq;
+        ok = nq + 4 <= 16;
+    }
+    e.ne = m;
+    if (E) *E = e;
+    return ok;
+}
+
+XFuse x_fuse(const StepArgs<float> &a, int variant, int mode) {
+    XFuse X{0, 0, 1 << 30, 0};
+    const Geom &g = a.g;
+    if (variant != kZMarchTma || mode == kModeAdjoint || a.bc != SIM_BC_CPML || !a.ca[2] || !x_row_pass(g, nullptr))
+        return X;
+    X.lqb = g.nbx0 > 0 ? std::min(g.NX, g.nbx0 + 4) : 0;
+    X.rqa = g.nbx1 > 0 ? std::max(0, g.NX - g.nbx1 - 4) : (1 << 30);
+    const int last = ((g.NX - 1) / TX) * TX;
+    X.on = X.lqb <= TX && (g.nbx1 == 0 || X.rqa >= last);
+    return X;
+}
+
+bool zmarch_folds_x(const StepArgs<float> &a, int variant, int mode) { return x_fuse(a, variant, mode).on != 0; }
+
 // Tensor maps of one launch (host): the pressure buffers pbuf[0] (both
 // parities of max_shots shots, fstride apart) and c, in the padded layout.
 cudaError_t make_maps(const StepArgs<float> &a, Tma3 &m) {
@@ -1017,9 +1127,12 @@ cudaError_t launch_step3d(const StepArgs<float> &a, int n, int variant, int zchu
         cfg.dynamicSmemBytes = kSmemTma;
         const int ms = (int)((a.pbuf[1] - a.pbuf[0]) / a.g.fstride);
         const long long spin = 1LL << 22;
-        if (mode == kModeRecord) return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeRecord>, a, m, n, zchunk, ms, qs, Gs, spin);
-        if (mode == kModeAdjoint) return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeAdjoint>, a, m, n, zchunk, ms, qs, Gs, spin);
-        return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeForward>, a, m, n, zchunk, ms, qs, Gs, spin);
+        const XFuse X = x_fuse(a, variant, mode);
+        if (mode == kModeRecord)
+            return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeRecord>, a, m, n, zchunk, ms, X, qs, Gs, spin);
+        if (mode == kModeAdjoint)
+            return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeAdjoint>, a, m, n, zchunk, ms, X, qs, Gs, spin);
+        return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeForward>, a, m, n, zchunk, ms, X, qs, Gs, spin);
     }
     if (variant != kZMarchAsync) return cudaErrorInvalidValue;
     if (mode == kModeRecord) return launch_step3d_mode<1, kModeRecord>(cfg, a, n, zchunk, qs, Gs);
@@ -1047,20 +1160,9 @@ cudaError_t launch_cpml3d(const StepArgs<float> &a, int n, int ax, int phase, in
     const int lo[3] = {g.nbz0, g.nby0, g.nbx0}, hi[3] = {g.nbz1, g.nby1, g.nbx1};
     if (ax == 2) {  // x: one pass after the update (phase 1), when each widened strip spans <= 12 float4s
         XEnds E{};
-        const int NX = N[2];
-        int qa[2], qb[2], m = 0;  // widened strips [qa, qb)
-        if (lo[2] > 0) qa[m] = 0, qb[m++] = std::min(NX, lo[2] + 4);
-        if (hi[2] > 0) qa[m] = std::max(0, NX - hi[2] - 4), qb[m++] = NX;
-        bool ok = m > 0 && (m < 2 || qa[1] - qb[0] >= 16);  // ends apart: no cell's psi formed twice
-        for (int k = 0; k < m && ok; k++) {
-            const int q4 = qa[k] & ~3, nq = (qb[k] - q4 + 3) >> 2;
-            E.xa[k] = q4 - 8;
-            E.nq[k] = nq;
-            ok = nq + 4 <= 16;
-        }
-        if (ok) {
+        if (x_row_pass(g, &E)) {
             if (phase == 0) return cudaSuccess;
-            E.ne = m;
+            const int m = E.ne;
             const long long nrows = (long long)g.NZ * g.NY, th = 16 * m * nrows;
             k_cpml_row3d<<<dim3((unsigned)((th + 127) / 128), nshots), 128, 0, st>>>(a, n, E, nrows, qs);
             return cudaGetLastError();

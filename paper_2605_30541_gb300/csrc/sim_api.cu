@@ -858,6 +858,25 @@ int zchunk_for(const sim_s *s, int nshots) {
     return (g.NZ + chunks - 1) / chunks;
 }
 
+// One forward-type 3D step without its point work: the CPML passes of the
+// absorbing axes around the z-march (the x axis first, as the march that
+// folds the x strips in adds their term first), skipping the x pass when the
+// march takes it over. slot: the record mode's imaging term (else NULL).
+cudaError_t step3d_core(const sim_s *s, const StepArgs<float> &a, int n, int variant, int zc, int nshots,
+                        cudaStream_t st, bool pdl, int mode, float *slot) {
+    const bool cpml = s->d.bc == SIM_BC_CPML;
+    const bool on[3] = {s->psi[0][0] != nullptr, s->psi[1][0] != nullptr, s->psi[2][0] != nullptr};
+    const bool fx = cpml && zmarch_folds_x(a, variant, mode);
+    const int order[3] = {2, 0, 1};
+    cudaError_t e = cudaSuccess;
+    for (int ax : order)
+        if (e == cudaSuccess && cpml && on[ax] && !(ax == 2 && fx)) e = launch_cpml3d(a, n, ax, 0, nshots, st);
+    if (e == cudaSuccess) e = launch_step3d(a, n, variant, zc, nshots, st, pdl, mode, slot, nullptr);
+    for (int ax : order)
+        if (e == cudaSuccess && cpml && on[ax] && !(ax == 2 && fx)) e = launch_cpml3d(a, n, ax, 1, nshots, st, slot);
+    return e;
+}
+
 // 3D launch shape: the z-march variant (per-thread cp.async or TMA staging)
 // and the planes per CTA (z chunk: fewer, longer columns re-read less halo;
 // more, shorter ones fill the GPU). The first forward or gradient call for a
@@ -901,7 +920,7 @@ sim_status autotune3d(sim_t s, int nshots) {
             const int warm = 1, timed = 3;
             for (int n = 0; n < warm + timed && e == cudaSuccess; n++) {
                 if (n == warm) e = cudaEventRecord(e0, s->st);
-                if (e == cudaSuccess) e = launch_step3d(a, n, v, zc, nshots, s->st, false);
+                if (e == cudaSuccess) e = step3d_core(s, a, n, v, zc, nshots, s->st, false, kModeForward, nullptr);
             }
             if (e == cudaSuccess) e = cudaEventRecord(e1, s->st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -984,8 +1003,6 @@ sim_status forward3d(sim_t s, int nshots, const void *wav, const double *src_pos
     a.inj_per_shot = 1;
     a.inj_kind = 0;
     a.sample = nrec > 0 && gdev != nullptr;
-    const bool cpml = d.bc == SIM_BC_CPML;
-    const int on[3] = {s->psi[0][0] != nullptr, s->psi[1][0] != nullptr, s->psi[2][0] != nullptr};
     const bool has_src = !src.empty(), has_snap = io.snaps != nullptr;
     const Pt3 *s3 = s->src3, *r3 = s->rec3;
     return run_graph(s, ((long long)nshots << 8) | (3 << 2) | 2, [&](cudaStream_t st) {
@@ -994,11 +1011,8 @@ sim_status forward3d(sim_t s, int nshots, const void *wav, const double *src_pos
             const StepTime t = step_time(s, a, n, kModeForward, nullptr, nullptr);
             if (has_snap && t.snap_k >= 0) e = launch_snap3d(a, t, d.snap_fp16, nshots, st);
             if (e == cudaSuccess && a.sample) e = launch_sample3d(a, t, r3, nrec, nshots, st);
-            for (int ax = 0; ax < 3 && cpml && e == cudaSuccess; ax++)
-                if (on[ax]) e = launch_cpml3d(a, n, ax, 0, nshots, st);
-            if (e == cudaSuccess) e = launch_step3d(a, n, s->zvariant, s->zchunk, nshots, st, false);
-            for (int ax = 0; ax < 3 && cpml && e == cudaSuccess; ax++)
-                if (on[ax]) e = launch_cpml3d(a, n, ax, 1, nshots, st);
+            if (e == cudaSuccess)
+                e = step3d_core(s, a, n, s->zvariant, s->zchunk, nshots, st, false, kModeForward, nullptr);
             if (e == cudaSuccess && has_src) e = launch_inject3d(a, t, s3, nshots, st);
         }
         return e;
@@ -1910,13 +1924,6 @@ sim_status adjoint3d(sim_t s, int nshots, const void *wavelet, const double *src
     StepArgs<float> quiet = a;  // recompute: no sampling
     quiet.sample = 0;
     const bool cpml = d.bc == SIM_BC_CPML;
-    const int on[3] = {s->psi[0][0] != nullptr, s->psi[1][0] != nullptr, s->psi[2][0] != nullptr};
-    auto cpml_pass = [&](int n, int phase, float *qslot, cudaStream_t st) {
-        cudaError_t e = cudaSuccess;
-        for (int ax = 0; ax < 3 && e == cudaSuccess; ax++)
-            if (on[ax]) e = launch_cpml3d(a, n, ax, phase, nshots, st, qslot);
-        return e;
-    };
     StepArgs<float> adj = a;
     adj.pbuf[0] = static_cast<float *>(s->ubuf);
     adj.pbuf[1] = static_cast<float *>(s->ubuf) + (long long)ms * g.fstride;
@@ -1934,9 +1941,7 @@ sim_status adjoint3d(sim_t s, int nshots, const void *wavelet, const double *src
                 cudaError_t e2 = cudaSuccess;
                 if (sample) e2 = launch_sample3d(A, step_time(s, A, n, kModeForward, nullptr, nullptr), r3, nrec,
                                                  nshots, st);
-                if (e2 == cudaSuccess && cpml) e2 = cpml_pass(n, 0, nullptr, st);
-                if (e2 == cudaSuccess) e2 = launch_step3d(A, n, zv, zc, nshots, st, true, mode, slot, nullptr);
-                if (e2 == cudaSuccess && cpml) e2 = cpml_pass(n, 1, slot, st);
+                if (e2 == cudaSuccess) e2 = step3d_core(s, A, n, zv, zc, nshots, st, true, mode, slot);
                 if (e2 == cudaSuccess)
                     e2 = launch_inj3d(A, n, n, s->src3g, nsg, s->src3e, 0, nshots, mode, slot, nullptr, st);
                 return e2;

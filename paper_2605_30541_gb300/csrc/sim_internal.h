@@ -235,6 +235,9 @@ struct Tma3 {
     CUtensorMap c;   // c = (v dt / h)^2: 128 x 8 x 1 boxes
 };
 cudaError_t configure_step3d();
+// The TMA march of the forward and record modes takes over the x-strip CPML
+// pass when the widened strips lie inside the first / last x tile.
+bool zmarch_folds_x(const StepArgs<float> &a, int variant, int mode);
 cudaError_t launch_step3d(const StepArgs<float> &a, int n, int variant, int zchunk, int nshots, cudaStream_t st,
                           bool pdl, int mode = kModeForward, float *qs = nullptr, float *Gs = nullptr);
 // 3D point injection grouped by target cell (the adjoint path): group =

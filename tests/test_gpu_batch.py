@@ -1,6 +1,7 @@
 """sim_batch: many shots on uneven grids, as one row-march launch per step over
-all members (the default), one tiled-kernel launch per step ("stepped") or one
-dataflow launch ("persistent"). Results must equal per-handle sim_forward bit
+all members, one tiled-kernel launch per step ("stepped") or one dataflow
+launch ("persistent"); by default the batch autotuner picks between the first
+two by timing. Results must equal per-handle sim_forward bit
 for bit (the row march on both sides; each cell's arithmetic does not depend on
 how the work is split), the two tiled schedules must equal each other bit for
 bit, the march must agree with them to FP32 rounding, and everything must
@@ -22,10 +23,11 @@ torch = pytest.importorskip("torch")
 def march_forward():
     # the bit-for-bit comparisons below are against per-handle forwards on the
     # row march, the kernel of the default batch schedule
-    keys = ("GSIM_RESIDENT", "GSIM_MARCH")
+    keys = ("GSIM_RESIDENT", "GSIM_MARCH", "GSIM_BATCH")
     old = {k: os.environ.get(k) for k in keys}
     os.environ["GSIM_RESIDENT"] = "0"
     os.environ["GSIM_MARCH"] = "1"
+    os.environ["GSIM_BATCH"] = "march"
     yield
     for k, v in old.items():
         if v is None:
@@ -142,5 +144,31 @@ def test_c3_batched_workload_sampled(pkg):
         o = oracle.forward(c, c["vel"].astype(np.float64), c["wavelet"][:600].astype(np.float64),
                            src=c["src"][shot], rec=c["rec"])["gather"]
         assert rel(gb[k][shot, :600].cpu().numpy(), o) <= 1e-4
+    for s in sims:
+        s.close()
+
+
+def test_autotuned_batch_matches_its_schedule_and_oracle(pkg, monkeypatch):
+    # the schedule the batch autotuner picks (march or stepped, with a tile
+    # height) gives the same bits as that schedule forced, and the oracle's
+    # gathers to FP32 tolerance
+    monkeypatch.delenv("GSIM_BATCH", raising=False)
+    monkeypatch.setenv("GSIM_TUNE_LOG", "1")
+    slices = uneven_slices()
+    sims = sims_for(pkg, slices)
+    entries = [dict(sim=s, wavelet=c["wavelet"], src=c["src"], rec=c["rec"]) for s, c in zip(sims, slices)]
+    tuned = [g.clone() for g in pkg.batch(entries)]
+    torch.cuda.synchronize()
+    forced = []
+    for sched, tz in (("march", "16"), ("stepped", "8"), ("stepped", "16"), ("stepped", "32")):
+        monkeypatch.setenv("GSIM_BATCH", sched)
+        monkeypatch.setenv("GSIM_TILE_Z", tz)
+        forced.append([g.clone() for g in pkg.batch(entries)])
+        torch.cuda.synchronize()
+    assert any(all(torch.equal(a, b) for a, b in zip(tuned, f)) for f in forced)
+    for c, g in zip(slices, tuned):
+        o = oracle.forward(c, c["vel"].astype(np.float64), c["wavelet"].astype(np.float64), src=c["src"][0],
+                           rec=c["rec"])["gather"]
+        assert rel(g[0].cpu().numpy(), o) <= 1e-4
     for s in sims:
         s.close()

@@ -168,9 +168,13 @@ def test_device_models_feed_the_batch(pkg):
     src = np.array([[300.0, 10.0], [900.0, 10.0]])
     rec = synth.line(0.0, (nx - 1) * 10.0, 50, 10.0)
     sims = [pkg.Simulator(c, m, max_shots=2, max_rec=len(rec)) for c, m in zip(slices, models)]
-    gb = pkg.batch([dict(sim=s, wavelet=w, src=src, rec=rec) for s in sims])
-    torch.cuda.synchronize()
     import os
+    os.environ["GSIM_BATCH"] = "march"  # the bit-for-bit reference below is the row march
+    try:
+        gb = pkg.batch([dict(sim=s, wavelet=w, src=src, rec=rec) for s in sims])
+        torch.cuda.synchronize()
+    finally:
+        del os.environ["GSIM_BATCH"]
     os.environ["GSIM_MARCH"] = "1"
     os.environ["GSIM_RESIDENT"] = "0"
     try:
