@@ -26,9 +26,8 @@
 //    register window.
 //
 // Segments (member, strip, rows) are claimed by the warps from a per-step
-// counter (16-row items, CPML items first), or come from a static host plan
-// of equal-cost pieces, one per resident warp; segment starts are multiples
-// of 4 rows.
+// counter (16-row items, CPML items first); segment starts are multiples of
+// 4 rows.
 #include <cfloat>
 #include <climits>
 

@@ -1,7 +1,10 @@
 """The two staging variants of the 3D z-march (per-thread cp.async copies,
 and bulk tensor copies by the tensor memory accelerator with mbarrier
-completion), at several z chunks per CTA: gathers and snapshots equal to each
-other bit for bit (the same arithmetic in the same order) and within 1e-4 of
+completion; the latter also takes over the x-strip CPML pass), at several z
+chunks per CTA: within a variant, every chunk gives the same bits; the two
+variants give the same bits where no x strip is folded in (sponge) and agree
+to FP32 rounding where it is (the same expressions, compiled into different
+kernels, may contract their multiply-adds differently); all within 1e-4 of
 the FP64 oracle; the 3D gradient likewise."""
 import numpy as np
 import pytest
@@ -55,17 +58,22 @@ def test_variants_and_chunks_agree_with_oracle(pkg, monkeypatch, bc, fs):
     cfg, vel, w, src, rec = case(bc, fs)
     ref = [oracle.forward(cfg, vel.astype(np.float64), w.astype(np.float64), src=s, rec=rec, snaps=True)
            for s in src]
-    base = None
+    first = {}
     for variant in ("async", "tma"):
         for chunk in (cfg["nz"] + 8, 13, 5):
             g, sn = run(pkg, monkeypatch, variant, chunk, cfg, vel, w, src, rec)
             for k in range(len(src)):
                 assert rel(g[k], ref[k]["gather"]) <= 1e-4, (variant, chunk, k)
                 assert rel(sn[k], ref[k]["snaps"]) <= 1e-4, (variant, chunk, k)
-            if base is None:
-                base = (g, sn)
+            if variant not in first:
+                first[variant] = (g, sn)
             else:
-                assert np.array_equal(g, base[0]) and np.array_equal(sn, base[1]), (variant, chunk)
+                assert np.array_equal(g, first[variant][0]) and np.array_equal(sn, first[variant][1]), (variant, chunk)
+    (ga, sa), (gt, st) = first["async"], first["tma"]
+    if bc == "cpml":
+        assert rel(gt, ga) <= 1e-6 and rel(st, sa) <= 1e-6
+    else:
+        assert np.array_equal(gt, ga) and np.array_equal(st, sa)
 
 
 def test_variants_give_the_same_gradient(pkg, monkeypatch):
@@ -89,5 +97,5 @@ def test_variants_give_the_same_gradient(pkg, monkeypatch):
         sim.sync()
         out.append(grad.cpu().numpy())
         sim.close()
-    assert np.array_equal(out[0], out[1])
-    assert rel(out[1], ref) <= 1e-4
+    assert rel(out[1], out[0]) <= 1e-6  # CPML: the x strips are folded into the TMA march
+    assert rel(out[0], ref) <= 1e-4 and rel(out[1], ref) <= 1e-4
