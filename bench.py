@@ -139,19 +139,21 @@ def gradient_bytes_per_shot(cfg, fp16, qbytes=None, levels=1):
                         strip_cell_axes(cfg) * (16 + extra + 16 + 24))
 
 
-def launches_per_solve(cfg, nsnap, path):
+def launches_per_solve(cfg, nsnap, path, x_folded=False):
     """Kernels of ours one solve launches: on the resident path one launch for
     the whole time loop; else the fused step kernel per step in 2D; in 3D the
     z-march plus, per step, receiver sampling, source injection and one CPML
     pass per absorbing axis (the bench volumes' strips are far apart and far
-    from the free surface), plus snapshot kernels; plus the final
-    finite-value check."""
+    from the free surface; none for x when the TMA march folds the x strips
+    in), plus snapshot kernels; plus the final finite-value check."""
     if path == PATH_RESIDENT:
         return 2
     if cfg["ndim"] == 2:
         return cfg["nt"] + 1
     nb = cfg["nb"]
     axes = sum(1 for a in range(3) if nb[2 * a] + nb[2 * a + 1] > 0) if cfg.get("bc") == "cpml" else 0
+    if x_folded and cfg.get("bc") == "cpml" and nb[4] + nb[5] > 0:
+        axes -= 1
     return cfg["nt"] * (1 + axes + 2) + nsnap + 1
 
 
@@ -575,6 +577,13 @@ def run_ours(args):
             "peak_kind": peak_kind + " (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind,
             "algorithmic_bytes_per_launch": algo, "avg_launch_us": per_launch_s * 1e6,
             "path": {PATH_RESIDENT: "resident", PATH_MARCH: "row march, one launch per step"}.get(path, "per-step")}
+    if cfg["ndim"] == 3:
+        inf = pkg.sim_get_info(sim.handle)
+        roof["z_march"] = {"staging": {1: "cp.async", 2: "TMA, x strips folded in", 3: "TMA"}.get(
+            inf.z_variant, inf.z_variant), "planes_per_cta": inf.z_chunk}
+        if inf.z_variant in (2, 3):
+            roof["kernel"] = "k_step3d_tma"
+            roof["traffic"] = ncu_traffic(kfile, "tma_" + args.workload)
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -624,7 +633,8 @@ def run_ours(args):
                                                         (L2_FLUSH_BYTES >> 20),
                            "parallelism": "replicas x%d" % world},
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(), "e2e": e2e, "gradient": grad,
-                "gpu_launches": args.steps * launches_per_solve(cfg, nsnap, path)}
+                "gpu_launches": args.steps * launches_per_solve(
+                    cfg, nsnap, path, x_folded=cfg["ndim"] == 3 and pkg.sim_get_info(sim.handle).z_variant == 2)}
         print(json.dumps(line), flush=True)
     sim.close()
     if dist:

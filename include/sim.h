@@ -127,6 +127,9 @@ typedef struct {
     int adj_sub;              /* second-level checkpoint slots */
     int pad1;
     size_t adj_bytes;         /* device memory of the gradient's buffers */
+    int z_variant;            /* 3D: z-march the autotuner chose (1 per-thread cp.async staging, 2 TMA
+                                 staging with the x-strip CPML folded in, 3 TMA staging) */
+    int z_chunk;              /* 3D: planes per CTA of the z-march */
 } sim_info;
 
 typedef struct sim_s *sim_t;

@@ -47,7 +47,7 @@ class SimInfo(ctypes.Structure):
         ("tile_z", ctypes.c_int), ("last_path", ctypes.c_int), ("last_rows", ctypes.c_int),
         ("adj_levels", ctypes.c_int), ("adj_slots", ctypes.c_int), ("adj_inner", ctypes.c_int),
         ("adj_top", ctypes.c_int), ("adj_sub", ctypes.c_int), ("pad1", ctypes.c_int),
-        ("adj_bytes", ctypes.c_size_t),
+        ("adj_bytes", ctypes.c_size_t), ("z_variant", ctypes.c_int), ("z_chunk", ctypes.c_int),
     ]
 
 

@@ -389,6 +389,15 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
         q[k] = v;
     }
 
+    // x-strip CPML memory of the next plane, loaded one plane ahead of its use
+    // (the edge tiles would otherwise wait on a DRAM round trip every plane)
+    const bool xlane = xtile && y0 + w < g.NY && xstrip4(g, gx0);
+    float4 psiN = make_float4(0.f, 0.f, 0.f, 0.f), zetaN = psiN;
+    if (xlane) {
+        const long long o = sh + own0 + (long long)zb * PP;
+        psiN = ld4g(A.psi[2][0] + o);
+        zetaN = ld4g(A.zeta[2] + o);
+    }
     bool bad = false;
     for (int zz = zb; zz < ze && !bad; zz += 9) {
 #pragma unroll
@@ -450,8 +459,12 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
                     if (strip) {
                         a4 = ld4g(A.ca[2] + gx0);
                         b4 = ld4g(A.cb[2] + gx0);
-                        old = ld4g(A.psi[2][0] + o);
-                        if (zrow) zo = ld4g(A.zeta[2] + o);
+                        old = psiN;
+                        if (zrow) zo = zetaN;
+                        if (z + 1 < ze) {  // the next plane's, in flight while this one is computed
+                            psiN = ld4g(A.psi[2][0] + o + PP);
+                            zetaN = ld4g(A.zeta[2] + o + PP);
+                        }
                     }
                     float4 ps = zero4;
                     if (strip) {
@@ -1121,7 +1134,7 @@ cudaError_t launch_step3d(const StepArgs<float> &a, int n, int variant, int zchu
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    if (variant == kZMarchTma) {
+    if (variant == kZMarchTma || variant == kZMarchTmaPlain) {
         Tma3 m;
         if (cudaError_t e = make_maps(a, m)) return e;
         cfg.dynamicSmemBytes = kSmemTma;

@@ -882,16 +882,18 @@ cudaError_t step3d_core(const sim_s *s, const StepArgs<float> &a, int n, int var
 // more, shorter ones fill the GPU). The first forward or gradient call for a
 // shot count times a few steps of each candidate on this GPU with CUDA
 // events (on zeroed fields, before the run resets them) and keeps the
-// fastest. GSIM_ZMARCH=async|tma fixes the variant, GSIM_ZCHUNK the chunk;
+// fastest. GSIM_ZMARCH=async|tma|tma-plain fixes the variant, GSIM_ZCHUNK the chunk;
 // GSIM_AUTOTUNE=0 takes the TMA variant with the default chunk untimed.
 sim_status autotune3d(sim_t s, int nshots) {
     if (s->tuned3d == nshots) return SIM_OK;
     s->tuned3d = nshots;
     const int base = zchunk_for(s, nshots), NZ = s->g.NZ;
-    std::vector<int> variants = {kZMarchTma, kZMarchAsync};
+    std::vector<int> variants = {kZMarchTma, kZMarchTmaPlain, kZMarchAsync};
+    if (s->d.bc != SIM_BC_CPML) variants = {kZMarchTma, kZMarchAsync};  // no x strips to fold
     if (const char *f = getenv("GSIM_ZMARCH")) {
         if (!strcmp(f, "async")) variants = {kZMarchAsync};
         if (!strcmp(f, "tma")) variants = {kZMarchTma};
+        if (!strcmp(f, "tma-plain")) variants = {kZMarchTmaPlain};
     }
     s->zvariant = variants[0];
     s->zchunk = base;
@@ -929,7 +931,8 @@ sim_status autotune3d(sim_t s, int nshots) {
             if (e != cudaSuccess) break;
             if (getenv("GSIM_TUNE_LOG"))
                 fprintf(stderr, "[gsim autotune] 3D %dx%dx%d shots %d %s chunk %d: %.1f us/step\n", s->g.NZ, s->g.NY,
-                        s->g.NX, nshots, v == kZMarchTma ? "tma" : "async", zc, 1e3 * ms / timed);
+                        s->g.NX, nshots, v == kZMarchTma ? "tma" : v == kZMarchTmaPlain ? "tma-plain" : "async", zc,
+                        1e3 * ms / timed);
             if (ms < best) {
                 best = ms;
                 s->zvariant = v;
@@ -2833,6 +2836,10 @@ sim_status sim_get_info(sim_t s, sim_info *out) {
     out->vmax = s->vmax;
     out->courant = s->vmax * s->d.dt / s->d.h;
     out->device_bytes = s->bytes;
+    if (s->g.ndim == 3 && s->tuned3d) {
+        out->z_variant = s->zvariant;
+        out->z_chunk = s->zchunk;
+    }
     if (s->adj_ready) {
         out->adj_levels = s->plan.levels;
         out->adj_slots = s->plan.L;

@@ -59,7 +59,7 @@ def test_variants_and_chunks_agree_with_oracle(pkg, monkeypatch, bc, fs):
     ref = [oracle.forward(cfg, vel.astype(np.float64), w.astype(np.float64), src=s, rec=rec, snaps=True)
            for s in src]
     first = {}
-    for variant in ("async", "tma"):
+    for variant in ("async", "tma", "tma-plain"):
         for chunk in (cfg["nz"] + 8, 13, 5):
             g, sn = run(pkg, monkeypatch, variant, chunk, cfg, vel, w, src, rec)
             for k in range(len(src)):
@@ -69,7 +69,8 @@ def test_variants_and_chunks_agree_with_oracle(pkg, monkeypatch, bc, fs):
                 first[variant] = (g, sn)
             else:
                 assert np.array_equal(g, first[variant][0]) and np.array_equal(sn, first[variant][1]), (variant, chunk)
-    (ga, sa), (gt, st) = first["async"], first["tma"]
+    (ga, sa), (gt, st), (gp, sp) = first["async"], first["tma"], first["tma-plain"]
+    assert np.array_equal(gp, ga) and np.array_equal(sp, sa)  # the same passes, the same bits
     if bc == "cpml":
         assert rel(gt, ga) <= 1e-6 and rel(st, sa) <= 1e-6
     else:
