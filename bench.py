@@ -579,9 +579,11 @@ def run_ours(args):
             "path": {PATH_RESIDENT: "resident", PATH_MARCH: "row march, one launch per step"}.get(path, "per-step")}
     if cfg["ndim"] == 3:
         inf = pkg.sim_get_info(sim.handle)
-        roof["z_march"] = {"staging": {1: "cp.async", 2: "TMA, x strips folded in", 3: "TMA"}.get(
+        roof["z_march"] = {"staging": {1: "cp.async", 2: "TMA, x strips folded in", 3: "TMA",
+                                       4: "TMA, plane loop not unrolled",
+                                       5: "TMA, x strips folded in, plane loop not unrolled"}.get(
             inf.z_variant, inf.z_variant), "planes_per_cta": inf.z_chunk}
-        if inf.z_variant in (2, 3):
+        if inf.z_variant in (2, 3, 4, 5):
             roof["kernel"] = "k_step3d_tma"
             roof["traffic"] = ncu_traffic(kfile, "tma_" + args.workload)
 
@@ -634,7 +636,7 @@ def run_ours(args):
                            "parallelism": "replicas x%d" % world},
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(), "e2e": e2e, "gradient": grad,
                 "gpu_launches": args.steps * launches_per_solve(
-                    cfg, nsnap, path, x_folded=cfg["ndim"] == 3 and pkg.sim_get_info(sim.handle).z_variant == 2)}
+                    cfg, nsnap, path, x_folded=cfg["ndim"] == 3 and pkg.sim_get_info(sim.handle).z_variant in (2, 5))}
         print(json.dumps(line), flush=True)
     sim.close()
     if dist:

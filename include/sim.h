@@ -128,7 +128,8 @@ typedef struct {
     int pad1;
     size_t adj_bytes;         /* device memory of the gradient's buffers */
     int z_variant;            /* 3D: z-march the autotuner chose (1 per-thread cp.async staging, 2 TMA
-                                 staging with the x-strip CPML folded in, 3 TMA staging) */
+                                 staging with the x-strip CPML folded in, 3 TMA staging; 4 and 5: 3 and
+                                 2 with the plane loop not unrolled) */
     int z_chunk;              /* 3D: planes per CTA of the z-march */
 } sim_info;
 

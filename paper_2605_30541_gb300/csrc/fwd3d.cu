@@ -308,7 +308,9 @@ __device__ __forceinline__ float4 shfl4w(const float4 v, bool up) {
     return r;
 }
 
-template <int MODE>
+// UN = 9: the plane loop unrolled by the queue's length (the queue rotates by
+// renaming); UN = 1: a plain loop that shifts the queue (smaller code).
+template <int MODE, int UN>
 __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, const __grid_constant__ Tma3 M,
                                                        const int n, const int zchunk, const int ms, const XFuse X,
                                                        float *qs, float *Gs, const long long spin) {
@@ -399,9 +401,9 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
         zetaN = ld4g(A.zeta[2] + o);
     }
     bool bad = false;
-    for (int zz = zb; zz < ze && !bad; zz += 9) {
+    for (int zz = zb; zz < ze && !bad; zz += UN) {
 #pragma unroll
-        for (int j = 0; j < 9; j++) {
+        for (int j = 0; j < UN; j++) {
             const int z = zz + j;
             if (z >= ze || bad) break;
             if (tid == 0) stage(z + NST - 1);
@@ -507,6 +509,10 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
                         *reinterpret_cast<float4 *>(Gs + sh + o) = g4;
                     }
                 }
+            }
+            if (UN == 1) {
+#pragma unroll
+                for (int k = 0; k < 8; k++) q[k] = q[k + 1];
             }
             // every thread is done with slot kz before it is restaged; a wait
             // that gave up anywhere ends the march for the whole block
@@ -1054,7 +1060,8 @@ bool x_row_pass(const Geom &g, XEnds *E) {
 XFuse x_fuse(const StepArgs<float> &a, int variant, int mode) {
     XFuse X{0, 0, 1 << 30, 0};
     const Geom &g = a.g;
-    if (variant != kZMarchTma || mode == kModeAdjoint || a.bc != SIM_BC_CPML || !a.ca[2] || !x_row_pass(g, nullptr))
+    if ((variant != kZMarchTma && variant != kZMarchTmaFoldLoop) || mode == kModeAdjoint || a.bc != SIM_BC_CPML ||
+        !a.ca[2] || !x_row_pass(g, nullptr))
         return X;
     X.lqb = g.nbx0 > 0 ? std::min(g.NX, g.nbx0 + 4) : 0;
     X.rqa = g.nbx1 > 0 ? std::max(0, g.NX - g.nbx1 - 4) : (1 << 30);
@@ -1101,7 +1108,8 @@ cudaError_t make_maps(const StepArgs<float> &a, Tma3 &m) {
 
 cudaError_t configure_step3d() {
     cudaError_t e = cudaSuccess;
-    for (auto k : {k_step3d_tma<kModeForward>, k_step3d_tma<kModeRecord>, k_step3d_tma<kModeAdjoint>})
+    for (auto k : {k_step3d_tma<kModeForward, 9>, k_step3d_tma<kModeRecord, 9>, k_step3d_tma<kModeAdjoint, 9>,
+                   k_step3d_tma<kModeForward, 1>, k_step3d_tma<kModeRecord, 1>, k_step3d_tma<kModeAdjoint, 1>})
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTma);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_step3d<1, kModeForward>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1134,18 +1142,25 @@ cudaError_t launch_step3d(const StepArgs<float> &a, int n, int variant, int zchu
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    if (variant == kZMarchTma || variant == kZMarchTmaPlain) {
+    if (variant >= kZMarchTma && variant <= kZMarchTmaFoldLoop) {
         Tma3 m;
         if (cudaError_t e = make_maps(a, m)) return e;
         cfg.dynamicSmemBytes = kSmemTma;
         const int ms = (int)((a.pbuf[1] - a.pbuf[0]) / a.g.fstride);
         const long long spin = 1LL << 22;
         const XFuse X = x_fuse(a, variant, mode);
+        if (variant == kZMarchTmaLoop || variant == kZMarchTmaFoldLoop) {
+            if (mode == kModeRecord)
+                return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeRecord, 1>, a, m, n, zchunk, ms, X, qs, Gs, spin);
+            if (mode == kModeAdjoint)
+                return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeAdjoint, 1>, a, m, n, zchunk, ms, X, qs, Gs, spin);
+            return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeForward, 1>, a, m, n, zchunk, ms, X, qs, Gs, spin);
+        }
         if (mode == kModeRecord)
-            return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeRecord>, a, m, n, zchunk, ms, X, qs, Gs, spin);
+            return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeRecord, 9>, a, m, n, zchunk, ms, X, qs, Gs, spin);
         if (mode == kModeAdjoint)
-            return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeAdjoint>, a, m, n, zchunk, ms, X, qs, Gs, spin);
-        return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeForward>, a, m, n, zchunk, ms, X, qs, Gs, spin);
+            return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeAdjoint, 9>, a, m, n, zchunk, ms, X, qs, Gs, spin);
+        return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeForward, 9>, a, m, n, zchunk, ms, X, qs, Gs, spin);
     }
     if (variant != kZMarchAsync) return cudaErrorInvalidValue;
     if (mode == kModeRecord) return launch_step3d_mode<1, kModeRecord>(cfg, a, n, zchunk, qs, Gs);

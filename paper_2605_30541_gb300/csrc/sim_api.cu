@@ -882,19 +882,19 @@ cudaError_t step3d_core(const sim_s *s, const StepArgs<float> &a, int n, int var
 // more, shorter ones fill the GPU). The first forward or gradient call for a
 // shot count times a few steps of each candidate on this GPU with CUDA
 // events (on zeroed fields, before the run resets them) and keeps the
-// fastest. GSIM_ZMARCH=async|tma|tma-plain fixes the variant, GSIM_ZCHUNK the chunk;
+// fastest. GSIM_ZMARCH=async|tma|tma-plain|tma-loop|tma-loop-fold fixes the
+// variant, GSIM_ZCHUNK the chunk;
 // GSIM_AUTOTUNE=0 takes the TMA variant with the default chunk untimed.
 sim_status autotune3d(sim_t s, int nshots) {
     if (s->tuned3d == nshots) return SIM_OK;
     s->tuned3d = nshots;
     const int base = zchunk_for(s, nshots), NZ = s->g.NZ;
-    std::vector<int> variants = {kZMarchTma, kZMarchTmaPlain, kZMarchAsync};
-    if (s->d.bc != SIM_BC_CPML) variants = {kZMarchTma, kZMarchAsync};  // no x strips to fold
-    if (const char *f = getenv("GSIM_ZMARCH")) {
-        if (!strcmp(f, "async")) variants = {kZMarchAsync};
-        if (!strcmp(f, "tma")) variants = {kZMarchTma};
-        if (!strcmp(f, "tma-plain")) variants = {kZMarchTmaPlain};
-    }
+    std::vector<int> variants = {kZMarchTmaPlain, kZMarchTmaLoop, kZMarchTma, kZMarchTmaFoldLoop, kZMarchAsync};
+    if (s->d.bc != SIM_BC_CPML) variants = {kZMarchTmaPlain, kZMarchTmaLoop, kZMarchAsync};  // no x strips to fold
+    static const char *const names[6] = {"", "async", "tma", "tma-plain", "tma-loop", "tma-loop-fold"};
+    if (const char *f = getenv("GSIM_ZMARCH"))
+        for (int v = 1; v <= 5; v++)
+            if (!strcmp(f, names[v])) variants = {v};
     s->zvariant = variants[0];
     s->zchunk = base;
     const char *at = getenv("GSIM_AUTOTUNE");
@@ -931,8 +931,7 @@ sim_status autotune3d(sim_t s, int nshots) {
             if (e != cudaSuccess) break;
             if (getenv("GSIM_TUNE_LOG"))
                 fprintf(stderr, "[gsim autotune] 3D %dx%dx%d shots %d %s chunk %d: %.1f us/step\n", s->g.NZ, s->g.NY,
-                        s->g.NX, nshots, v == kZMarchTma ? "tma" : v == kZMarchTmaPlain ? "tma-plain" : "async", zc,
-                        1e3 * ms / timed);
+                        s->g.NX, nshots, names[v], zc, 1e3 * ms / timed);
             if (ms < best) {
                 best = ms;
                 s->zvariant = v;
