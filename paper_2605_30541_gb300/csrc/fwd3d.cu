@@ -356,9 +356,8 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
     cudaGridDependencySynchronize();
 
     int zlast = zb - 1;        // last plane staged (thread 0)
-    auto stage = [&](int z) {  // thread 0 only
+    auto stage = [&](int z, int k) {  // thread 0 only; k = (z - zb) % NST
         zlast = z;
-        const int k = (z - zb) % NST;
         unsigned char *dst = ring + k * SLOT_T;
         const bool own = z < ze;
         mbar_expect(full + k, HALO_T + (own ? 2 * OWN_T : 0));
@@ -369,7 +368,7 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
         }
     };
     if (tid == 0)
-        for (int k = 0; k < NST - 1; k++) stage(zb + k);
+        for (int k = 0; k < NST - 1; k++) stage(zb + k, k);
 
     // register queue of this thread's cells: plane z + m lives in q[(j + m + 4) % 9]
     // at unrolled step j of a block of 9 planes
@@ -401,15 +400,17 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
         zetaN = ld4g(A.zeta[2] + o);
     }
     bool bad = false;
+    // ring slots and barrier phases of planes z and z + 4, advanced per plane
+    int kz = 0, pz = 0, k4 = 4 % NST, p4 = 4 / NST;
+    long long orow = own0 + (long long)zb * PP;  // this thread's float4 of plane z
     for (int zz = zb; zz < ze && !bad; zz += UN) {
 #pragma unroll
         for (int j = 0; j < UN; j++) {
             const int z = zz + j;
             if (z >= ze || bad) break;
-            if (tid == 0) stage(z + NST - 1);
-            const int kz = (z - zb) % NST, k4 = (z + 4 - zb) % NST;
-            bool ok = mbar_wait(full + kz, ((z - zb) / NST) & 1, spin);
-            ok = ok && mbar_wait(full + k4, ((z + 4 - zb) / NST) & 1, spin);
+            if (tid == 0) stage(z + NST - 1, kz == 0 ? NST - 1 : kz - 1);
+            bool ok = mbar_wait(full + kz, pz, spin);
+            ok = ok && mbar_wait(full + k4, p4, spin);
             ok = __all_sync(0xffffffffu, ok);  // the warp computes (and shuffles) together or not at all
             if (ok) {
                 const float *cur = reinterpret_cast<const float *>(ring + kz * SLOT_T);
@@ -453,7 +454,7 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
                 }
                 if (xtile) {  // x-strip CPML of the row, as k_cpml_row3d computes it after the update
                     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                    const long long o = sh + own0 + (long long)z * PP;
+                    const long long o = sh + orow;
                     const bool strip = gy < g.NY && xstrip4(g, gx0);
                     const bool inw = gy < g.NY && gx0 < g.NX && (gx0 < X.lqb || gx0 + 3 >= X.rqa);
                     const bool zrow = !(g.fs && z == 0);  // the free-surface row stays zero
@@ -495,7 +496,7 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
                 }
                 if (g.fs && z == 0) res[0] = res[1] = res[2] = res[3] = 0.f;
                 if (gy < g.NY) {
-                    const long long o = own0 + (long long)z * PP;
+                    const long long o = orow;
                     *reinterpret_cast<float4 *>(pn + o) = make_float4(res[0], res[1], res[2], res[3]);
                     if (MODE == kModeRecord)
                         *reinterpret_cast<float4 *>(qs + sh + o) = make_float4(qk[0], qk[1], qk[2], qk[3]);
@@ -514,6 +515,9 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
 #pragma unroll
                 for (int k = 0; k < 8; k++) q[k] = q[k + 1];
             }
+            orow += PP;
+            if (++kz == NST) kz = 0, pz ^= 1;
+            if (++k4 == NST) k4 = 0, p4 ^= 1;
             // every thread is done with slot kz before it is restaged; a wait
             // that gave up anywhere ends the march for the whole block
             bad = __syncthreads_or(!ok) != 0;
