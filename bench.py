@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c5", choices=["c2", "c2x32", "c3", "c5", "c5s", "c6g", "c6w", "model"])
+    ap.add_argument("--workload", default="c5", choices=["c2", "c2x32", "c3", "c4g", "c5", "c5s", "c6g", "c6w", "model"])
     ap.add_argument("--nt", type=int, default=0, help="override nt (profiling runs only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -779,6 +779,59 @@ def run_model(args):
     print(json.dumps(line), flush=True)
 
 
+def run_gradient(args):
+    """The FWI gradient workload alone (201 x 201 procedural model + 20-cell
+    CPML on every side, 16 shots, nt = 4000): one sim_adjoint of all shots
+    with FP16 checkpoints per step; value = padded cells x shots x steps of
+    the forward problem per second of gradient (the profiling command of the
+    adjoint-state kernels)."""
+    import torch
+    import synth
+    import paper_2605_30541_gb300 as pkg
+    torch.cuda.set_device(0)
+    c = synth.config_c4()
+    ns, nt, nrec = len(c["src"]), c["nt"], len(c["rec"])
+    true = pkg.Simulator(c, c["vel_true"], max_shots=ns, max_rec=nrec)
+    d = true.forward(c["wavelet"], c["src"], c["rec"])["gather"].contiguous()
+    true.close()
+    sim = pkg.Simulator(c, c["vel"], max_shots=ns, max_rec=nrec)
+    w = torch.as_tensor(c["wavelet"], device="cuda")
+    src, rec = np.ascontiguousarray(c["src"]), np.ascontiguousarray(c["rec"])
+    g = torch.zeros(c["vel"].shape, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        pkg.sim_adjoint(sim.handle, ns, w, src, nrec, rec, d, None, None, 1, g)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    per = e0.elapsed_time(e1) / 1e3 / args.steps
+    cells = padded_cells(c) * ns
+    peak, peak_kind = read_peaks()
+    algo = gradient_bytes_per_shot(c, True) * ns
+    line = {"metric": "Gcell-updates/s of the gradient (FP16 checkpoints)", "value": cells * nt / per / 1e9,
+            "unit": "Gcell/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f16 storage)",
+            "data": "synthetic",
+            "config": {"workload": "c4g: gradient, 201x201 + 20-cell CPML on every side, 16 shots, nt=4000, "
+                                   "FP16 checkpoints", "s_per_shot": per / ns, "l2": "not flushed (a whole "
+                                   "gradient per step)"},
+            "roofline": {"bound": "hbm", "achieved": algo / per / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": algo / per / 1e9 / peak, "peak_kind": peak_kind, "traffic": None,
+                         "algorithmic_bytes_per_step": algo},
+            "cpu_baseline": None, "clocks": clk.summary(), "gpu_launches": None}
+    print(json.dumps(line), flush=True)
+    sim.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -787,6 +840,8 @@ def main():
         run_model(args)
     elif args.workload in ("c3", "c6g"):
         run_batch(args)
+    elif args.workload == "c4g":
+        run_gradient(args)
     else:
         run_ours(args)
 
