@@ -11,7 +11,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsim.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["sim_api.cu", "setup.cu", "fwd2d.cu", "fwd2d_f32.cu", "fwd3d.cu", "adjoint.cu", "noalloc.cu", "resident2d.cu", "wavelet.cu", "march2d.cu", "model.cu", "cpml_adj.cu"]
+SOURCES = ["sim_api.cu", "setup.cu", "fwd2d.cu", "fwd2d_f32.cu", "fwd3d.cu", "adjoint.cu", "noalloc.cu", "resident2d.cu", "wavelet.cu", "march2d.cu", "march2x.cu", "model.cu", "cpml_adj.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE]

@@ -283,6 +283,7 @@ struct sim_s {
     int last_path = 0, last_rows = 0;      // see sim_info
     int zchunk = 0;                        // z-march chunk of the 3D kernel (planes per CTA)
     int zvariant = kZMarchTma;             // z-march staging (cp.async or TMA), see autotune3d
+    void *pbuf3 = nullptr;                 // two-step row march: third and fourth pressure fields (max_shots shots each)
     int tuned3d = 0;                       // shot count the 3D launch shape was tuned for
     // adjoint-state buffers, allocated by the first sim_adjoint call (on
     // their own list: a call that needs a larger plan frees and re-plans them)
@@ -2155,6 +2156,8 @@ struct BatchCtx {
     void *msegs = nullptr;  // row march items
     size_t cap_msegs = 0;
     unsigned *mctr = nullptr;                  // row march: per-step item counters
+    void *tbm = nullptr, *tbs = nullptr;       // two-step march: members, receiver samples
+    size_t cap_tbm = 0, cap_tbs = 0;
     cudaGraphExec_t exec = nullptr;
     std::vector<char> key;
     cudaEvent_t ev = nullptr;
@@ -2175,7 +2178,7 @@ cudaError_t grow(void **p, size_t *cap, size_t need) {
 // Batch schedules: the row march (one launch per step over every member),
 // the stepped tile kernel (one launch per step) and the persistent dataflow
 // kernel (one launch for all steps).
-enum { kBatchMarch = 0, kBatchStepped = 1, kBatchPersistent = 2 };
+enum { kBatchMarch = 0, kBatchStepped = 1, kBatchPersistent = 2, kBatchMarch2 = 3 };
 
 // One batch run with a given schedule and list tile height. probe > 0: run
 // only that many steps, launched directly (the autotuner's timing probe; no
@@ -2204,8 +2207,9 @@ sim_status batch_run(int nitems, const sim_batch_item *items, cudaStream_t bst, 
     const int nt = s0->d.nt;
     const int nsteps = probe > 0 ? std::min(probe, nt) : nt;
     const bool persistent = sched == kBatchPersistent;
+    const bool march2 = sched == kBatchMarch2;
     const bool march = sched == kBatchMarch;
-    const bool stepped = !persistent;
+    const bool stepped = !persistent && !march2;
     const int tz = tz_in;
     bool any_cpml = false;
     std::vector<StepArgs<float>> slices(nitems);
@@ -2216,6 +2220,18 @@ sim_status batch_run(int nitems, const sim_batch_item *items, cudaStream_t bst, 
         const sim_batch_item &it = items[i];
         set_tile_z(s, tz);
         any_cpml |= s->d.bc == SIM_BC_CPML;
+        if (march2) {  // the two-step march: no CPML; two more pressure fields per handle
+            if (s->d.bc == SIM_BC_CPML)
+                return thread_fail(SIM_ERR_UNSUPPORTED, "batch item %d: the two-step march takes no CPML", i);
+            if (!s->pbuf3) {
+                const size_t fb = 2 * (size_t)s->d.max_shots * s->g.fstride * sizeof(float);
+                sim_status rc = SIM_OK;
+                void *p3 = s->alloc(fb, &rc);
+                if (rc != SIM_OK) return rc;
+                if (sim_status r = s->cuda(cudaMemsetAsync(p3, 0, fb, s->st), "clear")) return r;
+                s->pbuf3 = p3;
+            }
+        }
         const void *wav = it.wavelet;
         if (!is_device_ptr(wav)) {
             if (sim_status r = s->cuda(cudaMemcpyAsync(s->wave, wav, (size_t)nt * sizeof(float),
@@ -2360,6 +2376,82 @@ sim_status batch_run(int nitems, const sim_batch_item *items, cudaStream_t bst, 
         mb.nitems = (int)segs.size();
         mb.tz = tz;
     }
+    int tb_nwarps = 0;
+    TBArgs tb{};
+    if (march2) {  // members, receiver samples and items of the two-step march
+        std::vector<TBMember> tm;
+        std::vector<TBSample> ts;
+        std::vector<MarchSeg> segs;
+        int rows = 32;
+        if (const char *f = getenv("GSIM_TB_ROWS")) rows = std::max(1, atoi(f));
+        for (size_t mi = 0; mi < members.size(); mi++) {
+            const BatchMember &m = members[mi];
+            const sim_batch_item &it = items[m.slice];
+            sim_s *s = it.sim;
+            const Geom &g = s->g;
+            TBMember M{};
+            M.slice = m.slice;
+            M.shot = m.shot;
+            M.p3 = static_cast<float *>(s->pbuf3);
+            M.pstride = (long long)s->d.max_shots * g.fstride;
+            int i0[3];
+            double t[3];
+            if (!locate(g, s->d.h, it.src_pos + (size_t)m.shot * 2, i0, t))
+                return thread_fail(SIM_ERR_ARG, "batch item %d: source %d lies outside the interior", m.slice, m.shot);
+            for (int dz = 0; dz < 2; dz++)
+                for (int dx = 0; dx < 2; dx++) {  // the corners the one-step injection lists hold
+                    const double w = corner_weight(t, dz, 0, dx);
+                    const int z = i0[0] + dz, x = i0[2] + dx;
+                    if (w == 0.0 || (g.fs && z == 0)) continue;
+                    M.sz[M.nsrc] = z;
+                    M.sx[M.nsrc] = x;
+                    M.sw[M.nsrc] = (float)w;
+                    M.nsrc++;
+                }
+            tm.push_back(M);
+            if (gdev[m.slice] && it.nrec > 0)
+                for (int r = 0; r < it.nrec; r++) {
+                    if (!locate(g, s->d.h, it.rec_pos + (size_t)r * 2, i0, t))
+                        return thread_fail(SIM_ERR_ARG, "batch item %d: receiver %d lies outside the interior", m.slice,
+                                           r);
+                    TBSample Q{};
+                    Q.member = (int)mi;
+                    Q.rec = r;
+                    Q.z = i0[0];
+                    Q.x = i0[2];
+                    int k = 0;
+                    for (int dz = 0; dz < 2; dz++)
+                        for (int dx = 0; dx < 2; dx++) Q.w[k++] = (float)corner_weight(t, dz, 0, dx);
+                    ts.push_back(Q);
+                }
+            const int nstrip = (g.NX + kTBW - 1) / kTBW;
+            for (int zc = 0; zc < g.NZ; zc += rows)
+                for (int bx = 0; bx < nstrip; bx++)
+                    segs.push_back(MarchSeg{(int)mi, m.shot, bx, zc, std::min(g.NZ, zc + rows), {0, 0, 0}});
+        }
+        if (!ctx->mctr && (e = cudaMalloc(&ctx->mctr, 2 * sizeof(unsigned)))) return fail(e, "allocation");
+        if ((e = grow(&ctx->msegs, &ctx->cap_msegs, segs.size() * sizeof(MarchSeg))) ||
+            (e = grow(&ctx->tbm, &ctx->cap_tbm, tm.size() * sizeof(TBMember))) ||
+            (e = grow(&ctx->tbs, &ctx->cap_tbs, std::max<size_t>(1, ts.size()) * sizeof(TBSample)))) {
+            if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+            ctx->exec = nullptr;
+            return fail(e, "allocation");
+        }
+        if ((e = cudaMemcpyAsync(ctx->msegs, segs.data(), segs.size() * sizeof(MarchSeg), cudaMemcpyHostToDevice,
+                                 bst)) ||
+            (e = cudaMemcpyAsync(ctx->tbm, tm.data(), tm.size() * sizeof(TBMember), cudaMemcpyHostToDevice, bst)) ||
+            (!ts.empty() &&
+             (e = cudaMemcpyAsync(ctx->tbs, ts.data(), ts.size() * sizeof(TBSample), cudaMemcpyHostToDevice, bst))))
+            return fail(e, "upload");
+        tb.slices = static_cast<const StepArgs<float> *>(ctx->slices);
+        tb.members = static_cast<const TBMember *>(ctx->tbm);
+        tb.segs = static_cast<const MarchSeg *>(ctx->msegs);
+        tb.samples = static_cast<const TBSample *>(ctx->tbs);
+        tb.ctr = ctx->mctr;
+        tb.nitems = (int)segs.size();
+        tb.nsamples = (long long)ts.size();
+        tb_nwarps = (int)std::min<long long>((long long)sms * std::max(1, march2x_warps_per_sm()), tb.nitems);
+    }
     if (stepped) {  // members with global tile offsets
         long long t0 = 0;
         for (BatchMember &m : members) {
@@ -2383,17 +2475,35 @@ sim_status batch_run(int nitems, const sim_batch_item *items, cudaStream_t bst, 
     b.flags = ctx->flags;
     const int grid = sms * std::max(1, batch_blocks_per_sm(tz, any_cpml));
     // counters reset + the persistent kernel, replayed as one graph
-    std::vector<char> key(sizeof b + sizeof mb + 3 * sizeof(int) + sizeof(long long));
-    memcpy(key.data(), &b, sizeof b);
-    memcpy(key.data() + sizeof b, &mb, sizeof mb);
-    const int kk[3] = {tz, (int)any_cpml | (stepped ? 2 : 0) | (march ? 4 : 0), grid};
-    memcpy(key.data() + sizeof b + sizeof mb, kk, sizeof kk);
-    memcpy(key.data() + sizeof b + sizeof mb + sizeof kk, &done_total, sizeof done_total);
+    const int kk[4] = {tz, (int)any_cpml | (stepped ? 2 : 0) | (march ? 4 : 0) | (march2 ? 8 : 0), grid, tb_nwarps};
+    std::vector<char> key(sizeof b + sizeof mb + sizeof tb + sizeof kk + sizeof done_total);
+    {
+        char *k = key.data();
+        memcpy(k, &b, sizeof b);
+        memcpy(k += sizeof b, &mb, sizeof mb);
+        memcpy(k += sizeof mb, &tb, sizeof tb);
+        memcpy(k += sizeof tb, kk, sizeof kk);
+        memcpy(k + sizeof kk, &done_total, sizeof done_total);
+    }
     if (!ctx->exec || key != ctx->key || bst == nullptr) {
         if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
         ctx->exec = nullptr;
     }
     auto body = [&](cudaStream_t st) {
+        if (march2) {  // passes of two steps (the last of one step when the count is odd)
+            cudaError_t r = cudaMemsetAsync(ctx->flags, 0, sizeof(unsigned), st);
+            if (r == cudaSuccess) r = cudaMemsetAsync(tb.ctr, 0, 2 * sizeof(unsigned), st);
+            for (int k = 0; 2 * k < nsteps && r == cudaSuccess; k++) {
+                TBPass t{};
+                t.k = k;
+                t.n = 2 * k;
+                t.two = t.n + 1 < nsteps;
+                t.inj0 = t.n;
+                t.inj1 = t.two ? t.n + 1 : -1;
+                r = launch_march2x(tb, t, tb_nwarps, st);
+            }
+            return r;
+        }
         if (march) {
             cudaError_t r = cudaMemsetAsync(ctx->flags, 0, sizeof(unsigned), st);
             if (r == cudaSuccess && mb.ctr) r = cudaMemsetAsync(mb.ctr, 0, 2 * sizeof(unsigned), st);
@@ -2465,13 +2575,14 @@ sim_status batch_run(int nitems, const sim_batch_item *items, cudaStream_t bst, 
     return SIM_OK;
 }
 
-// Batch autotuner: the schedule (row march, or the stepped kernel with list
-// tiles of 8, 16 or 32 rows) of a batch shape (every item's grid, boundary,
+// Batch autotuner: the schedule (row march, the two-step row march when no
+// item has CPML, or the stepped kernel with list tiles of 8, 16 or 32 rows)
+// of a batch shape (every item's grid, boundary,
 // shot count, receivers; nt) is picked on its first call by timing a short
 // probe of each candidate with CUDA events on the batch stream, and cached
 // for the process. The persistent kernel (slower wherever measured: every
 // item pays a counter, an acquire wait and a release) runs only when forced:
-// GSIM_BATCH=march|stepped|persistent fixes the schedule, GSIM_TILE_Z the
+// GSIM_BATCH=march|march2|stepped|persistent fixes the schedule, GSIM_TILE_Z the
 // tile height, GSIM_AUTOTUNE=0 takes the row march untimed.
 std::mutex g_btune_mu;
 std::map<std::vector<long long>, std::pair<int, int>> g_btune;
@@ -2483,6 +2594,7 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
         if (!strcmp(bm, "persistent")) sched = kBatchPersistent;
         else if (!strcmp(bm, "stepped")) sched = kBatchStepped;
         else if (!strcmp(bm, "march")) sched = kBatchMarch;
+        else if (!strcmp(bm, "march2")) sched = kBatchMarch2;
     }
     if (const char *f = getenv("GSIM_TILE_Z")) {
         const int v = atoi(f);
@@ -2509,6 +2621,9 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
     std::vector<std::pair<int, int>> cand;
     if (tz) cand = {{kBatchMarch, tz}, {kBatchStepped, tz}};
     else cand = {{kBatchMarch, 16}, {kBatchStepped, 8}, {kBatchStepped, 16}, {kBatchStepped, 32}};
+    bool cpml = false;
+    for (int i = 0; i < nitems; i++) cpml |= items[i].sim->d.bc == SIM_BC_CPML;
+    if (!cpml) cand.push_back({kBatchMarch2, tz ? tz : 16});  // two steps per pass
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
@@ -2531,7 +2646,8 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
         }
         if (getenv("GSIM_TUNE_LOG"))
             fprintf(stderr, "[gsim autotune] batch of %d items: %s tile %d: %.1f us/step (probe)\n", nitems,
-                    c.first == kBatchMarch ? "march" : "stepped", c.second, 1e3 * ms / steps);
+                    c.first == kBatchMarch ? "march" : c.first == kBatchMarch2 ? "two-step march" : "stepped",
+                    c.second, 1e3 * ms / steps);
         if (ms < best) best = ms, pick = c;
     }
     cudaEventDestroy(e0);
@@ -2704,6 +2820,7 @@ sim_status sim_create(const sim_desc *din, const void *vel, void *cuda_stream, s
     if (rc == SIM_OK && d.precision == SIM_FP32 && d.ndim == 2) {
         rc = s->cuda(configure_resident2d(), "kernel configuration");
         if (rc == SIM_OK) rc = s->cuda(configure_march2d(), "kernel configuration");
+        if (rc == SIM_OK) rc = s->cuda(configure_march2x(), "kernel configuration");
         s->rdone = static_cast<int *>(A(sizeof(int) * ms * max_tiles(s)));
         s->rtiles = static_cast<RTile *>(A(sizeof(RTile) * max_tiles(s)));
         // row march: one item per (shot, strip, 4 rows) at most

@@ -222,6 +222,47 @@ cudaError_t configure_march2d();
 int march2d_warps_per_sm(bool cpml);
 cudaError_t launch_march2d(const MarchArgs &m, bool cpml, const StepTime &t, cudaStream_t st, bool pdl);
 
+// Temporal blocking of the row march (march2x.cu): two steps per pass for
+// members without CPML. A member (slice, shot) has two more pressure fields
+// (p3 and p3 + pstride: the four fields alternate as two pairs over the
+// passes) and up to four source corners; items are MarchSeg over 120-column
+// strips (slice = member index). Receivers are TBSample entries sampled
+// after each pass.
+constexpr int kTBW = 120;
+struct TBMember {
+    int slice, shot;
+    float *p3;             // third and fourth pressure fields of the slice (per shot: + shot * fstride)
+    long long pstride;     // from the third field to the fourth
+    int nsrc, pad;
+    int sz[4], sx[4];      // source corners: computational-grid row and column
+    float sw[4];           // bilinear weights
+};
+struct TBSample {
+    int member, rec;
+    int z, x;              // base cell (computational grid) of the 2 x 2 corners
+    float w[4];            // corner weights (z, x), (z, x+1), (z+1, x), (z+1, x+1)
+};
+struct TBArgs {
+    const StepArgs<float> *slices;
+    const TBMember *members;
+    const MarchSeg *segs;
+    const TBSample *samples;
+    unsigned *ctr;         // two per-pass item counters
+    int nitems;
+    int pad;
+    long long nsamples;
+};
+struct TBPass {
+    int k;                 // pass index: even passes read fields 0, 1, odd passes fields 2, 3
+    int n;                 // first step of the pass
+    int two;               // 1: steps n and n + 1; 0: step n only
+    int inj0, inj1;        // wavelet rows injected at the two steps (-1: none)
+    int pad;
+};
+cudaError_t configure_march2x();
+int march2x_warps_per_sm();
+cudaError_t launch_march2x(const TBArgs &b, const TBPass &t, int nwarps, cudaStream_t st);
+
 // 3D launchers (fwd3d.cu). Per step: snapshot, sample, CPML psi, z-march
 // update, CPML zeta + addend, source injection.
 // z-march variants: kZMarchAsync stages each plane by per-thread 16-byte
