@@ -107,6 +107,16 @@ def algorithmic_bytes_per_launch(cfg, nshots):
     return nshots * (16 * cells + 16 * strip + rec + snap)
 
 
+def algorithmic_bytes_two_step(cfg, nshots, nt):
+    """Bytes the two-step row march must move at minimum over nt steps: 20 B
+    per cell and pass of two steps (read p^n, p^{n-1}, c; write p^{n+1},
+    p^{n+2}), 16 B per cell in the last pass when nt is odd (one step), 4 B
+    per receiver sample. Only batches without CPML or snapshots take it."""
+    nb = cfg["nb"]
+    cells = (nb[0] + cfg["nz"] + nb[1]) * (nb[4] + cfg["nx"] + nb[5])
+    return nshots * (cells * (10 * (nt - nt % 2) + 16 * (nt % 2)) + 4 * len(cfg["rec"]) * nt)
+
+
 def strip_cell_axes(cfg):
     """CPML strip cells counted once per absorbing axis whose strip holds them."""
     if cfg.get("bc") != "cpml":
@@ -367,10 +377,15 @@ def run_batch(args):
     total = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     value = args.steps * nt * cells / total / 1e9
     peak, peak_kind = read_peaks()
-    algo = sum(algorithmic_bytes_per_launch(c, len(c["src"])) for c in slices) * nt
-    sched = os.environ.get("GSIM_BATCH", "march")
+    inf = pkg.sim_get_info(sims[0].handle)
+    sched = {1: "march", 2: "march2", 3: "stepped", 4: "persistent"}.get(inf.batch_sched, "march")
+    if sched == "march2":
+        algo = sum(algorithmic_bytes_two_step(c, len(c["src"]), nt) for c in slices)
+    else:
+        algo = sum(algorithmic_bytes_per_launch(c, len(c["src"])) for c in slices) * nt
     kfile, kname, kkey = (("fwd2d_f32.cu", "k_multi2d", "multi_") if sched == "stepped" else
                           ("fwd2d_f32.cu", "k_batch2d", "batch_") if sched == "persistent" else
+                          ("march2x.cu", "k_march2x", "march2_") if sched == "march2" else
                           ("march2d.cu", "k_march2d", "march_"))
     line = {"metric": METRIC, "value": value, "unit": "Gcell/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
@@ -381,6 +396,7 @@ def run_batch(args):
                                    ("c3: 64 shots on a 619x1000 slice + 16 uneven slices x 8 shots, nt=%d, "
                                     "one launch per step over all slices and shots (%s batch)" % (nt, sched)),
                        "seconds_per_slice_band": total / args.steps if args.workload == "c6g" else None,
+                       "batch_schedule": sched + ("" if sched in ("march", "march2") else " tile %d" % inf.batch_tile),
                        "padded_cells_x_shots": cells,
                        "l2": "flushed between timed solves"},
             "roofline": {"bound": "hbm", "achieved": algo / (total / args.steps) / 1e9, "peak": peak,
@@ -388,7 +404,8 @@ def run_batch(args):
                          "traffic": ncu_traffic(kfile, kkey + args.workload), "traffic_per": "step launch",
                          "kernel": kname, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_solve": algo},
-            "clocks": clk.summary(), "gpu_launches": args.steps * nt}
+            "clocks": clk.summary(),
+            "gpu_launches": args.steps * (2 * ((nt + 1) // 2) if sched == "march2" else nt)}
     print(json.dumps(line), flush=True)
     for s in sims:
         s.close()

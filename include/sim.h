@@ -131,6 +131,10 @@ typedef struct {
                                  staging with the x-strip CPML folded in, 3 TMA staging; 4 and 5: 3 and
                                  2 with the plane loop not unrolled) */
     int z_chunk;              /* 3D: planes per CTA of the z-march */
+    int batch_sched;          /* schedule of the last sim_batch forward this handle took part in
+                                 (0 none yet, 1 row march, 2 two-step row march, 3 stepped tiles,
+                                 4 persistent tiles) */
+    int batch_tile;           /* its tile height (stepped and persistent schedules) */
 } sim_info;
 
 typedef struct sim_s *sim_t;

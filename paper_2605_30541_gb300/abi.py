@@ -48,6 +48,7 @@ class SimInfo(ctypes.Structure):
         ("adj_levels", ctypes.c_int), ("adj_slots", ctypes.c_int), ("adj_inner", ctypes.c_int),
         ("adj_top", ctypes.c_int), ("adj_sub", ctypes.c_int), ("pad1", ctypes.c_int),
         ("adj_bytes", ctypes.c_size_t), ("z_variant", ctypes.c_int), ("z_chunk", ctypes.c_int),
+        ("batch_sched", ctypes.c_int), ("batch_tile", ctypes.c_int),
     ]
 
 

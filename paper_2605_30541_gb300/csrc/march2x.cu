@@ -47,7 +47,7 @@ using f32::st4;
 using f32::unpack3;
 
 constexpr int NW2 = 4;        // warps per CTA
-constexpr int NS2 = 8;        // ring rows per field
+constexpr int NS2 = 8;        // ring rows per field (a power of two: slots are row & (NS2 - 1))
 constexpr int D2 = 3;         // rows staged ahead of use
 constexpr int PNW = 136;      // staged p^n row: columns x0 - 8 .. x0 + 127
 constexpr int OW = 128;       // staged p^{n-1} / c row: columns x0 - 4 .. x0 + 123
@@ -81,42 +81,29 @@ __device__ __forceinline__ float d2z9(const float4 *w, int k) {
                       lane_of(w[1], k), lane_of(w[7], k), lane_of(w[0], k), lane_of(w[8], k));
 }
 
-// the point sources of a member injected into row r of the lane's float4
-// (columns xl .. xl+3): value = wavelet[row] w summed per cell, as the one-step
-// march's injection groups sum their entries
-__device__ __forceinline__ bool src_row(const TBMember &M, int r, int xl, float val, float4 &inj) {
-    bool any = false;
-    for (int s = 0; s < M.nsrc; s++) {
-        const int k = M.sx[s] - xl;
-        if (M.sz[s] != r || k < 0 || k > 3) continue;
-        const float add = M.sw[s] * val;
-        if (k == 0) inj.x += add;
-        if (k == 1) inj.y += add;
-        if (k == 2) inj.z += add;
-        if (k == 3) inj.w += add;
-        any = true;
-    }
-    return any;
-}
-
-// one leapfrog update of the lane's four cells, as the row march computes it
+// one leapfrog update of the lane's four cells, as the row march computes it.
+// MODE 0: the plain update; 1: plus the injection inj (zeros in cells without
+// a source); 2: the sponge update plus the injection, with damping
+// a = c (ez + E4) (zero in undamped cells, where it gives the plain update's
+// bits). EDGE: cells outside [0, NX) give zeros.
+template <int MODE, bool EDGE>
 __device__ __forceinline__ float4 update4(const float *v, const float4 *w, const float4 pp4, const float4 c4,
-                                          const float4 inj, bool any_inj, float src_scale, bool spg, float ez,
-                                          const float4 E4, int gx, int NX) {
+                                          const float4 inj, float src_scale, float ez, const float4 E4, int gx,
+                                          int NX) {
     float res[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         float rhs = d2z9(w, k) + d2w(v, k);
-        if (any_inj) rhs += src_scale * lane_of(inj, k);
+        if (MODE >= 1) rhs += src_scale * lane_of(inj, k);
         const float p = v[4 + k], pp = lane_of(pp4, k), chv = lane_of(c4, k);
         float o;
-        if (spg) {
+        if (MODE == 2) {
             const float a = chv * (ez + lane_of(E4, k));
             o = __fdividef(2.f * p - (1.f - a) * pp + chv * rhs, 1.f + a);
         } else {
             o = 2.f * p - pp + chv * rhs;
         }
-        res[k] = gx + k >= 0 && gx + k < NX ? o : 0.f;
+        res[k] = !EDGE || (gx + k >= 0 && gx + k < NX) ? o : 0.f;
     }
     return make_float4(res[0], res[1], res[2], res[3]);
 }
@@ -134,60 +121,102 @@ __device__ void march2x_item(const StepArgs<float> &A, const TBMember &M, const 
     float *pw = odd ? b1 : b3;        // p^{n+1} out
     float *pw2 = odd ? b0 : b2;       // p^{n+2} out
     const int z0 = S.z0, z1 = S.z1;
+    const bool two = T.two;
     // step-1 rows: the item widened by 4 (two steps), or the item itself (one)
-    int rs = T.two ? z0 - 4 : z0;
+    int rs = two ? z0 - 4 : z0;
     if (fs && rs < 0) rs = 0;  // rows above the free surface are mirrors, not computed
-    const int re = T.two ? z1 + 3 : z1 - 1;
+    const int re = two ? z1 + 3 : z1 - 1;
     const bool sponge = A.bc == SIM_BC_SPONGE;
     const int zs0 = sponge ? g.nbz0 : 0, zs1 = sponge ? NZ - g.nbz1 : NZ;
     const bool spx = sponge && ((g.nbx0 > 0 && xl < g.nbx0) || (g.nbx1 > 0 && xl + 3 >= NX - g.nbx1));
     float4 E4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (sponge && xl >= -4 && xl < NX) E4 = __ldg(reinterpret_cast<const float4 *>(A.E[2] + xl));
     const float src_scale = A.src_scale;
-    const float *wav = static_cast<const float *>(A.io->wavelet);
+    const float *const E0 = A.E[0];
     const int colmax = P - kGhost;  // columns of a row: -kGhost .. colmax - 1
+    // the member's point source: its corners lie in rows zA and zA + 1; the
+    // injection of a row is summed from the member record when a row needs
+    // it (the one-step march's injection: weight x wavelet sample, one entry
+    // per cell, zeros elsewhere)
+    int zA = -(1 << 30);
+    bool hit = false;  // a corner in the lane's columns
+    for (int q = 0; q < M.nsrc; q++) {
+        zA = q == 0 ? M.sz[0] : min(zA, M.sz[q]);
+        hit |= M.sx[q] >= xl && M.sx[q] <= xl + 3;
+    }
+    const float *wav = static_cast<const float *>(A.io->wavelet);
+    auto src_row = [&](int r, int row) {  // the injection of row r, wavelet sample row
+        float4 inj = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float val = wav[row];
+        for (int q = 0; q < M.nsrc; q++) {
+            const int k = M.sx[q] - xl;
+            if (M.sz[q] != r || k < 0 || k > 3) continue;
+            const float add = M.sw[q] * val;
+            if (k == 0) inj.x = add;
+            if (k == 1) inj.y = add;
+            if (k == 2) inj.z = add;
+            if (k == 3) inj.w = add;
+        }
+        return inj;
+    };
+    // warp-uniform facts: rows with a source corner in the item, rows with
+    // damping (a sponge lane or a z-sponge row), items with columns outside
+    // [0, NX)
+    const bool hit_w = __any_sync(0xffffffffu, hit);
+    const bool spx_w = __any_sync(0xffffffffu, spx);
+    const bool edge_w = x0 - 4 < 0 || x0 + 124 > NX;
+    auto damped = [&](int r) { return spx_w || (sponge && (r < zs0 || r >= zs1)); };
+    auto src_in = [&](int r) { return hit_w && (r == zA || r == zA + 1); };
 
     // ring: p^n rows (columns x0 - 8 ..), p^{n-1} rows and c rows (columns x0 - 4 ..)
     float *RPN = W, *RPP = W + NS2 * PNW, *RCC = RPP + NS2 * OW;
-    const unsigned spn = (unsigned)__cvta_generic_to_shared(RPN), spp = (unsigned)__cvta_generic_to_shared(RPP),
-                   scc = (unsigned)__cvta_generic_to_shared(RCC);
-    auto zero_pn = [&](int slot, int c) {  // a staged p^n float4 beyond the row: zeros
-        *reinterpret_cast<float4 *>(RPN + slot * PNW + c - (x0 - 8)) = make_float4(0.f, 0.f, 0.f, 0.f);
-    };
-    auto stage_pn = [&](int row) {  // p^n row with columns x0 - 8 .. x0 + 127
-        const int slot = ((row % NS2) + NS2) % NS2;
-        const float *src = pc + (long long)row * P;
-        const int c0 = x0 - 8 + 4 * lane;
-        const bool in0 = c0 + 3 < colmax;
-        cp16_if(spn + 4u * (slot * PNW + 4 * lane), src + c0, in0);
-        if (!in0) zero_pn(slot, c0);
+    const unsigned spn = (unsigned)__cvta_generic_to_shared(RPN) + 16u * lane,
+                   spp = (unsigned)__cvta_generic_to_shared(RPP) + 16u * lane,
+                   scc = (unsigned)__cvta_generic_to_shared(RCC) + 16u * lane;
+    // the lane's staged columns and whether they lie in the row's memory
+    const int c0 = x0 - 8 + 4 * lane;
+    const bool in0 = c0 + 3 < colmax, in1 = lane < 2 && x0 + 123 + 4 * lane < colmax, ino = xl + 3 < colmax;
+    const long long oP = (long long)P;
+    // copy cursors: the next p^n row and the next p^{n-1} / c row to stage
+    const float *pn_src = pc + (long long)rs * P + c0;
+    const float *pp_src = pb + (long long)rs * P + xl;
+    const float *cc_src = A.ch + g.org + (long long)rs * P + xl;
+    int pn_row = rs, o_row = rs;
+    auto stage_pn = [&]() {  // p^n row pn_row, columns x0 - 8 .. x0 + 127
+        const unsigned d = spn + 4u * (pn_row & (NS2 - 1)) * PNW;
+        cp16_if(d, pn_src, in0);
+        if (!in0) *reinterpret_cast<float4 *>(RPN + (pn_row & (NS2 - 1)) * PNW + 4 * lane) = make_float4(0.f, 0.f, 0.f, 0.f);
         if (lane < 2) {
-            const int c1 = x0 + 120 + 4 * lane;
-            const bool in1 = c1 + 3 < colmax;
-            cp16_if(spn + 4u * (slot * PNW + 128 + 4 * lane), src + c1, in1);
-            if (!in1) zero_pn(slot, c1);
+            cp16_if(d + 512u, pn_src + 128, in1);
+            if (!in1)
+                *reinterpret_cast<float4 *>(RPN + (pn_row & (NS2 - 1)) * PNW + 128 + 4 * lane) =
+                    make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        pn_src += oP;
+        pn_row++;
     };
-    auto stage_o = [&](int row) {  // p^{n-1} and c rows, columns x0 - 4 .. x0 + 123
-        const int slot = ((row % NS2) + NS2) % NS2;
-        const long long o = (long long)row * P + xl;
-        const bool in = xl + 3 < colmax;
-        cp16_if(spp + 4u * (slot * OW + 4 * lane), pb + o, in);
-        cp16_if(scc + 4u * (slot * OW + 4 * lane), A.ch + g.org + o, in);
-        if (!in) {
-            *reinterpret_cast<float4 *>(RPP + slot * OW + 4 * lane) = make_float4(0.f, 0.f, 0.f, 0.f);
-            *reinterpret_cast<float4 *>(RCC + slot * OW + 4 * lane) = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto stage_o = [&]() {  // p^{n-1} and c rows o_row, columns x0 - 4 .. x0 + 123
+        const unsigned off = 4u * (o_row & (NS2 - 1)) * OW;
+        cp16_if(spp + off, pp_src, ino);
+        cp16_if(scc + off, cc_src, ino);
+        if (!ino) {
+            *reinterpret_cast<float4 *>(RPP + (o_row & (NS2 - 1)) * OW + 4 * lane) = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4 *>(RCC + (o_row & (NS2 - 1)) * OW + 4 * lane) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        pp_src += oP;
+        cc_src += oP;
+        o_row++;
     };
 
     // prologue: p^n rows rs .. rs + 3 (the first windows), then D2 groups of
     // the rows iterations rs .. rs + D2 - 1 will read
-    for (int r = rs; r < rs + 4; r++) stage_pn(r);
+    for (int r = rs; r < rs + 4; r++) stage_pn();
     cp_commit();
     for (int j = 0; j < D2; j++) {
-        const int r = rs + j;
-        if (r + 4 <= re + 4) stage_pn(r + 4);
-        if (r <= re) stage_o(r);
+        if (rs + j <= re) {
+            stage_pn();
+            stage_o();
+        }
         cp_commit();
     }
     // p^n window: rows r-4 .. r+4 of the lane's columns; rows above the
@@ -196,9 +225,8 @@ __device__ void march2x_item(const StepArgs<float> &A, const TBMember &M, const 
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const int r = rs - 4 + k;
-        const bool in = xl + 3 < colmax;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (in) v = (r < 0 && fs) ? neg4(ld4(pc + (long long)(-r) * P + xl)) : ld4(pc + (long long)r * P + xl);
+        if (ino) v = (r < 0 && fs) ? neg4(ld4(pc + (long long)(-r) * P + xl)) : ld4(pc + (long long)r * P + xl);
         w0[k] = v;
     }
 #pragma unroll
@@ -206,24 +234,23 @@ __device__ void march2x_item(const StepArgs<float> &A, const TBMember &M, const 
     cp_wait<D2>();
     __syncwarp();
 #pragma unroll
-    for (int k = 0; k < 4; k++) w0[4 + k] = ld4(RPN + (((rs + k) % NS2 + NS2) % NS2) * PNW + 4 + 4 * lane);
+    for (int k = 0; k < 4; k++) w0[4 + k] = ld4(RPN + ((rs + k) & (NS2 - 1)) * PNW + 4 + 4 * lane);
+    float *out1 = pw + (long long)(two ? z0 : rs) * P + xl, *out2 = pw2 + (long long)z0 * P + xl;
+    const bool st_lane = lane >= 1 && lane <= 30 && xl < NX;
 
     for (int r = rs; r <= re; r++) {
         // every lane's reads of the slots refilled below (rows r - 1 and
         // r - 5, read in the previous iteration) come before the refill
         __syncwarp();
-        {  // the rows iteration r + D2 reads
-            const int rr = r + D2;
-            if (rr <= re) {
-                stage_pn(rr + 4);
-                stage_o(rr);
-            }
-            cp_commit();
+        if (r + D2 <= re) {  // the rows iteration r + D2 reads
+            stage_pn();
+            stage_o();
         }
+        cp_commit();
         cp_wait<D2>();
         __syncwarp();
-        const int slot = ((r % NS2) + NS2) % NS2;
-        w0[8] = ld4(RPN + (((r + 4) % NS2 + NS2) % NS2) * PNW + 4 + 4 * lane);
+        const int slot = r & (NS2 - 1);
+        w0[8] = ld4(RPN + ((r + 4) & (NS2 - 1)) * PNW + 4 + 4 * lane);
         // step 1: p^{n+1} at row r
         float4 p1 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (r >= 0 && r < NZ && !(fs && r == 0)) {
@@ -231,41 +258,53 @@ __device__ void march2x_item(const StepArgs<float> &A, const TBMember &M, const 
             float v[12];
             unpack3(ld4(row + 4 * lane), w0[4], ld4(row + 4 * lane + 8), v);
             const float4 pp4 = ld4(RPP + slot * OW + 4 * lane), c4 = ld4(RCC + slot * OW + 4 * lane);
-            float4 inj = make_float4(0.f, 0.f, 0.f, 0.f);
-            const bool any = T.inj0 >= 0 && src_row(M, r, xl, wav[T.inj0], inj);
-            const bool spg = spx || (sponge && (r < zs0 || r >= zs1));
-            const float ez = spg ? __ldg(A.E[0] + r) : 0.f;
-            p1 = update4(v, w0, pp4, c4, inj, any, src_scale, spg, ez, E4, xl, NX);
+            const bool sr = src_in(r) && T.inj0 >= 0;
+            if (damped(r)) {
+                const float4 inj = sr ? src_row(r, T.inj0) : make_float4(0.f, 0.f, 0.f, 0.f);
+                p1 = update4<2, true>(v, w0, pp4, c4, inj, src_scale, __ldg(E0 + r), E4, xl, NX);
+            } else if (sr) {
+                p1 = update4<1, true>(v, w0, pp4, c4, src_row(r, T.inj0), src_scale, 0.f, E4, xl, NX);
+            } else if (edge_w) {
+                p1 = update4<0, true>(v, w0, pp4, c4, pp4, 0.f, 0.f, E4, xl, NX);
+            } else {
+                p1 = update4<0, false>(v, w0, pp4, c4, pp4, 0.f, 0.f, E4, xl, NX);
+            }
         }
         w1[8] = p1;
-        if (T.two && fs && r == 4) {  // the window now holds rows -4 .. 4: rows -4 .. -1 mirror rows 4 .. 1
+        if (two && fs && r == 4) {  // the window now holds rows -4 .. 4: rows -4 .. -1 mirror rows 4 .. 1
 #pragma unroll
             for (int k = 0; k < 4; k++) w1[k] = neg4(w1[8 - k]);
         }
-        if (!T.two) {  // one step: p^{n+1} of the item's own columns
-            if (lane >= 1 && lane <= 30 && xl < NX) st4(pw + (long long)r * P + xl, p1);
+        if (!two) {  // one step: p^{n+1} of the item's own columns
+            if (st_lane) st4(out1, p1);
+            out1 += P;
         } else if (r - 4 >= z0) {
             // step 2: p^{n+2} at row r2 = r - 4, from the p^{n+1} window
             const int r2 = r - 4;
             const float4 L = shfl4(w1[4], true), R = shfl4(w1[4], false);
-            if (lane >= 1 && lane <= 30) {
-                float4 p2 = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (r2 < NZ && !(fs && r2 == 0)) {
-                    float v[12];
-                    unpack3(L, w1[4], R, v);
-                    const int s2 = ((r2 % NS2) + NS2) % NS2;
-                    const float4 c4 = ld4(RCC + s2 * OW + 4 * lane);
-                    float4 inj = make_float4(0.f, 0.f, 0.f, 0.f);
-                    const bool any = T.inj1 >= 0 && src_row(M, r2, xl, wav[T.inj1], inj);
-                    const bool spg = spx || (sponge && (r2 < zs0 || r2 >= zs1));
-                    const float ez = spg ? __ldg(A.E[0] + r2) : 0.f;
-                    p2 = update4(v, w1, w0[0], c4, inj, any, src_scale, spg, ez, E4, xl, NX);
-                }
-                if (xl < NX) {
-                    st4(pw + (long long)r2 * P + xl, w1[4]);
-                    st4(pw2 + (long long)r2 * P + xl, p2);
+            float4 p2 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r2 < NZ && !(fs && r2 == 0)) {
+                float v[12];
+                unpack3(L, w1[4], R, v);
+                const float4 c4 = ld4(RCC + (r2 & (NS2 - 1)) * OW + 4 * lane);
+                const bool sr = src_in(r2) && T.inj1 >= 0;
+                if (damped(r2)) {
+                    const float4 inj = sr ? src_row(r2, T.inj1) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    p2 = update4<2, true>(v, w1, w0[0], c4, inj, src_scale, __ldg(E0 + r2), E4, xl, NX);
+                } else if (sr) {
+                    p2 = update4<1, true>(v, w1, w0[0], c4, src_row(r2, T.inj1), src_scale, 0.f, E4, xl, NX);
+                } else if (edge_w) {
+                    p2 = update4<0, true>(v, w1, w0[0], c4, c4, 0.f, 0.f, E4, xl, NX);
+                } else {
+                    p2 = update4<0, false>(v, w1, w0[0], c4, c4, 0.f, 0.f, E4, xl, NX);
                 }
             }
+            if (st_lane) {
+                st4(out1, w1[4]);
+                st4(out2, p2);
+            }
+            out1 += P;
+            out2 += P;
         }
 #pragma unroll
         for (int k = 0; k < 8; k++) {
@@ -277,7 +316,7 @@ __device__ void march2x_item(const StepArgs<float> &A, const TBMember &M, const 
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(NW2 * 32) k_march2x(const TBArgs B, const TBPass T) {
+__global__ void __launch_bounds__(NW2 * 32, 4) k_march2x(const TBArgs B, const TBPass T) {
     extern __shared__ float4 smx[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     float *W = reinterpret_cast<float *>(smx) + (size_t)wib * WARPF;

@@ -283,6 +283,7 @@ struct sim_s {
     int last_path = 0, last_rows = 0;      // see sim_info
     int zchunk = 0;                        // z-march chunk of the 3D kernel (planes per CTA)
     int zvariant = kZMarchTma;             // z-march staging (cp.async or TMA), see autotune3d
+    int batch_sched = 0, batch_tile = 0;   // schedule and tile of the last batch forward (as sim_info)
     void *pbuf3 = nullptr;                 // two-step row march: third and fourth pressure fields (max_shots shots each)
     int tuned3d = 0;                       // shot count the 3D launch shape was tuned for
     // adjoint-state buffers, allocated by the first sim_adjoint call (on
@@ -2532,6 +2533,10 @@ sim_status batch_run(int nitems, const sim_batch_item *items, cudaStream_t bst, 
         if ((e = body(bst))) return fail(e, "launch");
         return SIM_OK;
     }
+    for (int i = 0; i < nitems; i++) {
+        items[i].sim->batch_sched = march ? 1 : march2 ? 2 : stepped ? 3 : 4;
+        items[i].sim->batch_tile = tz;
+    }
     if (bst == nullptr) {  // the legacy stream cannot be captured: launch directly
         if ((e = body(bst))) return fail(e, "launch");
     } else {
@@ -2952,6 +2957,8 @@ sim_status sim_get_info(sim_t s, sim_info *out) {
     out->vmax = s->vmax;
     out->courant = s->vmax * s->d.dt / s->d.h;
     out->device_bytes = s->bytes;
+    out->batch_sched = s->batch_sched;
+    out->batch_tile = s->batch_tile;
     if (s->g.ndim == 3 && s->tuned3d) {
         out->z_variant = s->zvariant;
         out->z_chunk = s->zchunk;
