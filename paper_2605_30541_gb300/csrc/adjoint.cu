@@ -149,7 +149,11 @@ __global__ void k_residual(const T *__restrict__ gath, const T *__restrict__ d, 
 }
 
 // Interior cell i gathers every computational cell whose velocity copies it:
-// itself, plus the absorbing cells beyond it when it sits on an edge.
+// itself, plus the absorbing cells beyond it when it sits on an edge. Per
+// cell, the shots' imaging terms are summed first and then scaled by
+// -2 / (h^2 v) (one FP64 division per cell, not per cell and shot: FP64
+// division is slow on this part, and the edge cells fold whole absorbing
+// rows, columns or corner blocks serially).
 template <typename T>
 __global__ void k_fold(const Geom g, const T *__restrict__ G, long long gshot, int nshots,
                        const T *__restrict__ vpad, double inv_h2, double *acc) {
@@ -162,13 +166,14 @@ __global__ void k_fold(const Geom g, const T *__restrict__ G, long long gshot, i
         const int ya = iy == 0 ? 0 : iy + g.oy, yb = iy == g.ny - 1 ? g.NY : iy + g.oy + 1;
         const int xa = ix == 0 ? 0 : ix + g.ox, xb = ix == g.nx - 1 ? g.NX : ix + g.ox + 1;
         double sum = 0.0;
-        for (int s = 0; s < nshots; s++)
-            for (int z = za; z < zb; z++)
-                for (int y = ya; y < yb; y++)
-                    for (int x = xa; x < xb; x++) {
-                        const double v = (double)vpad[cell_off(g, z, y, x)];
-                        sum += -2.0 * inv_h2 / v * (double)G[s * gshot + cell_off(g, z, y, x)];
-                    }
+        for (int z = za; z < zb; z++)
+            for (int y = ya; y < yb; y++)
+                for (int x = xa; x < xb; x++) {
+                    const long long o = cell_off(g, z, y, x);
+                    double gs = 0.0;
+                    for (int s = 0; s < nshots; s++) gs += (double)G[s * gshot + o];
+                    sum += -2.0 * inv_h2 / (double)vpad[o] * gs;
+                }
         acc[i] += sum;
     }
 }

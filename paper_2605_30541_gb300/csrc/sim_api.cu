@@ -2184,7 +2184,8 @@ enum { kBatchMarch = 0, kBatchStepped = 1, kBatchPersistent = 2, kBatchMarch2 = 
 // One batch run with a given schedule and list tile height. probe > 0: run
 // only that many steps, launched directly (the autotuner's timing probe; no
 // graph, no output copies).
-sim_status batch_run(int nitems, const sim_batch_item *items, cudaStream_t bst, int sched, int tz_in, int probe) {
+sim_status batch_run(int nitems, const sim_batch_item *items, cudaStream_t bst, int sched, int tz_in, int probe,
+                     cudaEvent_t pe0 = nullptr, cudaEvent_t pe1 = nullptr) {
     if (nitems < 1 || !items) return thread_fail(SIM_ERR_ARG, "empty batch");
     sim_t s0 = items[0].sim;
     if (!s0) return thread_fail(SIM_ERR_ARG, "batch item 0 has no handle");
@@ -2383,7 +2384,7 @@ sim_status batch_run(int nitems, const sim_batch_item *items, cudaStream_t bst, 
         std::vector<TBMember> tm;
         std::vector<TBSample> ts;
         std::vector<MarchSeg> segs;
-        int rows = 32;
+        int rows = 40;  // item height: 40 and 48 measured fastest on the 619 x 1000 production slice
         if (const char *f = getenv("GSIM_TB_ROWS")) rows = std::max(1, atoi(f));
         for (size_t mi = 0; mi < members.size(); mi++) {
             const BatchMember &m = members[mi];
@@ -2529,8 +2530,10 @@ sim_status batch_run(int nitems, const sim_batch_item *items, cudaStream_t bst, 
         if (r == cudaSuccess) r = launch_batch2d(b, tz, any_cpml, grid, st);
         return r;
     };
-    if (probe > 0) {  // timing probe: launch directly, leave outputs alone
+    if (probe > 0) {  // timing probe: launch directly, leave outputs alone; the events bracket the launches only
+        if (pe0 && (e = cudaEventRecord(pe0, bst))) return fail(e, "timing");
         if ((e = body(bst))) return fail(e, "launch");
+        if (pe1 && (e = cudaEventRecord(pe1, bst))) return fail(e, "timing");
         return SIM_OK;
     }
     for (int i = 0; i < nitems; i++) {
@@ -2640,9 +2643,7 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
     for (const auto &c : cand) {
         const int steps = 6;
         if ((rc = batch_run(nitems, items, bst, c.first, c.second, 2))) break;  // warm-up (and first-use set-up)
-        cudaEventRecord(e0, bst);
-        if ((rc = batch_run(nitems, items, bst, c.first, c.second, steps))) break;
-        cudaEventRecord(e1, bst);
+        if ((rc = batch_run(nitems, items, bst, c.first, c.second, steps, e0, e1))) break;
         float ms = 0;
         if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
             cudaGetLastError();
