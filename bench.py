@@ -599,9 +599,10 @@ def run_ours(args):
         inf = pkg.sim_get_info(sim.handle)
         roof["z_march"] = {"staging": {1: "cp.async", 2: "TMA, x strips folded in", 3: "TMA",
                                        4: "TMA, plane loop not unrolled",
-                                       5: "TMA, x strips folded in, plane loop not unrolled"}.get(
+                                       5: "TMA, x strips folded in, plane loop not unrolled",
+                                       6: "TMA, plane loop unrolled by 3"}.get(
             inf.z_variant, inf.z_variant), "planes_per_cta": inf.z_chunk}
-        if inf.z_variant in (2, 3, 4, 5):
+        if inf.z_variant in (2, 3, 4, 5, 6):
             roof["kernel"] = "k_step3d_tma"
             roof["traffic"] = ncu_traffic(kfile, "tma_" + args.workload)
 

@@ -129,7 +129,7 @@ typedef struct {
     size_t adj_bytes;         /* device memory of the gradient's buffers */
     int z_variant;            /* 3D: z-march the autotuner chose (1 per-thread cp.async staging, 2 TMA
                                  staging with the x-strip CPML folded in, 3 TMA staging; 4 and 5: 3 and
-                                 2 with the plane loop not unrolled) */
+                                 2 with the plane loop not unrolled; 6: 3 with the loop unrolled by 3) */
     int z_chunk;              /* 3D: planes per CTA of the z-march */
     int batch_sched;          /* schedule of the last sim_batch forward this handle took part in
                                  (0 none yet, 1 row march, 2 two-step row march, 3 stepped tiles,

@@ -30,6 +30,52 @@ __device__ __forceinline__ float lane4(const float4 &v, int k) {
     return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
 __device__ __forceinline__ float4 ld4g(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+
+// The four cells of one thread at one plane: x window L, C, R (C the cells),
+// the nine y rows yv (yv[4] = C) and the nine z planes z0..z8 (z4 = C) of
+// p^n. The second differences run in cell pairs (0, 1) and (2, 3) with the
+// pair arithmetic, in d2c's order of roundings; rhs = D2x + D2y + D2z. The
+// plain update p^{n+1} = 2 p - p^{n-1} + c rhs is fma(c, rhs, fma(2, p,
+// -p^{n-1})), also in pairs; the sponge update (Eq. cerjan_pde) runs per
+// cell. Both z-marches call this, so they give the same bits.
+struct Cells4 {
+    float res[4], rhs[4], d2x[4];
+};
+__device__ __forceinline__ Cells4 cells4(const float4 &L, const float4 &C, const float4 &R, const float4 (&yv)[9],
+                                         const float4 &z0, const float4 &z1, const float4 &z2, const float4 &z3,
+                                         const float4 &z5, const float4 &z6, const float4 &z7, const float4 &z8,
+                                         const float4 &pp4, const float4 &ch4, bool spg, float es0,
+                                         const float4 &Ex4) {
+    // x: pairs of the 12-float window; (v3, v4), (v5, v6), (v1, v2), (v7, v8), (v9, v10) straddle float4s
+    const float2 v34 = make_float2(L.w, C.x), v56 = make_float2(C.y, C.z), v12 = make_float2(L.y, L.z),
+                 v78 = make_float2(C.w, R.x), v910 = make_float2(R.y, R.z);
+    const float2 xa = d2c2(lo2(C), v34, v56, hi2(L), hi2(C), v12, v78, lo2(L), lo2(R));
+    const float2 xb = d2c2(hi2(C), v56, v78, lo2(C), lo2(R), v34, v910, hi2(L), hi2(R));
+    const float2 ya = d2c2(lo2(C), lo2(yv[3]), lo2(yv[5]), lo2(yv[2]), lo2(yv[6]), lo2(yv[1]), lo2(yv[7]),
+                           lo2(yv[0]), lo2(yv[8]));
+    const float2 yb = d2c2(hi2(C), hi2(yv[3]), hi2(yv[5]), hi2(yv[2]), hi2(yv[6]), hi2(yv[1]), hi2(yv[7]),
+                           hi2(yv[0]), hi2(yv[8]));
+    const float2 za = d2c2(lo2(C), lo2(z3), lo2(z5), lo2(z2), lo2(z6), lo2(z1), lo2(z7), lo2(z0), lo2(z8));
+    const float2 zb = d2c2(hi2(C), hi2(z3), hi2(z5), hi2(z2), hi2(z6), hi2(z1), hi2(z7), hi2(z0), hi2(z8));
+    const float2 ra = add2(add2(xa, ya), za), rb = add2(add2(xb, yb), zb);
+    Cells4 o;
+    o.d2x[0] = xa.x, o.d2x[1] = xa.y, o.d2x[2] = xb.x, o.d2x[3] = xb.y;
+    o.rhs[0] = ra.x, o.rhs[1] = ra.y, o.rhs[2] = rb.x, o.rhs[3] = rb.y;
+    if (!spg) {
+        const float2 two = splat2(2.f);
+        const float2 oa = fma2(lo2(ch4), ra, fma2(two, lo2(C), neg2(lo2(pp4))));
+        const float2 ob = fma2(hi2(ch4), rb, fma2(two, hi2(C), neg2(hi2(pp4))));
+        o.res[0] = oa.x, o.res[1] = oa.y, o.res[2] = ob.x, o.res[3] = ob.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float p = lane4(C, k), chv = lane4(ch4, k), pp = lane4(pp4, k);
+            const float a = chv * (es0 + lane4(Ex4, k));
+            o.res[k] = (2.f * p - (1.f - a) * pp + chv * o.rhs[k]) / (1.f + a);
+        }
+    }
+    return o;
+}
 __device__ __forceinline__ void cp16(void *smem, const void *gmem) {
     const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
@@ -151,34 +197,19 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d(const StepArgs<float> A, cons
             const float *row = cur + (ly + 4) * SW3 + 4 + 4 * lane;  // this thread's float4 in the staged plane
             const float4 L = *reinterpret_cast<const float4 *>(row - 4), C = *reinterpret_cast<const float4 *>(row),
                          R = *reinterpret_cast<const float4 *>(row + 4);
-            const float v[12] = {L.x, L.y, L.z, L.w, C.x, C.y, C.z, C.w, R.x, R.y, R.z, R.w};
             float4 yv[9];
 #pragma unroll
             for (int m = 0; m < 9; m++) yv[m] = *reinterpret_cast<const float4 *>(row + (m - 4) * SW3);
             const float4 pp4 = *reinterpret_cast<const float4 *>(cur + NR * SW3 + ly * TX + 4 * lane);
             const float4 ch4 = *reinterpret_cast<const float4 *>(cur + NR * SW3 + TY * TX + ly * TX + 4 * lane);
+            const Cells4 cu = cells4(L, C, R, yv, q[0][r], q[1][r], q[2][r], q[3][r], q[5][r], q[6][r], q[7][r],
+                                     q[8][r], pp4, ch4, spg, ez + Ey[r], Ex4);
             float res[4], qk[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                const float p = v[4 + k];
-                const float d2x = d2c<float>(p, v[3 + k], v[5 + k], v[2 + k], v[6 + k], v[1 + k], v[7 + k], v[k], v[8 + k]);
-                const float d2y = d2c<float>(p, lane4(yv[3], k), lane4(yv[5], k), lane4(yv[2], k), lane4(yv[6], k),
-                                                lane4(yv[1], k), lane4(yv[7], k), lane4(yv[0], k), lane4(yv[8], k));
-                const float d2z = d2c<float>(p, lane4(q[3][r], k), lane4(q[5][r], k), lane4(q[2][r], k),
-                                                lane4(q[6][r], k), lane4(q[1][r], k), lane4(q[7][r], k),
-                                                lane4(q[0][r], k), lane4(q[8][r], k));
-                const float rhs = d2x + d2y + d2z;
-                const float chv = lane4(ch4, k), pp = lane4(pp4, k);
-                float out, es = 0.f;
-                if (spg) {
-                    es = ez + Ey[r] + lane4(Ex4, k);
-                    const float a = chv * es;
-                    out = (2.f * p - (1.f - a) * pp + chv * rhs) / (1.f + a);
-                } else {
-                    out = 2.f * p - pp + chv * rhs;
-                }
-                res[k] = out;
-                qk[k] = es * (out - pp) - rhs;
+                res[k] = cu.res[k];
+                const float es = spg ? ez + Ey[r] + lane4(Ex4, k) : 0.f;
+                qk[k] = es * (res[k] - lane4(pp4, k)) - cu.rhs[k];
             }
             if (xedge) {
 #pragma unroll
@@ -242,16 +273,21 @@ __device__ __forceinline__ bool xstrip4(const Geom &g, int x) {
 //
 // The same update as k_step3d, with the planes staged by the tensor memory
 // accelerator: one thread issues, per plane, three bulk tensor copies (p^n
-// with its radius-4 x/y halo, 136 x 16 cells; p^{n-1} and c of the tile's own
-// 128 x 8 cells) into a ring slot and arms the slot's mbarrier with their
-// byte count; every thread waits on the barrier (bounded) instead of issuing
-// its own 16-byte copies. The z loop is unrolled by the 9 planes of the
-// register queue, so the queue rotates by renaming registers, not by moving
-// them. A wait that gives up sets kFlagTimeout; all threads then leave
-// together after the copies already issued have landed (also bounded).
-constexpr int NST = 6;                                  // ring slots
-constexpr int SLOT_T = 16 * SW3 * 4 + 2 * 8 * TX * 4;   // bytes per slot: 8704 + 8192
-constexpr int HALO_T = 16 * SW3 * 4, OWN_T = 8 * TX * 4;
+// with its radius-4 x/y halo, 136 x 16 cells, into the halo ring; p^{n-1} and
+// c of the tile's own 128 x 8 cells into the own ring) and arms each slot's
+// mbarrier with its byte count; every thread waits on the barriers (bounded)
+// instead of issuing its own 16-byte copies. The z loop is unrolled by the 9
+// planes of the register queue (the queue rotates by renaming registers) or
+// not (it shifts). A wait that gives up sets kFlagTimeout; all threads then
+// leave together after the copies already issued have landed (also bounded).
+// Two rings: the p^n halo tiles (read four planes ahead of their own update,
+// for the register queue, and again at it) and the p^{n-1} / c tiles of the
+// own cells (read only at the update). The halo ring stages NSH - 1 planes
+// ahead, so the queue's plane z + 4 was requested three planes before its
+// use; the own ring stages NSO - 1 planes ahead. 8 x 8704 + 3 x 8192 bytes:
+// two CTAs per SM.
+constexpr int NSH = 8, NSO = 3;
+constexpr int HALO_T = 16 * SW3 * 4, OWN_T = 8 * TX * 4, OSLOT_T = 2 * OWN_T;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned cnt) {
@@ -309,15 +345,17 @@ __device__ __forceinline__ float4 shfl4w(const float4 v, bool up) {
 }
 
 // UN = 9: the plane loop unrolled by the queue's length (the queue rotates by
-// renaming); UN = 1: a plain loop that shifts the queue (smaller code).
+// renaming); UN = 1: a plain loop that shifts the queue (smaller code); UN =
+// 3: unrolled by three, the queue rotated by three after each block.
 template <int MODE, int UN>
 __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, const __grid_constant__ Tma3 M,
                                                        const int n, const int zchunk, const int ms, const XFuse X,
                                                        float *qs, float *Gs, const long long spin) {
     constexpr int TY = NW, NR = TY + 8;
     extern __shared__ __align__(128) unsigned char sm_t[];
-    unsigned char *const ring = sm_t;
-    unsigned long long *const full = reinterpret_cast<unsigned long long *>(sm_t + NST * SLOT_T);
+    unsigned char *const hring = sm_t, *const oring = sm_t + NSH * HALO_T;
+    unsigned long long *const fh = reinterpret_cast<unsigned long long *>(sm_t + NSH * HALO_T + NSO * OSLOT_T);
+    unsigned long long *const fo = fh + NSH;
 
     const Geom &g = A.g;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -348,27 +386,34 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
     const int tx = x0 + kGhost, ty = y0 + kGhost;
     const int wcur = (n & 1) * ms + shot, wprev = ((n + 1) & 1) * ms + shot;
     if (tid == 0) {
-        for (int k = 0; k < NST; k++) mbar_init(full + k, 1);
+        for (int k = 0; k < NSH + NSO; k++) mbar_init(fh + k, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
 
     cudaGridDependencySynchronize();
 
-    int zlast = zb - 1;        // last plane staged (thread 0)
-    auto stage = [&](int z, int k) {  // thread 0 only; k = (z - zb) % NST
+    // thread 0 stages: the halo tile of plane z into halo slot (z - zb) % NSH
+    // (planes up to ze + 3 feed the queue; beyond the grid the copy fills
+    // zeros), the own tiles of plane z < ze into own slot (z - zb) % NSO
+    int zlast = zb - 1, olast = zb - 1;  // last planes staged (thread 0)
+    auto stage_h = [&](int z, int k) {
         zlast = z;
-        unsigned char *dst = ring + k * SLOT_T;
-        const bool own = z < ze;
-        mbar_expect(full + k, HALO_T + (own ? 2 * OWN_T : 0));
-        tma_load4(dst, &M.ph, tx - 4, ty - 4, z + kGhost, wcur, full + k);
-        if (own) {
-            tma_load4(dst + HALO_T, &M.po, tx, ty, z + kGhost, wprev, full + k);
-            tma_load3(dst + HALO_T + OWN_T, &M.c, tx, ty, z + kGhost, full + k);
-        }
+        mbar_expect(fh + k, HALO_T);
+        tma_load4(hring + k * HALO_T, &M.ph, tx - 4, ty - 4, z + kGhost, wcur, fh + k);
     };
-    if (tid == 0)
-        for (int k = 0; k < NST - 1; k++) stage(zb + k, k);
+    auto stage_o = [&](int z, int k) {
+        if (z >= ze) return;
+        olast = z;
+        unsigned char *dst = oring + k * OSLOT_T;
+        mbar_expect(fo + k, OSLOT_T);
+        tma_load4(dst, &M.po, tx, ty, z + kGhost, wprev, fo + k);
+        tma_load3(dst + OWN_T, &M.c, tx, ty, z + kGhost, fo + k);
+    };
+    if (tid == 0) {
+        for (int k = 0; k < NSH - 1; k++) stage_h(zb + k, k);
+        for (int k = 0; k < NSO - 1; k++) stage_o(zb + k, k);
+    }
 
     // register queue of this thread's cells: plane z + m lives in q[(j + m + 4) % 9]
     // at unrolled step j of a block of 9 planes
@@ -400,21 +445,29 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
         zetaN = ld4g(A.zeta[2] + o);
     }
     bool bad = false;
-    // ring slots and barrier phases of planes z and z + 4, advanced per plane
-    int kz = 0, pz = 0, k4 = 4 % NST, p4 = 4 / NST;
+    // halo slots and barrier phases of planes z and z + 4, own slot and phase
+    // of plane z, advanced per plane
+    int kz = 0, pz = 0, k4 = 4 % NSH, p4 = 4 / NSH, ko = 0, po = 0;
     long long orow = own0 + (long long)zb * PP;  // this thread's float4 of plane z
     for (int zz = zb; zz < ze && !bad; zz += UN) {
 #pragma unroll
         for (int j = 0; j < UN; j++) {
             const int z = zz + j;
             if (z >= ze || bad) break;
-            if (tid == 0) stage(z + NST - 1, kz == 0 ? NST - 1 : kz - 1);
-            bool ok = mbar_wait(full + kz, pz, spin);
-            ok = ok && mbar_wait(full + k4, p4, spin);
+            if (tid == 0) {  // into the slots plane z - 1 used
+                stage_h(z + NSH - 1, kz == 0 ? NSH - 1 : kz - 1);
+                stage_o(z + NSO - 1, ko == 0 ? NSO - 1 : ko - 1);
+            }
+            // plane z's halo arrived before plane z - 4 used it (a completed
+            // phase answers at once); plane z + 4's and the own tiles are new
+            bool ok = mbar_wait(fh + kz, pz, spin);
+            ok = ok && mbar_wait(fh + k4, p4, spin);
+            ok = ok && mbar_wait(fo + ko, po, spin);
             ok = __all_sync(0xffffffffu, ok);  // the warp computes (and shuffles) together or not at all
             if (ok) {
-                const float *cur = reinterpret_cast<const float *>(ring + kz * SLOT_T);
-                const float *ahead = reinterpret_cast<const float *>(ring + k4 * SLOT_T);
+                const float *cur = reinterpret_cast<const float *>(hring + kz * HALO_T);
+                const float *ahead = reinterpret_cast<const float *>(hring + k4 * HALO_T);
+                const float *own = reinterpret_cast<const float *>(oring + ko * OSLOT_T);
                 q[(j + 8) % 9] = *reinterpret_cast<const float4 *>(ahead + (w + 4) * SW3 + 4 + 4 * lane);
                 const float ez = spg ? __ldg(A.E[0] + z) : 0.f;
                 const int gy = y0 + w;
@@ -425,32 +478,18 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
                 float4 yv[9];
 #pragma unroll
                 for (int m = 0; m < 9; m++) yv[m] = *reinterpret_cast<const float4 *>(row + (m - 4) * SW3);
-                const float4 pp4 = *reinterpret_cast<const float4 *>(cur + NR * SW3 + w * TX + 4 * lane);
-                const float4 ch4 = *reinterpret_cast<const float4 *>(cur + NR * SW3 + TY * TX + w * TX + 4 * lane);
+                const float4 pp4 = *reinterpret_cast<const float4 *>(own + w * TX + 4 * lane);
+                const float4 ch4 = *reinterpret_cast<const float4 *>(own + TY * TX + w * TX + 4 * lane);
+                const Cells4 cu = cells4(L, C, R, yv, q[j % 9], q[(j + 1) % 9], q[(j + 2) % 9], q[(j + 3) % 9],
+                                         q[(j + 5) % 9], q[(j + 6) % 9], q[(j + 7) % 9], q[(j + 8) % 9], pp4, ch4,
+                                         spg, ez + Ey, Ex4);
                 float res[4], qk[4], d2xs[4];
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
-                    const float p = v[4 + k];
-                    const float d2x = d2c<float>(p, v[3 + k], v[5 + k], v[2 + k], v[6 + k], v[1 + k], v[7 + k], v[k], v[8 + k]);
-                    d2xs[k] = d2x;
-                    const float d2y = d2c<float>(p, lane4(yv[3], k), lane4(yv[5], k), lane4(yv[2], k), lane4(yv[6], k),
-                                                lane4(yv[1], k), lane4(yv[7], k), lane4(yv[0], k), lane4(yv[8], k));
-                    const float d2z = d2c<float>(p, lane4(q[(j + 3) % 9], k), lane4(q[(j + 5) % 9], k),
-                                                    lane4(q[(j + 2) % 9], k), lane4(q[(j + 6) % 9], k),
-                                                    lane4(q[(j + 1) % 9], k), lane4(q[(j + 7) % 9], k),
-                                                    lane4(q[j % 9], k), lane4(q[(j + 8) % 9], k));
-                    const float rhs = d2x + d2y + d2z;
-                    const float chv = lane4(ch4, k), pp = lane4(pp4, k);
-                    float out, es = 0.f;
-                    if (spg) {
-                        es = ez + Ey + lane4(Ex4, k);
-                        const float a = chv * es;
-                        out = (2.f * p - (1.f - a) * pp + chv * rhs) / (1.f + a);
-                    } else {
-                        out = 2.f * p - pp + chv * rhs;
-                    }
-                    res[k] = out;
-                    qk[k] = es * (out - pp) - rhs;
+                    res[k] = cu.res[k];
+                    d2xs[k] = cu.d2x[k];
+                    const float es = spg ? ez + Ey + lane4(Ex4, k) : 0.f;
+                    qk[k] = es * (res[k] - lane4(pp4, k)) - cu.rhs[k];
                 }
                 if (xtile) {  // x-strip CPML of the row, as k_cpml_row3d computes it after the update
                     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -516,21 +555,33 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
                 for (int k = 0; k < 8; k++) q[k] = q[k + 1];
             }
             orow += PP;
-            if (++kz == NST) kz = 0, pz ^= 1;
-            if (++k4 == NST) k4 = 0, p4 ^= 1;
+            if (++kz == NSH) kz = 0, pz ^= 1;
+            if (++k4 == NSH) k4 = 0, p4 ^= 1;
+            if (++ko == NSO) ko = 0, po ^= 1;
             // every thread is done with slot kz before it is restaged; a wait
             // that gave up anywhere ends the march for the whole block
             bad = __syncthreads_or(!ok) != 0;
         }
+        if (UN == 3) {  // plane zz + 3 + m back to q[(m + 4) % 9] for the next block
+            const float4 t0 = q[0], t1 = q[1];
+#pragma unroll
+            for (int k = 0; k < 6; k++) q[k] = q[k + 3];
+            q[6] = t0;
+            q[7] = t1;
+        }
     }
-    // the last NST planes staged (ahead of the march) may still be in
-    // flight: wait for each (a completed phase returns at once) so no copy
-    // outlives the block
+    // the last planes staged (ahead of the march) may still be in flight:
+    // wait for each slot's last phase (a completed phase returns at once) so
+    // no copy outlives the block
     if (tid == 0) {
         if (bad) atomicOr(A.flags, kFlagTimeout);
-        for (int z = max(zb, zlast - NST + 1); z <= zlast; z++) {
-            const int k = (z - zb) % NST;
-            if (!mbar_wait(full + k, ((z - zb) / NST) & 1, spin)) atomicOr(A.flags, kFlagTimeout);
+        for (int z = max(zb, zlast - NSH + 1); z <= zlast; z++) {
+            const int k = (z - zb) % NSH;
+            if (!mbar_wait(fh + k, ((z - zb) / NSH) & 1, spin)) atomicOr(A.flags, kFlagTimeout);
+        }
+        for (int z = max(zb, olast - NSO + 1); z <= olast; z++) {
+            const int k = (z - zb) % NSO;
+            if (!mbar_wait(fo + k, ((z - zb) / NSO) & 1, spin)) atomicOr(A.flags, kFlagTimeout);
         }
     }
     __syncthreads();
@@ -1037,7 +1088,7 @@ size_t smem3d() {
 
 }  // namespace
 
-constexpr size_t kSmemTma = (size_t)NST * SLOT_T + NST * sizeof(unsigned long long);
+constexpr size_t kSmemTma = (size_t)NSH * HALO_T + NSO * OSLOT_T + (NSH + NSO) * sizeof(unsigned long long);
 
 // Which x-strip pass a CPML step uses: the one-pass kernel k_cpml_row3d when
 // each widened strip spans at most 12 float4s and the two ends are apart;
@@ -1113,7 +1164,8 @@ cudaError_t make_maps(const StepArgs<float> &a, Tma3 &m) {
 cudaError_t configure_step3d() {
     cudaError_t e = cudaSuccess;
     for (auto k : {k_step3d_tma<kModeForward, 9>, k_step3d_tma<kModeRecord, 9>, k_step3d_tma<kModeAdjoint, 9>,
-                   k_step3d_tma<kModeForward, 1>, k_step3d_tma<kModeRecord, 1>, k_step3d_tma<kModeAdjoint, 1>})
+                   k_step3d_tma<kModeForward, 1>, k_step3d_tma<kModeRecord, 1>, k_step3d_tma<kModeAdjoint, 1>,
+                   k_step3d_tma<kModeForward, 3>, k_step3d_tma<kModeRecord, 3>, k_step3d_tma<kModeAdjoint, 3>})
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTma);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_step3d<1, kModeForward>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1146,7 +1198,7 @@ cudaError_t launch_step3d(const StepArgs<float> &a, int n, int variant, int zchu
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    if (variant >= kZMarchTma && variant <= kZMarchTmaFoldLoop) {
+    if (variant >= kZMarchTma && variant <= kZMarchTmaLoop3) {
         Tma3 m;
         if (cudaError_t e = make_maps(a, m)) return e;
         cfg.dynamicSmemBytes = kSmemTma;
@@ -1159,6 +1211,13 @@ cudaError_t launch_step3d(const StepArgs<float> &a, int n, int variant, int zchu
             if (mode == kModeAdjoint)
                 return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeAdjoint, 1>, a, m, n, zchunk, ms, X, qs, Gs, spin);
             return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeForward, 1>, a, m, n, zchunk, ms, X, qs, Gs, spin);
+        }
+        if (variant == kZMarchTmaLoop3) {
+            if (mode == kModeRecord)
+                return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeRecord, 3>, a, m, n, zchunk, ms, X, qs, Gs, spin);
+            if (mode == kModeAdjoint)
+                return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeAdjoint, 3>, a, m, n, zchunk, ms, X, qs, Gs, spin);
+            return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeForward, 3>, a, m, n, zchunk, ms, X, qs, Gs, spin);
         }
         if (mode == kModeRecord)
             return cudaLaunchKernelEx(&cfg, k_step3d_tma<kModeRecord, 9>, a, m, n, zchunk, ms, X, qs, Gs, spin);

@@ -884,18 +884,20 @@ cudaError_t step3d_core(const sim_s *s, const StepArgs<float> &a, int n, int var
 // more, shorter ones fill the GPU). The first forward or gradient call for a
 // shot count times a few steps of each candidate on this GPU with CUDA
 // events (on zeroed fields, before the run resets them) and keeps the
-// fastest. GSIM_ZMARCH=async|tma|tma-plain|tma-loop|tma-loop-fold fixes the
+// fastest. GSIM_ZMARCH=async|tma|tma-plain|tma-loop|tma-loop-fold|tma-loop3 fixes the
 // variant, GSIM_ZCHUNK the chunk;
 // GSIM_AUTOTUNE=0 takes the TMA variant with the default chunk untimed.
 sim_status autotune3d(sim_t s, int nshots) {
     if (s->tuned3d == nshots) return SIM_OK;
     s->tuned3d = nshots;
     const int base = zchunk_for(s, nshots), NZ = s->g.NZ;
-    std::vector<int> variants = {kZMarchTmaPlain, kZMarchTmaLoop, kZMarchTma, kZMarchTmaFoldLoop, kZMarchAsync};
-    if (s->d.bc != SIM_BC_CPML) variants = {kZMarchTmaPlain, kZMarchTmaLoop, kZMarchAsync};  // no x strips to fold
-    static const char *const names[6] = {"", "async", "tma", "tma-plain", "tma-loop", "tma-loop-fold"};
+    std::vector<int> variants = {kZMarchTmaLoop3, kZMarchTmaPlain, kZMarchTmaLoop, kZMarchTma, kZMarchTmaFoldLoop,
+                                 kZMarchAsync};
+    if (s->d.bc != SIM_BC_CPML)  // no x strips to fold
+        variants = {kZMarchTmaLoop3, kZMarchTmaPlain, kZMarchTmaLoop, kZMarchAsync};
+    static const char *const names[7] = {"", "async", "tma", "tma-plain", "tma-loop", "tma-loop-fold", "tma-loop3"};
     if (const char *f = getenv("GSIM_ZMARCH"))
-        for (int v = 1; v <= 5; v++)
+        for (int v = 1; v <= 6; v++)
             if (!strcmp(f, names[v])) variants = {v};
     s->zvariant = variants[0];
     s->zchunk = base;

@@ -270,9 +270,10 @@ cudaError_t launch_march2x(const TBArgs &b, const TBPass &t, int nwarps, cudaStr
 // issued by one thread, completion on mbarriers, and folds the x-strip CPML
 // in where it can; kZMarchTmaPlain is the TMA march leaving the x strips to
 // their own pass; the two ...Loop variants are the same without unrolling
-// the plane loop (smaller code, the register queue shifted by moves). All
-// take z chunks of `zchunk` planes per CTA.
-enum { kZMarchAsync = 1, kZMarchTma = 2, kZMarchTmaPlain = 3, kZMarchTmaLoop = 4, kZMarchTmaFoldLoop = 5 };
+// the plane loop (smaller code, the register queue shifted by moves);
+// kZMarchTmaLoop3 unrolls it by 3 (the queue rotated by moves once per three
+// planes). All take z chunks of `zchunk` planes per CTA.
+enum { kZMarchAsync = 1, kZMarchTma = 2, kZMarchTmaPlain = 3, kZMarchTmaLoop = 4, kZMarchTmaFoldLoop = 5, kZMarchTmaLoop3 = 6 };
 struct Tma3 {
     CUtensorMap ph;  // p (both parities, all shots): 136 x 16 x 1 boxes, the plane with its x / y halo
     CUtensorMap po;  // the same buffers: 128 x 8 x 1 boxes, a tile's own cells

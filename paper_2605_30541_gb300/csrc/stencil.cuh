@@ -19,21 +19,48 @@ constexpr double kD1 = 4.0 / 5.0, kD2 = -1.0 / 5.0, kD3 = 4.0 / 105.0, kD4 = -1.
 //                                   + sum_{m=3,4} w_m (p_m + p_-m) + kC34 p_0.
 constexpr double kC34 = -2.0 * (kC3 + kC4);
 
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Second difference along one axis (without 1/h^2) from the nine values
 // c = p_0 and m_k = p_-k, p_k = p_+k. The two inner pairs, whose weights are
 // large, enter as differences from the centre: for a smooth field those are
 // exact in floating point and small, so the result carries no rounding error
 // of the size of w_0 p_0 (the plain form cancels terms 2.85 |p_0| large; over
 // thousands of FP32 steps that error accumulates into the wavefield). Summed
-// from the smallest term up; every kernel uses this one expression, so all
-// paths give the same bits.
+// from the smallest term up, every product-sum one fused multiply-add; every
+// kernel uses this one sequence of roundings (d2c2 below is the same sequence
+// on two cells at once), so all paths give the same bits.
 template <typename T>
 __device__ __forceinline__ T d2c(T c, T m1, T p1, T m2, T p2, T m3, T p3, T m4, T p4) {
     T r = T(kC34) * c;
-    r += T(kC4) * (p4 + m4);
-    r += T(kC3) * (p3 + m3);
-    r += T(kC2) * ((p2 - c) + (m2 - c));
-    r += T(kC1) * ((p1 - c) + (m1 - c));
+    r = fma_rn(T(kC4), p4 + m4, r);
+    r = fma_rn(T(kC3), p3 + m3, r);
+    r = fma_rn(T(kC2), (p2 - c) + (m2 - c), r);
+    r = fma_rn(T(kC1), (p1 - c) + (m1 - c), r);
+    return r;
+}
+
+// Two cells per instruction: the FP32 pair arithmetic of this architecture
+// (one instruction rounds both lanes as the scalar one rounds each), so a
+// pair of cells costs the instructions of one.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
+
+// d2c on two cells: the same operations in the same order, lane by lane
+__device__ __forceinline__ float2 d2c2(float2 c, float2 m1, float2 p1, float2 m2, float2 p2, float2 m3, float2 p3,
+                                       float2 m4, float2 p4) {
+    const float2 nc = neg2(c);
+    float2 r = mul2(splat2(float(kC34)), c);
+    r = fma2(splat2(float(kC4)), add2(p4, m4), r);
+    r = fma2(splat2(float(kC3)), add2(p3, m3), r);
+    r = fma2(splat2(float(kC2)), add2(add2(p2, nc), add2(m2, nc)), r);
+    r = fma2(splat2(float(kC1)), add2(add2(p1, nc), add2(m1, nc)), r);
     return r;
 }
 

@@ -59,7 +59,7 @@ def test_variants_and_chunks_agree_with_oracle(pkg, monkeypatch, bc, fs):
     ref = [oracle.forward(cfg, vel.astype(np.float64), w.astype(np.float64), src=s, rec=rec, snaps=True)
            for s in src]
     first = {}
-    for variant in ("async", "tma", "tma-plain", "tma-loop", "tma-loop-fold"):
+    for variant in ("async", "tma", "tma-plain", "tma-loop", "tma-loop-fold", "tma-loop3"):
         for chunk in (cfg["nz"] + 8, 13, 5):
             g, sn = run(pkg, monkeypatch, variant, chunk, cfg, vel, w, src, rec)
             for k in range(len(src)):
@@ -72,6 +72,7 @@ def test_variants_and_chunks_agree_with_oracle(pkg, monkeypatch, bc, fs):
     (ga, sa), (gt, st), (gp, sp) = first["async"], first["tma"], first["tma-plain"]
     assert np.array_equal(gp, ga) and np.array_equal(sp, sa)  # the same passes, the same bits
     assert np.array_equal(first["tma-loop"][0], ga) and np.array_equal(first["tma-loop"][1], sa)
+    assert np.array_equal(first["tma-loop3"][0], ga) and np.array_equal(first["tma-loop3"][1], sa)
     assert rel(first["tma-loop-fold"][0], ga) <= 1e-6 and rel(first["tma-loop-fold"][1], sa) <= 1e-6
     if bc == "cpml":
         assert rel(gt, ga) <= 1e-6 and rel(st, sa) <= 1e-6
