@@ -40,7 +40,11 @@ namespace {
 
 using f32::cp_async16;
 using f32::d1w;
+using f32::d2_pairs;
 using f32::d2w;
+using f32::Pairs4;
+using f32::plain1;
+using f32::plain4;
 using f32::lane_of;
 using f32::ld4;
 using f32::st4;
@@ -368,16 +372,9 @@ __device__ __forceinline__ void march_lean(const StepArgs<float> &A, const StepT
 #pragma unroll
             for (int j = 0; j < RB; j++) {
                 const float *row = sb + j * RW;
-                float v[12];
-                unpack3(ld4(row + 4 * lane - 4), w[4 + j], ld4(row + 4 * lane + 4), v);
+                const Pairs4 d = d2_pairs(ld4(row + 4 * lane - 4), w[4 + j], ld4(row + 4 * lane + 4), w + j);
                 const float4 pp4 = ld4(os + j * 256 + 4 * lane), c4 = ld4(os + j * 256 + 128 + 4 * lane);
-                float res[4];
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    const float rhs = d2z_at(w + j, k) + d2w(v, k);
-                    res[k] = 2.f * v[4 + k] - lane_of(pp4, k) + lane_of(c4, k) * rhs;
-                }
-                st4(out_row, make_float4(res[0], res[1], res[2], res[3]));
+                st4(out_row, plain4(w[4 + j], pp4, c4, add2(d.za, d.xa), add2(d.zb, d.xb)));
                 out_row += P;
             }
         } else {
@@ -388,6 +385,9 @@ __device__ __forceinline__ void march_lean(const StepArgs<float> &A, const StepT
                 const float *row = sb + j * RW;
                 float v[12];
                 unpack3(ld4(row + 4 * lane - 4), w[4 + j], ld4(row + 4 * lane + 4), v);
+                const Pairs4 d = d2_pairs(ld4(row + 4 * lane - 4), w[4 + j], ld4(row + 4 * lane + 4), w + j);
+                const float2 ra = add2(d.za, d.xa), rb = add2(d.zb, d.xb);
+                const float r4[4] = {ra.x, ra.y, rb.x, rb.y};
                 float4 inj = make_float4(0.f, 0.f, 0.f, 0.f);
                 bool any_inj = false;
                 if (lists && live) {
@@ -401,7 +401,7 @@ __device__ __forceinline__ void march_lean(const StepArgs<float> &A, const StepT
                 float res[4];
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
-                    float rhs = d2z_at(w + j, k) + d2w(v, k);
+                    float rhs = r4[k];
                     if (any_inj) rhs += src_scale * lane_of(inj, k);
                     const float p = v[4 + k], pp = lane_of(pp4, k), chv = lane_of(c4, k);
                     float o;
@@ -409,7 +409,7 @@ __device__ __forceinline__ void march_lean(const StepArgs<float> &A, const StepT
                         const float a = chv * (ez + lane_of(E4, k));
                         o = __fdividef(2.f * p - (1.f - a) * pp + chv * rhs, 1.f + a);
                     } else {
-                        o = 2.f * p - pp + chv * rhs;
+                        o = plain1(p, pp, chv, rhs);
                     }
                     res[k] = gx0 + k < NX ? o : 0.f;
                 }
@@ -636,12 +636,8 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
 
         float v[12];
         unpack3(ld4(rz + 4 * lane - 4), q[4], ld4(rz + 4 * lane + 4), v);
-        float d2x[4], d2z[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            d2x[k] = d2w(v, k);
-            d2z[k] = d2z_at(q, k);
-        }
+        const Pairs4 dp = d2_pairs(ld4(rz + 4 * lane - 4), q[4], ld4(rz + 4 * lane + 4), q);
+        const float d2x[4] = {dp.xa.x, dp.xa.y, dp.xb.x, dp.xb.y}, d2z[4] = {dp.za.x, dp.za.y, dp.zb.x, dp.zb.y};
 
         // CPML memory terms: the per-cell addend D1 psi^n + zeta^n of each axis
         float cadd[4] = {0.f, 0.f, 0.f, 0.f};
@@ -714,7 +710,7 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
             float rhs = d2z[k] + d2x[k];
             rhs += cadd[k];
             if (any_inj) rhs += src_scale * lane_of(inj, k);
-            const float out = 2.f * v[4 + k] - lane_of(pp4, k) + lane_of(c4, k) * rhs;
+            const float out = plain1(v[4 + k], lane_of(pp4, k), lane_of(c4, k), rhs);
             res[k] = gx0 + k < NX ? out : 0.f;
         }
         if (fs && z == 0) res[0] = res[1] = res[2] = res[3] = 0.f;

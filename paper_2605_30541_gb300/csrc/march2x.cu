@@ -40,7 +40,10 @@
 namespace gsim {
 namespace {
 
-using f32::d2w;
+using f32::d2_pairs;
+using f32::Pairs4;
+using f32::plain1;
+using f32::plain4;
 using f32::lane_of;
 using f32::ld4;
 using f32::st4;
@@ -74,13 +77,6 @@ __device__ __forceinline__ float4 shfl4(const float4 v, bool up) {
     return r;
 }
 
-// second difference along z at cell k of the 9-row window w (centre w[4]):
-// the row march's own expression
-__device__ __forceinline__ float d2z9(const float4 *w, int k) {
-    return d2c<float>(lane_of(w[4], k), lane_of(w[3], k), lane_of(w[5], k), lane_of(w[2], k), lane_of(w[6], k),
-                      lane_of(w[1], k), lane_of(w[7], k), lane_of(w[0], k), lane_of(w[8], k));
-}
-
 // one leapfrog update of the lane's four cells, as the row march computes it.
 // MODE 0: the plain update; 1: plus the injection inj (zeros in cells without
 // a source); 2: the sponge update plus the injection, with damping
@@ -90,21 +86,29 @@ template <int MODE, bool EDGE>
 __device__ __forceinline__ float4 update4(const float *v, const float4 *w, const float4 pp4, const float4 c4,
                                           const float4 inj, float src_scale, float ez, const float4 E4, int gx,
                                           int NX) {
+    const Pairs4 d = d2_pairs(make_float4(v[0], v[1], v[2], v[3]), w[4], make_float4(v[8], v[9], v[10], v[11]), w);
+    const float2 ra = add2(d.za, d.xa), rb = add2(d.zb, d.xb);
     float res[4];
+    if (MODE == 0) {
+        const float4 o = plain4(w[4], pp4, c4, ra, rb);
+        res[0] = o.x, res[1] = o.y, res[2] = o.z, res[3] = o.w;
+    } else {
+        const float r4[4] = {ra.x, ra.y, rb.x, rb.y};
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        float rhs = d2z9(w, k) + d2w(v, k);
-        if (MODE >= 1) rhs += src_scale * lane_of(inj, k);
-        const float p = v[4 + k], pp = lane_of(pp4, k), chv = lane_of(c4, k);
-        float o;
-        if (MODE == 2) {
-            const float a = chv * (ez + lane_of(E4, k));
-            o = __fdividef(2.f * p - (1.f - a) * pp + chv * rhs, 1.f + a);
-        } else {
-            o = 2.f * p - pp + chv * rhs;
+        for (int k = 0; k < 4; k++) {
+            const float rhs = r4[k] + src_scale * lane_of(inj, k);
+            const float p = v[4 + k], pp = lane_of(pp4, k), chv = lane_of(c4, k);
+            if (MODE == 2) {
+                const float a = chv * (ez + lane_of(E4, k));
+                res[k] = __fdividef(2.f * p - (1.f - a) * pp + chv * rhs, 1.f + a);
+            } else {
+                res[k] = plain1(p, pp, chv, rhs);
+            }
         }
-        res[k] = !EDGE || (gx + k >= 0 && gx + k < NX) ? o : 0.f;
     }
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        if (EDGE && !(gx + k >= 0 && gx + k < NX)) res[k] = 0.f;
     return make_float4(res[0], res[1], res[2], res[3]);
 }
 
