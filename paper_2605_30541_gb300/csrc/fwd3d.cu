@@ -80,6 +80,10 @@ __device__ __forceinline__ void cp16(void *smem, const void *gmem) {
     const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
 }
+// 16-byte copy that writes zeros (reads nothing) when v is false
+__device__ __forceinline__ void cp16z(unsigned dst, const void *gmem, bool v) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(gmem), "r"(v ? 16 : 0) : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -771,6 +775,8 @@ __device__ __forceinline__ float comp4(const float4 &v, int c) {
     return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
 }
 
+constexpr int CNS = 4;  // positions in a column pass thread's copy ring
+
 struct ColRanges {
     int n;            // ranges (1 or 2)
     int s0[2], s1[2]; // [s0, s1) along the axis
@@ -802,20 +808,28 @@ __global__ void __launch_bounds__(128) k_cpml_col3d(const StepArgs<float> A, con
     auto strip = [&](int r) { return (lo > 0 && r >= 0 && r < lo) || (hi > 0 && r >= N - hi && r < N); };
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
 
-    // the loads of position r (p^n at r + 4, psi^{n-1} at r, and at q = r - 4
-    // zeta^{n-1}, c, p^{n+1}), issued one position ahead of their use
-    struct Ld {
-        float4 p, ps, zo, c, pv;
-    };
-    auto load = [&](int r, Ld &L) {
-        L.p = ld4g(p + (long long)(r + 4) * s);
-        L.ps = strip(r) ? ld4g(psi + (long long)r * s) : zero;
+    // The loads of position r (p^n at r + 4, psi^{n-1} at r, and at q = r - 4
+    // zeta^{n-1}, c, p^{n+1}) go by cp.async into this thread's slots of a
+    // shared-memory ring, CNS - 1 positions ahead of their use; a load that
+    // does not apply fills its slot with zeros (source size 0). Slot (k, f) of
+    // thread t is float4 (k * 5 + f) * blockDim + t: a warp's 16-byte accesses
+    // are consecutive. The thread reads only its own slots, so its own
+    // cp.async.wait_group orders them.
+    extern __shared__ float4 col_ring[];
+    const unsigned ring0 = (unsigned)__cvta_generic_to_shared(col_ring + threadIdx.x);
+    const unsigned fstep = 16u * blockDim.x;  // bytes from one field's slot to the next
+    auto issue = [&](int r, int slot) {
+        const unsigned d = ring0 + (unsigned)(slot * 5) * fstep;
         const int q = r - 4;
-        if (q >= s0 && !skip_row) {
-            L.zo = strip(q) ? ld4g(zeta + (long long)q * s) : zero;
-            L.c = ld4g(ch + (long long)q * s);
-            L.pv = ld4g(pn + (long long)q * s);
-        }
+        const bool qq = q >= s0 && !skip_row;
+        cp16z(d, p + (long long)(r + 4) * s, true);
+        cp16z(d + fstep, strip(r) ? psi + (long long)r * s : p, strip(r));
+        cp16z(d + 2 * fstep, qq && strip(q) ? zeta + (long long)q * s : p, qq && strip(q));
+        cp16z(d + 3 * fstep, qq ? ch + (long long)q * s : p, qq);
+        cp16z(d + 4 * fstep, qq ? pn + (long long)q * s : p, qq);
+    };
+    auto slot_ld = [&](int slot, int f) {
+        return col_ring[(slot * 5 + f) * blockDim.x + threadIdx.x];
     };
 
     float4 P[13], S[9];
@@ -825,26 +839,34 @@ __global__ void __launch_bounds__(128) k_cpml_col3d(const StepArgs<float> A, con
     for (int m = 0; m < 8; m++) P[4 + m] = ld4g(p + (long long)(s0 - 8 + m) * s);
 #pragma unroll
     for (int m = 0; m < 9; m++) S[m] = zero;
-    Ld nx{zero, zero, zero, zero, zero};
-    load(s0 - 4, nx);
+    const int r0 = s0 - 4, r1 = s1 + 4;
+#pragma unroll
+    for (int k = 0; k < CNS - 1; k++) {
+        if (r0 + k < r1) issue(r0 + k, k);
+        cp_commit();
+    }
 
-    for (int r = s0 - 4; r < s1 + 4; r++) {
-        const Ld cur = nx;
-        if (r + 1 < s1 + 4) load(r + 1, nx);
+    for (int r = r0, slot = 0; r < r1; r++, slot = slot == CNS - 1 ? 0 : slot + 1) {
+        // position r + CNS - 1 into the slot position r - 1 used
+        if (r + CNS - 1 < r1) issue(r + CNS - 1, slot == 0 ? CNS - 1 : slot - 1);
+        cp_commit();
+        cp_wait<CNS - 1>();
+        struct {
+            float4 p, ps, zo, c, pv;
+        } cur = {slot_ld(slot, 0), slot_ld(slot, 1), slot_ld(slot, 2), slot_ld(slot, 3), slot_ld(slot, 4)};
         P[12] = cur.p;
         // psi^n at r (zero off the strips)
         float4 ps = zero;
         if (strip(r)) {
             const float a = __ldg(ca + r), b = __ldg(cb + r);
-            float d[4];
-#pragma unroll
-            for (int c = 0; c < 4; c++)
-                d[c] = float(kD1) * (comp4(P[9], c) - comp4(P[7], c)) +
-                       float(kD2) * (comp4(P[10], c) - comp4(P[6], c)) +
-                       float(kD3) * (comp4(P[11], c) - comp4(P[5], c)) +
-                       float(kD4) * (comp4(P[12], c) - comp4(P[4], c));
+            const float2 da = d1c2(lo2(P[7]), lo2(P[9]), lo2(P[6]), lo2(P[10]), lo2(P[5]), lo2(P[11]), lo2(P[4]),
+                                   lo2(P[12]));
+            const float2 db = d1c2(hi2(P[7]), hi2(P[9]), hi2(P[6]), hi2(P[10]), hi2(P[5]), hi2(P[11]), hi2(P[4]),
+                                   hi2(P[12]));
             const float4 old = cur.ps;
-            ps = make_float4(b * old.x + a * d[0], b * old.y + a * d[1], b * old.z + a * d[2], b * old.w + a * d[3]);
+            const float2 pa = fma2(splat2(a), da, mul2(splat2(b), lo2(old)));
+            const float2 pb = fma2(splat2(a), db, mul2(splat2(b), hi2(old)));
+            ps = make_float4(pa.x, pa.y, pb.x, pb.y);
             *reinterpret_cast<float4 *>(psi + (long long)r * s) = ps;
         }
         S[8] = ps;
@@ -860,23 +882,27 @@ __global__ void __launch_bounds__(128) k_cpml_col3d(const StepArgs<float> A, con
             const float4 zo = cur.zo, c4 = cur.c;
             float4 pv = cur.pv;
             float zt[4], add[4];
-#pragma unroll
-            for (int c = 0; c < 4; c++) {
-                const float d2 = d2c<float>(comp4(P[4], c), comp4(P[3], c), comp4(P[5], c), comp4(P[2], c),
-                                            comp4(P[6], c), comp4(P[1], c), comp4(P[7], c), comp4(P[0], c),
-                                            comp4(P[8], c));
-                const float dps = float(kD1) * (comp4(S[5], c) - comp4(S[3], c)) +
-                                  float(kD2) * (comp4(S[6], c) - comp4(S[2], c)) +
-                                  float(kD3) * (comp4(S[7], c) - comp4(S[1], c)) +
-                                  float(kD4) * (comp4(S[8], c) - comp4(S[0], c));
-                zt[c] = b * comp4(zo, c) + a * (d2 + dps);
-                add[c] = dps + zt[c];
+            {
+                const float2 d2a = d2c2(lo2(P[4]), lo2(P[3]), lo2(P[5]), lo2(P[2]), lo2(P[6]), lo2(P[1]), lo2(P[7]),
+                                        lo2(P[0]), lo2(P[8]));
+                const float2 d2b = d2c2(hi2(P[4]), hi2(P[3]), hi2(P[5]), hi2(P[2]), hi2(P[6]), hi2(P[1]), hi2(P[7]),
+                                        hi2(P[0]), hi2(P[8]));
+                const float2 dsa = d1c2(lo2(S[3]), lo2(S[5]), lo2(S[2]), lo2(S[6]), lo2(S[1]), lo2(S[7]), lo2(S[0]),
+                                        lo2(S[8]));
+                const float2 dsb = d1c2(hi2(S[3]), hi2(S[5]), hi2(S[2]), hi2(S[6]), hi2(S[1]), hi2(S[7]), hi2(S[0]),
+                                        hi2(S[8]));
+                const float2 za = fma2(splat2(a), add2(d2a, dsa), mul2(splat2(b), lo2(zo)));
+                const float2 zb = fma2(splat2(a), add2(d2b, dsb), mul2(splat2(b), hi2(zo)));
+                const float2 aa = add2(dsa, za), ab = add2(dsb, zb);
+                zt[0] = za.x, zt[1] = za.y, zt[2] = zb.x, zt[3] = zb.y;
+                add[0] = aa.x, add[1] = aa.y, add[2] = ab.x, add[3] = ab.y;
             }
             if (in) *reinterpret_cast<float4 *>(zeta + (long long)q * s) = make_float4(zt[0], zt[1], zt[2], zt[3]);
-            pv.x += c4.x * add[0];
-            pv.y += c4.y * add[1];
-            pv.z += c4.z * add[2];
-            pv.w += c4.w * add[3];
+            {
+                const float2 va = fma2(lo2(c4), make_float2(add[0], add[1]), lo2(pv));
+                const float2 vb = fma2(hi2(c4), make_float2(add[2], add[3]), hi2(pv));
+                pv = make_float4(va.x, va.y, vb.x, vb.y);
+            }
             *reinterpret_cast<float4 *>(pn + (long long)q * s) = pv;
             if (qcol) {  // the addend is part of the Laplacian in the imaging term
                 float4 qv = ld4g(qcol + (long long)q * s);
@@ -892,6 +918,7 @@ __global__ void __launch_bounds__(128) k_cpml_col3d(const StepArgs<float> A, con
 #pragma unroll
         for (int m = 0; m < 8; m++) S[m] = S[m + 1];
     }
+    cp_wait<0>();  // no copy outlives the thread
 }
 
 // CPML of the x axis in one pass after the update: a half-warp per (z, y)
@@ -915,69 +942,90 @@ __device__ __forceinline__ float4 shfl4(const float4 v, int d, bool up) {
     return r;
 }
 
+// Two row ends per half-warp (items 2 hw and 2 hw + 1 of the (end, row)
+// list): the loads of both are issued before either's arithmetic, so twice
+// the bytes are in flight per thread.
+constexpr int XR = 2;
 __global__ void __launch_bounds__(128) k_cpml_row3d(const StepArgs<float> A, const int n, const XEnds E,
                                                     const long long nrows, float *qrec) {
     const Geom &g = A.g;
     const long long hw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 4;
     const int j = threadIdx.x & 15;
-    const bool live = hw < (long long)E.ne * nrows;  // every lane takes part in the shuffles
-    const int e = live && hw >= nrows ? 1 : 0;
-    const long long row = live ? hw - e * nrows : 0;
-    const int z = (int)(row / g.NY), y = (int)(row - (long long)z * g.NY);
-    const int xa = e ? E.xa[1] : E.xa[0], nq = e ? E.nq[1] : E.nq[0];
-    const int xj = xa + 4 * j;
-    const long long o = (long long)blockIdx.y * g.fstride + cell_off(g, z, y, 0) + xj;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int NX = g.NX, nbx0 = g.nbx0, nbx1 = g.nbx1;
-    const bool strip = xstrip4(g, xj);
-    const bool pl = live && j < nq + 4, sl = live && j >= 1 && j < nq + 3, ql = live && j >= 2 && j < nq + 2;
-
-    // every load of the lane first (one DRAM round trip), then the arithmetic
-    const bool qs = ql && !(g.fs && z == 0);  // the free-surface row stays zero
-    float *__restrict__ psi = A.psi[2][0] + o;
-    float *__restrict__ zeta = A.zeta[2] + o;
-    float *__restrict__ pn = A.pbuf[(n + 1) & 1] + o;
-    const float4 pc = pl ? ld4g(A.pbuf[n & 1] + o) : zero;
-    const bool ss = sl && strip;
-    const float4 old = ss ? ld4g(psi) : zero;
-    float4 a4 = zero, b4 = zero;
-    if (ss) {
-        a4 = ld4g(A.ca[2] + xj);
-        b4 = ld4g(A.cb[2] + xj);
-    }
-    const float4 zo = qs && strip ? ld4g(zeta) : zero;
-    const float4 c4 = qs ? ld4g(A.ch + (o - (long long)blockIdx.y * g.fstride)) : zero;
-    float4 pv = qs ? ld4g(pn) : zero;
-
-    const float4 pL = shfl4(pc, 1, true), pR = shfl4(pc, 1, false);
-    const float v[12] = {pL.x, pL.y, pL.z, pL.w, pc.x, pc.y, pc.z, pc.w, pR.x, pR.y, pR.z, pR.w};
-    // psi^n of the lane's cells
-    float4 ps = zero;
-    if (ss) {
-        ps = xcpml_psi(v, old, a4, b4);
-        *reinterpret_cast<float4 *>(psi) = ps;
-    }
-    const float4 sL = shfl4(ps, 1, true), sR = shfl4(ps, 1, false);
-    if (!qs) return;
-    const float w[12] = {sL.x, sL.y, sL.z, sL.w, ps.x, ps.y, ps.z, ps.w, sR.x, sR.y, sR.z, sR.w};
-    float d2[4], zt[4], add[4];
+    const long long sh = (long long)blockIdx.y * g.fstride;
+    struct It {
+        long long o;
+        int z, xj;
+        bool strip, pl, ss, qs, ql;
+        float4 pc, old, a4, b4, zo, c4, pv;
+    };
+    It it[XR];
 #pragma unroll
-    for (int k = 0; k < 4; k++)
-        d2[k] = d2c<float>(v[4 + k], v[3 + k], v[5 + k], v[2 + k], v[6 + k], v[1 + k], v[7 + k], v[k], v[8 + k]);
-    xcpml_zeta(w, d2, zo, a4, b4, zt, add);
-    if (strip) *reinterpret_cast<float4 *>(zeta) = make_float4(zt[0], zt[1], zt[2], zt[3]);
-    pv.x += c4.x * add[0];
-    pv.y += c4.y * add[1];
-    pv.z += c4.z * add[2];
-    pv.w += c4.w * add[3];
-    *reinterpret_cast<float4 *>(pn) = pv;
-    if (qrec) {  // record mode: the addend is part of the Laplacian in the imaging term
-        float4 qv = ld4g(qrec + o);
-        qv.x -= add[0];
-        qv.y -= add[1];
-        qv.z -= add[2];
-        qv.w -= add[3];
-        *reinterpret_cast<float4 *>(qrec + o) = qv;
+    for (int u = 0; u < XR; u++) {  // every load of both items first
+        It &I = it[u];
+        const long long idx = XR * hw + u;
+        const bool live = idx < (long long)E.ne * nrows;  // every lane takes part in the shuffles
+        const int e = live && idx >= nrows ? 1 : 0;
+        const long long row = live ? idx - e * nrows : 0;
+        const int z = (int)(row / g.NY), y = (int)(row - (long long)z * g.NY);
+        const int xa = e ? E.xa[1] : E.xa[0], nq = e ? E.nq[1] : E.nq[0];
+        I.z = z;
+        I.xj = xa + 4 * j;
+        I.o = cell_off(g, z, y, 0) + I.xj;
+        I.strip = xstrip4(g, I.xj);
+        I.pl = live && j < nq + 4;
+        const bool sl = live && j >= 1 && j < nq + 3;
+        I.ql = live && j >= 2 && j < nq + 2;
+        I.qs = I.ql && !(g.fs && z == 0);  // the free-surface row stays zero
+        I.ss = sl && I.strip;
+        I.pc = I.pl ? ld4g(A.pbuf[n & 1] + sh + I.o) : zero;
+        I.old = I.ss ? ld4g(A.psi[2][0] + sh + I.o) : zero;
+        I.a4 = zero, I.b4 = zero;
+        if (I.ss) {
+            I.a4 = ld4g(A.ca[2] + I.xj);
+            I.b4 = ld4g(A.cb[2] + I.xj);
+        }
+        I.zo = I.qs && I.strip ? ld4g(A.zeta[2] + sh + I.o) : zero;
+        I.c4 = I.qs ? ld4g(A.ch + I.o) : zero;
+        I.pv = I.qs ? ld4g(A.pbuf[(n + 1) & 1] + sh + I.o) : zero;
+    }
+#pragma unroll
+    for (int u = 0; u < XR; u++) {
+        const It &I = it[u];
+        float *__restrict__ psi = A.psi[2][0] + sh + I.o;
+        float *__restrict__ zeta = A.zeta[2] + sh + I.o;
+        float *__restrict__ pn = A.pbuf[(n + 1) & 1] + sh + I.o;
+        const float4 pL = shfl4(I.pc, 1, true), pR = shfl4(I.pc, 1, false);
+        const float v[12] = {pL.x, pL.y, pL.z, pL.w, I.pc.x, I.pc.y, I.pc.z, I.pc.w, pR.x, pR.y, pR.z, pR.w};
+        // psi^n of the lane's cells
+        float4 ps = zero;
+        if (I.ss) {
+            ps = xcpml_psi(v, I.old, I.a4, I.b4);
+            *reinterpret_cast<float4 *>(psi) = ps;
+        }
+        const float4 sL = shfl4(ps, 1, true), sR = shfl4(ps, 1, false);
+        if (!I.qs) continue;
+        const float w[12] = {sL.x, sL.y, sL.z, sL.w, ps.x, ps.y, ps.z, ps.w, sR.x, sR.y, sR.z, sR.w};
+        float d2[4], zt[4], add[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            d2[k] = d2c<float>(v[4 + k], v[3 + k], v[5 + k], v[2 + k], v[6 + k], v[1 + k], v[7 + k], v[k], v[8 + k]);
+        xcpml_zeta(w, d2, I.zo, I.a4, I.b4, zt, add);
+        if (I.strip) *reinterpret_cast<float4 *>(zeta) = make_float4(zt[0], zt[1], zt[2], zt[3]);
+        float4 pv = I.pv;
+        pv.x += I.c4.x * add[0];
+        pv.y += I.c4.y * add[1];
+        pv.z += I.c4.z * add[2];
+        pv.w += I.c4.w * add[3];
+        *reinterpret_cast<float4 *>(pn) = pv;
+        if (qrec) {  // record mode: the addend is part of the Laplacian in the imaging term
+            float4 qv = ld4g(qrec + sh + I.o);
+            qv.x -= add[0];
+            qv.y -= add[1];
+            qv.z -= add[2];
+            qv.w -= add[3];
+            *reinterpret_cast<float4 *>(qrec + sh + I.o) = qv;
+        }
     }
 }
 
@@ -1254,7 +1302,7 @@ cudaError_t launch_cpml3d(const StepArgs<float> &a, int n, int ax, int phase, in
         if (x_row_pass(g, &E)) {
             if (phase == 0) return cudaSuccess;
             const int m = E.ne;
-            const long long nrows = (long long)g.NZ * g.NY, th = 16 * m * nrows;
+            const long long nrows = (long long)g.NZ * g.NY, th = 16 * ((m * nrows + XR - 1) / XR);
             k_cpml_row3d<<<dim3((unsigned)((th + 127) / 128), nshots), 128, 0, st>>>(a, n, E, nrows, qs);
             return cudaGetLastError();
         }
@@ -1276,7 +1324,8 @@ cudaError_t launch_cpml3d(const StepArgs<float> &a, int n, int ax, int phase, in
             if (phase == 0 || R.n == 0) return cudaSuccess;
             const int ncols = (ax == 0 ? g.NY : g.NZ) * ((g.NX + 3) >> 2);
             const long long th = (long long)R.n * ncols;
-            k_cpml_col3d<<<dim3((unsigned)((th + 127) / 128), nshots), 128, 0, st>>>(a, n, ax, R, ncols, qs);
+            k_cpml_col3d<<<dim3((unsigned)((th + 127) / 128), nshots), 128, 128 * CNS * 5 * sizeof(float4), st>>>(
+                a, n, ax, R, ncols, qs);
             return cudaGetLastError();
         }
     }

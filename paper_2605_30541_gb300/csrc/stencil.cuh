@@ -52,6 +52,18 @@ __device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
 
+// First difference (without 1/h) of two cells from the eight neighbours
+// m_k = p_-k, p_k = p_+k: d_1 (p_1 - m_1) + d_2 (p_2 - m_2) + d_3 (p_3 - m_3) +
+// d_4 (p_4 - m_4), each further term one fused multiply-add
+__device__ __forceinline__ float2 d1c2(float2 m1, float2 p1, float2 m2, float2 p2, float2 m3, float2 p3, float2 m4,
+                                       float2 p4) {
+    float2 r = mul2(splat2(float(kD1)), add2(p1, neg2(m1)));
+    r = fma2(splat2(float(kD2)), add2(p2, neg2(m2)), r);
+    r = fma2(splat2(float(kD3)), add2(p3, neg2(m3)), r);
+    r = fma2(splat2(float(kD4)), add2(p4, neg2(m4)), r);
+    return r;
+}
+
 // d2c on two cells: the same operations in the same order, lane by lane
 __device__ __forceinline__ float2 d2c2(float2 c, float2 m1, float2 p1, float2 m2, float2 p2, float2 m3, float2 p3,
                                        float2 m4, float2 p4) {
