@@ -51,6 +51,24 @@ __device__ __forceinline__ Pairs4 d2_pairs(const float4 &L, const float4 &C, con
     o.zb = d2c2(hi2(C), hi2(w[3]), hi2(w[5]), hi2(w[2]), hi2(w[6]), hi2(w[1]), hi2(w[7]), hi2(w[0]), hi2(w[8]));
     return o;
 }
+// First differences of a lane's four cells in pairs (d1c2): along x from the
+// row's float4s L, C, R, and along an axis from the float4s of the four
+// positions below (m4 .. m1) and above (p1 .. p4).
+__device__ __forceinline__ void d1x_pairs(const float4 &L, const float4 &C, const float4 &R, float2 &da, float2 &db) {
+    const float2 v34 = make_float2(L.w, C.x), v56 = make_float2(C.y, C.z), v12 = make_float2(L.y, L.z),
+                 v78 = make_float2(C.w, R.x), v910 = make_float2(R.y, R.z);
+    da = d1c2(v34, v56, hi2(L), hi2(C), v12, v78, lo2(L), lo2(R));
+    db = d1c2(v56, v78, lo2(C), lo2(R), v34, v910, hi2(L), hi2(R));
+}
+__device__ __forceinline__ void d1_pairs(const float4 &m4, const float4 &m3, const float4 &m2, const float4 &m1,
+                                         const float4 &p1, const float4 &p2, const float4 &p3, const float4 &p4,
+                                         float2 &da, float2 &db) {
+    da = d1c2(lo2(m1), lo2(p1), lo2(m2), lo2(p2), lo2(m3), lo2(p3), lo2(m4), lo2(p4));
+    db = d1c2(hi2(m1), hi2(p1), hi2(m2), hi2(p2), hi2(m3), hi2(p3), hi2(m4), hi2(p4));
+}
+// the CPML memory recursion b m + a d of a pair: fma(a, d, b m)
+__device__ __forceinline__ float2 rec2(float2 a, float2 d, float2 b, float2 m) { return fma2(a, d, mul2(b, m)); }
+
 // the plain leapfrog update p^{n+1} = fma(c, rhs, fma(2, p, -p^{n-1})) of
 // four cells in pairs; the scalar form is plain1 (the same roundings)
 __device__ __forceinline__ float4 plain4(const float4 &p, const float4 &pp, const float4 &c, float2 ra, float2 rb) {

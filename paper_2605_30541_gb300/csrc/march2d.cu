@@ -39,7 +39,10 @@ namespace gsim {
 namespace {
 
 using f32::cp_async16;
+using f32::d1_pairs;
 using f32::d1w;
+using f32::d1x_pairs;
+using f32::rec2;
 using f32::d2_pairs;
 using f32::d2w;
 using f32::Pairs4;
@@ -77,20 +80,14 @@ __device__ __forceinline__ float4 psi_z_row(const float4 &m4, const float4 &m3, 
                                             const float4 &p1, const float4 &p2, const float4 &p3, const float4 &p4,
                                             const float4 &old, const float az, const float bz, const int gx0,
                                             const int NX) {
-    float o[4];
+    float2 da, db;
+    d1_pairs(m4, m3, m2, m1, p1, p2, p3, p4, da, db);
+    const float2 a2 = rec2(splat2(az), da, splat2(bz), lo2(old)), b2 = rec2(splat2(az), db, splat2(bz), hi2(old));
+    float o[4] = {a2.x, a2.y, b2.x, b2.y};
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const float d1 = float(kD1) * (lane_of(p1, k) - lane_of(m1, k)) + float(kD2) * (lane_of(p2, k) - lane_of(m2, k)) +
-                         float(kD3) * (lane_of(p3, k) - lane_of(m3, k)) + float(kD4) * (lane_of(p4, k) - lane_of(m4, k));
-        o[k] = gx0 + k < NX ? bz * lane_of(old, k) + az * d1 : 0.f;
-    }
+    for (int k = 0; k < 4; k++)
+        if (gx0 + k >= NX) o[k] = 0.f;
     return make_float4(o[0], o[1], o[2], o[3]);
-}
-
-// z-part of the Laplacian (without 1/h^2) at cell k of the window row w[4]
-__device__ __forceinline__ float d2z_at(const float4 *w, int k) {
-    return d2c<float>(lane_of(w[4], k), lane_of(w[3], k), lane_of(w[5], k), lane_of(w[2], k), lane_of(w[6], k),
-                      lane_of(w[1], k), lane_of(w[7], k), lane_of(w[0], k), lane_of(w[8], k));
 }
 
 // ---------------------------------------------------------------- per-row I/O
@@ -609,15 +606,14 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
     // for the row's own cells, into the field
     auto psi_chunk = [&](const float *rz, const float *pso, float *pw, int c, const float4 &a4, const float4 &b4) {
         const int gx = x0 - 4 + 4 * c;
-        float w12[12];
-        unpack3(ld4(rz + 4 * c - 8), ld4(rz + 4 * c - 4), ld4(rz + 4 * c), w12);
         const float4 old = ld4(pso + 4 * c);
-        float o[4];
+        float2 da, db;
+        d1x_pairs(ld4(rz + 4 * c - 8), ld4(rz + 4 * c - 4), ld4(rz + 4 * c), da, db);
+        const float2 pa = rec2(lo2(a4), da, lo2(b4), lo2(old)), pb = rec2(hi2(a4), db, hi2(b4), hi2(old));
+        float o[4] = {pa.x, pa.y, pb.x, pb.y};
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const bool in = gx + k >= 0 && gx + k < NX;
-            o[k] = in ? lane_of(b4, k) * lane_of(old, k) + lane_of(a4, k) * d1w(w12, k) : 0.f;
-        }
+        for (int k = 0; k < 4; k++)
+            if (!(gx + k >= 0 && gx + k < NX)) o[k] = 0.f;
         const float4 o4 = make_float4(o[0], o[1], o[2], o[3]);
         st4(SC + 4 * c, o4);
         if (c >= 1 && c <= 32) st4(pw + gx, o4);
@@ -649,16 +645,14 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
                 psi_chunk(rz, pso, pw, c, __ldg(reinterpret_cast<const float4 *>(cax + x0 - 4 + 4 * c)),
                           __ldg(reinterpret_cast<const float4 *>(cbx + x0 - 4 + 4 * c)));
             __syncwarp();
-            float px[12];
-            unpack3(ld4(SC + 4 * lane), ld4(SC + 4 * lane + 4), ld4(SC + 4 * lane + 8), px);
             const float4 z4 = zxl ? ld4(os + C::O_ZX + 4 * lane) : make_float4(0.f, 0.f, 0.f, 0.f);
-            float zo[4];
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const float dps = d1w(px, k);
-                zo[k] = lane_of(bx4, k) * lane_of(z4, k) + lane_of(ax4, k) * (d2x[k] + dps);
-                cadd[k] += dps + zo[k];
-            }
+            float2 da, db;
+            d1x_pairs(ld4(SC + 4 * lane), ld4(SC + 4 * lane + 4), ld4(SC + 4 * lane + 8), da, db);
+            const float2 za = rec2(lo2(ax4), add2(dp.xa, da), lo2(bx4), lo2(z4));
+            const float2 zb = rec2(hi2(ax4), add2(dp.xb, db), hi2(bx4), hi2(z4));
+            const float2 ca = add2(da, za), cb = add2(db, zb);
+            const float zo[4] = {za.x, za.y, zb.x, zb.y};
+            cadd[0] += ca.x, cadd[1] += ca.y, cadd[2] += cb.x, cadd[3] += cb.y;
             if (zxl) st4(zex + ro, make_float4(zo[0], zo[1], zo[2], zo[3]));
         }
         if (cpz) {
@@ -685,16 +679,13 @@ __device__ __forceinline__ void march_cpml(const StepArgs<float> &A, const StepT
                     bz = __ldg(cbz + z);
                     z4 = ld4(os + C::O_ZZ + 4 * lane);
                 }
-                float zo[4];
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    const float dps = float(kD1) * (lane_of(qz[5], k) - lane_of(qz[3], k)) +
-                                      float(kD2) * (lane_of(qz[6], k) - lane_of(qz[2], k)) +
-                                      float(kD3) * (lane_of(qz[7], k) - lane_of(qz[1], k)) +
-                                      float(kD4) * (lane_of(qz[8], k) - lane_of(qz[0], k));
-                    zo[k] = bz * lane_of(z4, k) + az * (d2z[k] + dps);
-                    cadd[k] += dps + zo[k];
-                }
+                float2 da, db;
+                d1_pairs(qz[0], qz[1], qz[2], qz[3], qz[5], qz[6], qz[7], qz[8], da, db);
+                const float2 za = rec2(splat2(az), add2(dp.za, da), splat2(bz), lo2(z4));
+                const float2 zb = rec2(splat2(az), add2(dp.zb, db), splat2(bz), hi2(z4));
+                const float2 ca = add2(da, za), cb = add2(db, zb);
+                const float zo[4] = {za.x, za.y, zb.x, zb.y};
+                cadd[0] += ca.x, cadd[1] += ca.y, cadd[2] += cb.x, cadd[3] += cb.y;
                 if (in) st4(zez + ro, make_float4(zo[0], zo[1], zo[2], zo[3]));
             }
         }
