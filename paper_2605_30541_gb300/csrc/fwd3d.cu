@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, 
                         if (gx0 + k >= g.NX) res[k] = 0.f;
                 }
                 if (g.fs && z == 0) res[0] = res[1] = res[2] = res[3] = 0.f;
-                if (gy < g.NY) {
+                if (gy < g.NY && gx0 < g.NX) {  // cells past the grid stay zero: no store
                     const long long o = orow;
                     *reinterpret_cast<float4 *>(pn + o) = make_float4(res[0], res[1], res[2], res[3]);
                     if (MODE == kModeRecord)
@@ -1191,7 +1191,11 @@ cudaError_t make_maps(const StepArgs<float> &a, Tma3 &m) {
     const Geom &g = a.g;
     const long long ms = (a.pbuf[1] - a.pbuf[0]) / g.fstride;
     const long long planes = g.fstride / ((long long)g.PY * g.P);
-    const cuuint64_t dims[4] = {(cuuint64_t)g.P, (cuuint64_t)g.PY, (cuuint64_t)planes, (cuuint64_t)(2 * ms)};
+    // x extent: the ghost columns left of the grid, the grid and the 4 columns
+    // of the last cells' halo; columns past it (the padding of the last x tile,
+    // all zeros) come as the copy's zero fill instead of DRAM reads
+    const cuuint64_t nxt = std::min<cuuint64_t>((cuuint64_t)g.P, (cuuint64_t)(kGhost + g.NX + 4));
+    const cuuint64_t dims[4] = {nxt, (cuuint64_t)g.PY, (cuuint64_t)planes, (cuuint64_t)(2 * ms)};
     const cuuint64_t strides[3] = {(cuuint64_t)g.P * 4, (cuuint64_t)g.PY * g.P * 4, (cuuint64_t)g.fstride * 4};
     const cuuint32_t one[4] = {1, 1, 1, 1};
     const cuuint32_t bh[4] = {TX + 8, 16, 1, 1}, bo[4] = {TX, 8, 1, 1};
