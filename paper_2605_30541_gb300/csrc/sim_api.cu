@@ -1201,7 +1201,8 @@ int march_item_rows() {
     if (const char *f = getenv("GSIM_MARCH_ITEM")) k = std::max(4, atoi(f));
     return (k + 3) & ~3;
 }
-int plan_march_items(const std::vector<MarchMember> &mem, long long max_warps, int item, std::vector<MarchSeg> &segs) {
+int plan_march_items(const std::vector<MarchMember> &mem, long long max_warps, int item, std::vector<MarchSeg> &segs,
+                     int *ncpml = nullptr) {
     segs.clear();
     for (int pass = 0; pass < 2; pass++)
         for (const MarchMember &m : mem) {
@@ -1216,6 +1217,7 @@ int plan_march_items(const std::vector<MarchMember> &mem, long long max_warps, i
                                           (g.nbz0 > 0 && zc < g.nbz0 + 4) || (g.nbz1 > 0 && ze > NZ - g.nbz1 - 4));
                     if (c == (pass == 0)) segs.push_back(MarchSeg{m.slice, m.shot, bx, zc, ze, {0, 0, 0}});
                 }
+            if (pass == 0 && ncpml) *ncpml = (int)segs.size();
         }
     return (int)std::min<long long>(max_warps, (long long)segs.size());
 }
@@ -2158,7 +2160,9 @@ struct BatchCtx {
     size_t cap_slices = 0, cap_groups = 0, cap_members = 0, cap_done = 0;
     void *msegs = nullptr;  // row march items
     size_t cap_msegs = 0;
-    unsigned *mctr = nullptr;                  // row march: per-step item counters
+    unsigned *mctr = nullptr;                  // row march: per-step item counters (two pairs)
+    cudaStream_t st2 = nullptr;                // row march with CPML: the plain items' kernel
+    cudaEvent_t evf = nullptr, evj = nullptr;  //   forks to it and joins back each step
     void *tbm = nullptr, *tbs = nullptr;       // two-step march: members, receiver samples
     size_t cap_tbm = 0, cap_tbs = 0;
     cudaGraphExec_t exec = nullptr;
@@ -2357,14 +2361,16 @@ sim_status batch_run(int nitems, const sim_batch_item *items, cudaStream_t bst, 
         (e = cudaMemcpyAsync(ctx->members, members.data(), members.size() * sizeof(BatchMember),
                              cudaMemcpyHostToDevice, bst)))
         return fail(e, "upload");
-    MarchArgs mb{};
+    MarchArgs mb{}, mpl{};
+    bool split = false;
     if (march) {  // the row-march plan over all members
         std::vector<MarchMember> mm;
         for (const BatchMember &m : members) mm.push_back({m.slice, m.shot, items[m.slice].sim});
         std::vector<MarchSeg> segs;
         const long long maxw = (long long)sms * std::max(1, march2d_warps_per_sm(any_cpml));
-        const int nw = plan_march_items(mm, maxw, march_item_rows(), segs);
-        if (!ctx->mctr && (e = cudaMalloc(&ctx->mctr, 2 * sizeof(unsigned)))) return fail(e, "allocation");
+        int ncp = 0;
+        const int nw = plan_march_items(mm, maxw, march_item_rows(), segs, &ncp);
+        if (!ctx->mctr && (e = cudaMalloc(&ctx->mctr, 4 * sizeof(unsigned)))) return fail(e, "allocation");
         if ((e = grow(&ctx->msegs, &ctx->cap_msegs, segs.size() * sizeof(MarchSeg)))) {
             if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
             ctx->exec = nullptr;
@@ -2379,6 +2385,24 @@ sim_status batch_run(int nitems, const sim_batch_item *items, cudaStream_t bst, 
         mb.nwarps = nw;
         mb.nitems = (int)segs.size();
         mb.tz = tz;
+        // With CPML, the items that take the CPML loop run in the CPML instance
+        // of the kernel (2 CTAs per SM) and the plain ones in the plain
+        // instance (3 CTAs per SM) on a second stream: launched together each
+        // step, the plain kernel's CTAs take each SM as the CPML ones leave it.
+        const char *sp = getenv("GSIM_MARCH_SPLIT");
+        split = any_cpml && ncp > 0 && ncp < (int)segs.size() && !(sp && sp[0] == '0');
+        if (split) {
+            if (!ctx->st2 && (e = cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking))) return fail(e, "stream");
+            if (!ctx->evf && (e = cudaEventCreateWithFlags(&ctx->evf, cudaEventDisableTiming))) return fail(e, "event");
+            if (!ctx->evj && (e = cudaEventCreateWithFlags(&ctx->evj, cudaEventDisableTiming))) return fail(e, "event");
+            mpl = mb;
+            mpl.segs = static_cast<const MarchSeg *>(ctx->msegs) + ncp;
+            mpl.nitems = (int)segs.size() - ncp;
+            mpl.ctr = ctx->mctr + 2;
+            mpl.nwarps = (int)std::min<long long>((long long)sms * std::max(1, march2d_warps_per_sm(false)), mpl.nitems);
+            mb.nitems = ncp;
+            mb.nwarps = (int)std::min<long long>(maxw, ncp);
+        }
     }
     int tb_nwarps = 0;
     TBArgs tb{};
@@ -2433,7 +2457,7 @@ sim_status batch_run(int nitems, const sim_batch_item *items, cudaStream_t bst, 
                 for (int bx = 0; bx < nstrip; bx++)
                     segs.push_back(MarchSeg{(int)mi, m.shot, bx, zc, std::min(g.NZ, zc + rows), {0, 0, 0}});
         }
-        if (!ctx->mctr && (e = cudaMalloc(&ctx->mctr, 2 * sizeof(unsigned)))) return fail(e, "allocation");
+        if (!ctx->mctr && (e = cudaMalloc(&ctx->mctr, 4 * sizeof(unsigned)))) return fail(e, "allocation");
         if ((e = grow(&ctx->msegs, &ctx->cap_msegs, segs.size() * sizeof(MarchSeg))) ||
             (e = grow(&ctx->tbm, &ctx->cap_tbm, tm.size() * sizeof(TBMember))) ||
             (e = grow(&ctx->tbs, &ctx->cap_tbs, std::max<size_t>(1, ts.size()) * sizeof(TBSample)))) {
@@ -2479,13 +2503,15 @@ sim_status batch_run(int nitems, const sim_batch_item *items, cudaStream_t bst, 
     b.flags = ctx->flags;
     const int grid = sms * std::max(1, batch_blocks_per_sm(tz, any_cpml));
     // counters reset + the persistent kernel, replayed as one graph
-    const int kk[4] = {tz, (int)any_cpml | (stepped ? 2 : 0) | (march ? 4 : 0) | (march2 ? 8 : 0), grid, tb_nwarps};
-    std::vector<char> key(sizeof b + sizeof mb + sizeof tb + sizeof kk + sizeof done_total);
+    const int kk[4] = {tz, (int)any_cpml | (stepped ? 2 : 0) | (march ? 4 : 0) | (march2 ? 8 : 0) | (split ? 16 : 0), grid,
+                       tb_nwarps};
+    std::vector<char> key(sizeof b + 2 * sizeof mb + sizeof tb + sizeof kk + sizeof done_total);
     {
         char *k = key.data();
         memcpy(k, &b, sizeof b);
         memcpy(k += sizeof b, &mb, sizeof mb);
-        memcpy(k += sizeof mb, &tb, sizeof tb);
+        memcpy(k += sizeof mb, &mpl, sizeof mpl);
+        memcpy(k += sizeof mpl, &tb, sizeof tb);
         memcpy(k += sizeof tb, kk, sizeof kk);
         memcpy(k + sizeof kk, &done_total, sizeof done_total);
     }
@@ -2510,13 +2536,23 @@ sim_status batch_run(int nitems, const sim_batch_item *items, cudaStream_t bst, 
         }
         if (march) {
             cudaError_t r = cudaMemsetAsync(ctx->flags, 0, sizeof(unsigned), st);
-            if (r == cudaSuccess && mb.ctr) r = cudaMemsetAsync(mb.ctr, 0, 2 * sizeof(unsigned), st);
+            if (r == cudaSuccess && mb.ctr) r = cudaMemsetAsync(mb.ctr, 0, 4 * sizeof(unsigned), st);
             for (int n = 0; n < nsteps && r == cudaSuccess; n++) {
                 StepTime t{};
                 t.n = n;
                 t.snap_k = t.max_k = -1;
                 t.inj_row = n;
-                r = launch_march2d(mb, any_cpml, t, st, st != nullptr);
+                if (!split) {
+                    r = launch_march2d(mb, any_cpml, t, st, st != nullptr);
+                    continue;
+                }
+                // fork: the plain items on the second stream; join before the next step
+                if (r == cudaSuccess) r = cudaEventRecord(ctx->evf, st);
+                if (r == cudaSuccess) r = cudaStreamWaitEvent(ctx->st2, ctx->evf, 0);
+                if (r == cudaSuccess) r = launch_march2d(mb, true, t, st, false);
+                if (r == cudaSuccess) r = launch_march2d(mpl, false, t, ctx->st2, false);
+                if (r == cudaSuccess) r = cudaEventRecord(ctx->evj, ctx->st2);
+                if (r == cudaSuccess) r = cudaStreamWaitEvent(st, ctx->evj, 0);
             }
             return r;
         }
