@@ -383,6 +383,10 @@ def run_batch(args):
         algo = sum(algorithmic_bytes_two_step(c, len(c["src"]), nt) for c in slices)
     else:
         algo = sum(algorithmic_bytes_per_launch(c, len(c["src"])) for c in slices) * nt
+    # a batch with CPML runs its CPML and plain row-march items as two kernels per step
+    split = sched == "march" and any(c.get("bc") == "cpml" for c in slices) and \
+        os.environ.get("GSIM_MARCH_SPLIT", "1") != "0"
+    per_step = 2 if split else 1
     kfile, kname, kkey = (("fwd2d_f32.cu", "k_multi2d", "multi_") if sched == "stepped" else
                           ("fwd2d_f32.cu", "k_batch2d", "batch_") if sched == "persistent" else
                           ("march2x.cu", "k_march2x", "march2_") if sched == "march2" else
@@ -402,11 +406,12 @@ def run_batch(args):
             "roofline": {"bound": "hbm", "achieved": algo / (total / args.steps) / 1e9, "peak": peak,
                          "unit": "GB/s", "frac": algo / (total / args.steps) / 1e9 / peak,
                          "traffic": ncu_traffic(kfile, kkey + args.workload),
-                         "traffic_per": "pass launch (two steps)" if sched == "march2" else "step launch",
+                         "traffic_per": "pass launch (two steps)" if sched == "march2" else
+                         ("step (its two launches)" if split else "step launch"),
                          "kernel": kname, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_solve": algo},
             "clocks": clk.summary(),
-            "gpu_launches": args.steps * (2 * ((nt + 1) // 2) if sched == "march2" else nt)}
+            "gpu_launches": args.steps * (2 * ((nt + 1) // 2) if sched == "march2" else per_step * nt)}
     print(json.dumps(line), flush=True)
     for s in sims:
         s.close()
