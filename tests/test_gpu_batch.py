@@ -172,3 +172,18 @@ def test_autotuned_batch_matches_its_schedule_and_oracle(pkg, monkeypatch):
         assert rel(g[0].cpu().numpy(), o) <= 1e-4
     for s in sims:
         s.close()
+
+
+def test_cpml_batch_in_one_or_two_kernels(pkg, monkeypatch):
+    # a batch with CPML runs its CPML and plain row-march items as two kernels
+    # per step (on two streams); one kernel for all items gives the same bits
+    slices = uneven_slices(nt=120)
+    sims = sims_for(pkg, slices)
+    entries = [dict(sim=s, wavelet=c["wavelet"], src=c["src"], rec=c["rec"]) for s, c in zip(sims, slices)]
+    two = [g.clone() for g in pkg.batch(entries)]
+    monkeypatch.setenv("GSIM_MARCH_SPLIT", "0")
+    one = [g.clone() for g in pkg.batch(entries)]
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(one, two))
+    for s in sims:
+        s.close()

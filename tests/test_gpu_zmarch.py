@@ -90,7 +90,7 @@ def test_variants_give_the_same_gradient(pkg, monkeypatch):
     for k, s in enumerate(src):
         ref += oracle.gradient(cfg, v0.astype(np.float64), w.astype(np.float64), s, rec, d[k])["grad"]
     out = []
-    for variant in ("async", "tma"):
+    for variant in ("async", "tma", "tma-loop3", "tma-plain"):
         monkeypatch.setenv("GSIM_ZMARCH", variant)
         monkeypatch.setenv("GSIM_ZCHUNK", "11")
         sim = pkg.Simulator(cfg, v0, max_shots=len(src), max_rec=len(rec))
@@ -102,4 +102,6 @@ def test_variants_give_the_same_gradient(pkg, monkeypatch):
         out.append(grad.cpu().numpy())
         sim.close()
     assert rel(out[1], out[0]) <= 1e-6  # CPML: the x strips are folded into the TMA march
+    # unfolded TMA marches (record and adjoint modes, loop unrolled by 3 or 9): the cp.async march's bits
+    assert np.array_equal(out[2], out[0]) and np.array_equal(out[3], out[0])
     assert rel(out[0], ref) <= 1e-4 and rel(out[1], ref) <= 1e-4
