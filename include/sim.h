@@ -232,15 +232,19 @@ typedef struct {
 } sim_batch_item;
 
 /* Forward modelling of many shots on many (uneven) 2D FP32 grids in one
- * batch. All handles must share dt and nt. Default schedule: per time step
- * ONE launch of the row-march kernel over every (slice, shot, strip) of the
- * batch, warps taking row items from a per-step counter; the nt launches are
- * captured as one CUDA graph and replayed. The schedule (row march, the
- * stepped tile kernel, or one persistent dataflow launch for all steps whose
- * tiles wait on their neighbours with bounded waits, SIM_ERR_TIMEOUT when a
- * wait gives up) and the tile height are picked by timing on the first call
- * for a batch shape; GSIM_BATCH=march|stepped|persistent forces one.
- * `cuda_stream` as in sim_create. */
+ * batch. All handles must share dt and nt. Schedules: the row march, per
+ * time step one launch over every (slice, shot, strip) of the batch, warps
+ * taking row items from a per-step counter (two launches on two streams when
+ * members have CPML: the CPML items and the plain ones); the two-step row
+ * march (members without CPML: one launch per two steps, temporal
+ * blocking); the stepped tile kernel (one launch per step); one persistent
+ * dataflow launch for all steps whose tiles wait on their neighbours with
+ * bounded waits (SIM_ERR_TIMEOUT when a wait gives up). On a stream other
+ * than the legacy one the launches are captured as one CUDA graph and
+ * replayed. The schedule and the tile height are picked by timing on the
+ * first call for a batch shape (sim_get_info reports the pick);
+ * GSIM_BATCH=march|march2|stepped|persistent forces one. `cuda_stream` as in
+ * sim_create. */
 sim_status sim_batch(int nitems, const sim_batch_item *items, void *cuda_stream);
 
 /* The batch with a mode: 0 forward (sim_batch); 1 gradient: for each item,

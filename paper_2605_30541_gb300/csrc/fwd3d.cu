@@ -4,16 +4,18 @@
 // owns a 128 x TY column of the grid (TY = 8 RY); each lane owns 4
 // consecutive x cells in RY y-rows and keeps the 9 planes z-4 .. z+4 of those
 // cells in a register queue, so p^n is read from memory once per cell for the
-// z-derivative. The current plane with its radius-4 x/y halo is staged into a
-// double-buffered shared-memory tile by cp.async one plane ahead of use. The
-// update is the leapfrog step with the centred sponge term (Eq. cerjan_pde),
-// the free-surface plane z = 0 held at zero with an odd mirror above it
-// (Eq. free_surface), and no boundary arithmetic outside absorbing tiles.
+// z-derivative. The planes with their radius-4 x/y halo are staged into a
+// shared-memory ring ahead of use: by per-thread cp.async copies (k_step3d)
+// or by tensor-memory-accelerator copies that one thread issues (k_step3d_tma,
+// the autotuner's usual pick). The update is the leapfrog step with the
+// centred sponge term (Eq. cerjan_pde), the free-surface plane z = 0 held at
+// zero with an odd mirror above it (Eq. free_surface), and no boundary
+// arithmetic outside absorbing tiles.
 //
 // Side kernels of a step touch only small parts of the grid: the CPML memory
-// terms (psi before the update, zeta and the D1 psi + zeta addend after it,
-// strips only), point injection of the source, trilinear receiver sampling
-// and snapshot output.
+// terms of each axis (one pass after the update on its strips: psi, zeta and
+// the D1 psi + zeta addend), point injection of the source, trilinear
+// receiver sampling and snapshot output.
 #include <cfloat>
 
 #include <cudaTypedefs.h>

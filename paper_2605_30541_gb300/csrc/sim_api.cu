@@ -2182,14 +2182,16 @@ cudaError_t grow(void **p, size_t *cap, size_t need) {
     return e;
 }
 
-// Batch schedules: the row march (one launch per step over every member),
-// the stepped tile kernel (one launch per step) and the persistent dataflow
+// Batch schedules: the row march (one launch per step over every member; two
+// concurrent launches when members have CPML: the CPML items and the plain
+// ones), the two-step row march (one launch per two steps, no CPML), the
+// stepped tile kernel (one launch per step) and the persistent dataflow
 // kernel (one launch for all steps).
 enum { kBatchMarch = 0, kBatchStepped = 1, kBatchPersistent = 2, kBatchMarch2 = 3 };
 
 // One batch run with a given schedule and list tile height. probe > 0: run
 // only that many steps, launched directly (the autotuner's timing probe; no
-// graph, no output copies).
+// graph, no output copies), with pe0 / pe1 recorded around the launches.
 sim_status batch_run(int nitems, const sim_batch_item *items, cudaStream_t bst, int sched, int tz_in, int probe,
                      cudaEvent_t pe0 = nullptr, cudaEvent_t pe1 = nullptr) {
     if (nitems < 1 || !items) return thread_fail(SIM_ERR_ARG, "empty batch");
