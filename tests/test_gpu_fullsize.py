@@ -5,7 +5,8 @@
   FP64 oracle, with the relative L2 error reported every 1000 steps (FP32
   drift over the whole record).
 - One shot of the paper's 64-shot production gather run (60-cell sponge,
-  band-passed source, nt = 8001) on the row march, and the 5 s production
+  band-passed source, nt = 8001) on the batch autotuner's schedule (the
+  one-step or the two-step row march), and the 5 s production
   wavefield (358 snapshots, nt = 5001) on the resident path.
 - The 3D volume at its full size (619 x 1000 x 1000 + 30-cell CPML on x, y
   and bottom, free top: 729 M padded cells, 2.9 GB per field) for the first

@@ -150,3 +150,20 @@ def test_autotuner_candidates_without_cpml(pkg, monkeypatch):
     assert any(all(torch.equal(a, b) for a, b in zip(tuned, f)) for f in forced)
     for s in sims:
         s.close()
+
+
+def test_production_gathers_full_length(pkg):
+    # the production run itself (64 shots, 8001 steps, 60-cell sponge, free
+    # surface, 1000 receivers, band-passed wavelet): the two-step march gives
+    # the one-step march's bits on every gather sample (whichever of the two
+    # the batch autotuner picks is compared with the FP64 oracle at full
+    # length in test_gpu_fullsize)
+    c6 = synth.config_c6("gather")
+    lo, hi, f0 = c6["band"]
+    wav = pkg.bandpass_ricker(c6["nt"], c6["dt"], f0, lo, hi).cpu().numpy()
+    sim = pkg.Simulator(c6, c6["vel"], max_shots=len(c6["src"]), max_rec=len(c6["rec"]))
+    one = run(pkg, [sim], [dict(c6, wavelet=wav)], "march")[0]
+    two = run(pkg, [sim], [dict(c6, wavelet=wav)], "march2")[0]
+    assert torch.isfinite(two).all()
+    assert torch.equal(one, two)
+    sim.close()
