@@ -353,6 +353,19 @@ __device__ __forceinline__ void tile_step(const StepArgs<float> &A, const StepTi
         const int o = lo + j * P;
         float v[12];
         unpack3(ld4(S + (rb + j) * SW + c0 - 4), zw[j + 4], ld4(S + (rb + j) * SW + c0 + 4), v);
+        // second differences in FP32 pairs (the bits of d2w / d2c cell by cell)
+        float2 dxa, dxb, dza, dzb;
+        {
+            const float4 L = ld4(S + (rb + j) * SW + c0 - 4), C = zw[j + 4], R = ld4(S + (rb + j) * SW + c0 + 4);
+            const float2 v34 = make_float2(L.w, C.x), v56 = make_float2(C.y, C.z), v12 = make_float2(L.y, L.z),
+                         v78 = make_float2(C.w, R.x), v910 = make_float2(R.y, R.z);
+            dxa = d2c2(lo2(C), v34, v56, hi2(L), hi2(C), v12, v78, lo2(L), lo2(R));
+            dxb = d2c2(hi2(C), v56, v78, lo2(C), lo2(R), v34, v910, hi2(L), hi2(R));
+            const float4 *q = zw + j;
+            dza = d2c2(lo2(C), lo2(q[3]), lo2(q[5]), lo2(q[2]), lo2(q[6]), lo2(q[1]), lo2(q[7]), lo2(q[0]), lo2(q[8]));
+            dzb = d2c2(hi2(C), hi2(q[3]), hi2(q[5]), hi2(q[2]), hi2(q[6]), hi2(q[1]), hi2(q[7]), hi2(q[0]), hi2(q[8]));
+        }
+        const float d2xs[4] = {dxa.x, dxa.y, dxb.x, dxb.y}, d2zs[4] = {dza.x, dza.y, dzb.x, dzb.y};
         float res[4], qk[4];
         float4 inj4 = make_float4(0, 0, 0, 0), ext4 = make_float4(0, 0, 0, 0);
         if (has_inj) inj4 = ld4(INJ + lz * TX + 4 * lane);
@@ -361,10 +374,7 @@ __device__ __forceinline__ void tile_step(const StepArgs<float> &A, const StepTi
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             const float p = v[4 + k];
-            const float d2x = d2w(v, k);
-            const float d2z = d2c<float>(p, lane_of(zw[j + 3], k), lane_of(zw[j + 5], k), lane_of(zw[j + 2], k), lane_of(zw[j + 6], k),
-                                         lane_of(zw[j + 1], k), lane_of(zw[j + 7], k), lane_of(zw[j], k), lane_of(zw[j + 8], k));
-            float rhs = d2z + d2x;
+            float rhs = d2zs[k] + d2xs[k];
             if (cpx || cpz) rhs += lane_of(cadd[j], k);
             if (MODE == kModeAdjoint && A.cext) rhs += lane_of(ext4, k);
             if (has_inj) rhs += A.src_scale * lane_of(inj4, k);
