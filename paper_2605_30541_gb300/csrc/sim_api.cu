@@ -2677,8 +2677,8 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
         cudaGetLastError();
         return thread_fail(SIM_ERR_CUDA, "batch autotune: event creation failed");
     }
-    float best = 1e30f;
-    std::pair<int, int> pick = cand[0];
+    float best = 1e30f, best1 = 1e30f;  // best1: the fastest schedule of one step per launch
+    std::pair<int, int> pick = cand[0], pick1 = cand[0];
     sim_status rc = SIM_OK;
     for (const auto &c : cand) {
         const int steps = 6;
@@ -2695,10 +2695,14 @@ sim_status batch_impl(int nitems, const sim_batch_item *items, cudaStream_t bst)
                     c.first == kBatchMarch ? "march" : c.first == kBatchMarch2 ? "two-step march" : "stepped",
                     c.second, 1e3 * ms / steps);
         if (ms < best) best = ms, pick = c;
+        if (c.first != kBatchMarch2 && ms < best1) best1 = ms, pick1 = c;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
+    // the two-step march only when it is clearly faster than every schedule
+    // of one launch per step (a probe difference within 2% is noise)
+    if (pick.first == kBatchMarch2 && best1 < 1.02f * best) pick = pick1;
     {
         std::lock_guard<std::mutex> lk(g_btune_mu);
         g_btune[key] = pick;
