@@ -68,3 +68,21 @@ def test_padded_cells(bench):
     c = small_3d_cpml()
     nb = c["nb"]
     assert bench.padded_cells(c) == (nb[0] + 20 + nb[1]) * (nb[2] + 24 + nb[3]) * (nb[4] + 28 + nb[5])
+
+
+@pytest.mark.parametrize("nt", [1, 2, 7, 8001])
+def test_two_step_bytes_match_a_pass_by_pass_count(bench, nt):
+    # the two-step row march moves, per pass, p^n, p^{n-1}, c in and p^{n+1},
+    # p^{n+2} out (20 B per cell), or 16 B when the last pass has one step;
+    # every step samples each receiver once (4 B)
+    c = synth.config_c6("gather", nt=nt)
+    shots = len(c["src"])
+    nb = c["nb"]
+    cells = (nb[0] + c["nz"] + nb[1]) * (nb[4] + c["nx"] + nb[5])
+    total, n = 0, 0
+    while n < nt:
+        two = n + 1 < nt
+        total += cells * (20 if two else 16)
+        n += 2 if two else 1
+    total = shots * (total + 4 * len(c["rec"]) * nt)
+    assert bench.algorithmic_bytes_two_step(c, shots, nt) == total
