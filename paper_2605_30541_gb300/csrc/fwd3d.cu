@@ -357,7 +357,7 @@ template <int MODE, int UN>
 __global__ void __launch_bounds__(NTH, 2) k_step3d_tma(const StepArgs<float> A, const __grid_constant__ Tma3 M,
                                                        const int n, const int zchunk, const int ms, const XFuse X,
                                                        float *qs, float *Gs, const long long spin) {
-    constexpr int TY = NW, NR = TY + 8;
+    constexpr int TY = NW;
     extern __shared__ __align__(128) unsigned char sm_t[];
     unsigned char *const hring = sm_t, *const oring = sm_t + NSH * HALO_T;
     unsigned long long *const fh = reinterpret_cast<unsigned long long *>(sm_t + NSH * HALO_T + NSO * OSLOT_T);
@@ -773,9 +773,6 @@ __global__ void k_cpml_add3d(const StepArgs<float> A, const int n, const int ax,
 // other buffer). Same arithmetic as k_psi3d + k_cpml_add3d, with every value
 // read once. Not used for a z range within reach of a free surface (its D2
 // needs the odd mirror; the two-kernel path handles it).
-__device__ __forceinline__ float comp4(const float4 &v, int c) {
-    return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
-}
 
 constexpr int CNS = 4;  // positions in a column pass thread's copy ring
 

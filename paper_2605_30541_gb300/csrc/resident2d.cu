@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(NTR, 1) k_resident2d(const StepArgs<float> A, 
         for (int j = 0; j < RZ + 8; j++) zw[j] = ld4(cur + (rb - 4 + j) * SW + c0);
 #pragma unroll
         for (int j = 0; j < RZ; j++) {
-            const int lz = w * rpw + j, gz = z0 + lz;
+            const int lz = w * rpw + j;
             if (j >= rpw || lz >= rows) continue;
             float v[12];
             unpack3(ld4(cur + (rb + j) * SW + c0 - 4), zw[j + 4], ld4(cur + (rb + j) * SW + c0 + 4), v);
